@@ -1,0 +1,148 @@
+"""Pins for the oracle's tile map and tile-level symbolic factorization.
+
+* with T = 1 the tile closure must equal the nonzero pattern of the
+  numerical Cholesky factor computed by LAPACK (random values, no
+  cancellation);
+* for T > 1 the closure must equal the LAPACK factor pattern of the
+  quotient (tile) matrix, and contain every tile that the element-level
+  factor touches;
+* closed form for a full band plus a dense arrow;
+* the paper's accumulation count of Section V.E (4,166 at n = 500,010,
+  tile 120, arrow 10);
+* a dense matrix's task flops equal the dense Cholesky count.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ordering, tiles
+from paper_2501_02483_b300 import inputs
+
+
+def _random_sparse_spd(n, density, seed, n_arrow=0):
+    rng = np.random.default_rng(seed)
+    mask = np.tril(rng.random((n, n)) < density, -1)
+    if n_arrow:
+        mask[n - n_arrow:, :] = np.tril(np.ones((n_arrow, n), bool), n - n_arrow - 1)
+    r, c = np.nonzero(mask)
+    vals = rng.uniform(-1, 1, r.size)
+    a = np.zeros((n, n))
+    a[r, c] = vals
+    a = a + a.T
+    a += np.diag(np.abs(a).sum(axis=1) + 1.0)
+    rr, cc = np.nonzero(np.tril(a))
+    colptr, rowidx, values = inputs.coo_to_csc_lower(n, rr, cc, a[rr, cc])
+    return {"n": n, "n_arrow": n_arrow, "colptr": colptr, "rowidx": rowidx, "values": values}, a
+
+
+def _lapack_pattern(a):
+    l = np.linalg.cholesky(a)
+    return np.abs(l) > 0
+
+
+def _closure_set(m, T, perm=None):
+    n = m["n"]
+    perm = np.arange(n) if perm is None else perm
+    nt, tcolptr, trowidx = tiles.plan(n, m["colptr"], m["rowidx"], perm, T)
+    s = set()
+    for k in range(nt):
+        for i in trowidx[tcolptr[k]:tcolptr[k + 1]]:
+            s.add((int(i), k))
+    return nt, s
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_closure_T1_equals_lapack_pattern(seed):
+    m, a = _random_sparse_spd(60, 0.05, seed, n_arrow=seed % 3)
+    _, s = _closure_set(m, 1)
+    pat = _lapack_pattern(a)
+    expect = {(int(i), int(j)) for i, j in zip(*np.nonzero(pat))}
+    assert s == expect
+
+
+@pytest.mark.parametrize("seed,T", [(0, 3), (1, 4), (2, 5), (3, 7), (4, 8), (5, 16)])
+def test_closure_equals_quotient_factor_pattern(seed, T):
+    m, a = _random_sparse_spd(120, 0.02, seed, n_arrow=2)
+    nt, s = _closure_set(m, T)
+    # quotient matrix: random SPD values on the tile pattern of A
+    rng = np.random.default_rng(100 + seed)
+    q = np.zeros((nt, nt))
+    nz = np.abs(a) > 0
+    for i in range(nt):
+        for j in range(i):
+            if nz[i * T:(i + 1) * T, j * T:(j + 1) * T].any():
+                q[i, j] = q[j, i] = rng.uniform(0.1, 1.0)
+    q += np.diag(np.abs(q).sum(axis=1) + 1.0)
+    expect = {(int(i), int(j)) for i, j in zip(*np.nonzero(_lapack_pattern(q)))}
+    assert s == expect
+    # the element-level factor never touches a tile outside the closure
+    pat = _lapack_pattern(a)
+    touched = {(int(i) // T, int(j) // T) for i, j in zip(*np.nonzero(pat))}
+    assert touched <= s
+    assert nt <= 40
+
+
+@pytest.mark.parametrize("n_body,b,w,T", [(200, 10, 3, 8), (500, 37, 10, 16), (300, 64, 5, 32), (257, 1, 1, 64)])
+def test_full_band_plus_arrow_closed_form(n_body, b, w, T):
+    m = inputs.band_arrow(n_body, w, b, 1.0, 0)
+    nt, s = _closure_set(m, T)
+    c = -(-b // T)  # ceil(b / T): tile half-width of a full band of half-width b
+    expect = set()
+    first_arrow_tile = n_body // T
+    for i in range(nt):
+        if i >= first_arrow_tile and w > 0:
+            expect.update((i, j) for j in range(i + 1))
+        else:
+            expect.update((i, j) for j in range(max(0, i - c), i + 1))
+    assert s == expect
+
+
+def test_paper_accumulation_count_id14():
+    """Section V.E: with tile 120, the n = 500,010 matrix with a 10-wide arrow
+    has 4,166 accumulations into the arrow's corner tile."""
+    m = inputs.band_arrow(500_000, 10, 1, 1.0, 0, nrhs=0)
+    nt, tcolptr, trowidx = tiles.plan(m["n"], m["colptr"], m["rowidx"], np.arange(m["n"]), 120)
+    rows = tiles.row_lists(nt, tcolptr, trowidx)
+    corner = nt - 1
+    assert sum(1 for j in rows[corner] if j < corner) == 4166
+
+
+def test_paper_accumulation_count_id2_reading():
+    """The same count for the n = 10,010 matrix is 83 on this reading; the
+    paper prints 84 (recorded as a deviation)."""
+    m = inputs.band_arrow(10_000, 10, 1, 1.0, 0, nrhs=0)
+    nt, tcolptr, trowidx = tiles.plan(m["n"], m["colptr"], m["rowidx"], np.arange(m["n"]), 120)
+    rows = tiles.row_lists(nt, tcolptr, trowidx)
+    assert sum(1 for j in rows[nt - 1] if j < nt - 1) == 83
+
+
+@pytest.mark.parametrize("n,T", [(50, 7), (64, 16), (65, 16), (100, 100), (33, 1)])
+def test_dense_task_flops_equal_dense_cholesky(n, T):
+    idx = np.tril_indices(n)
+    colptr, rowidx, values = inputs.coo_to_csc_lower(n, idx[0], idx[1], np.ones(idx[0].size))
+    m = {"n": n, "n_arrow": 0, "colptr": colptr, "rowidx": rowidx, "values": values}
+    nt, tcolptr, trowidx = tiles.plan(n, colptr, rowidx, np.arange(n), T)
+    f = tiles.task_flops(n, T, tcolptr, trowidx)
+    assert f["total"] == n * (n + 1) * (2 * n + 1) // 6
+
+
+def test_permuted_entries_land_in_lower_triangle():
+    m = inputs.band_arrow(100, 4, 5, 0.5, 3)
+    perm = ordering.partial_rcm(m["n"], m["colptr"], m["rowidx"], m["n_arrow"])
+    r, c = tiles.permuted_lower_entries(m["n"], m["colptr"], m["rowidx"], perm)
+    assert np.all(r >= c)
+    a = inputs.dense_from_csc(m)
+    pa = a[np.ix_(perm, perm)]
+    assert np.count_nonzero(np.tril(pa)) == r.size
+    assert np.all(np.tril(pa)[r, c] != 0)
+
+
+def test_neighbors_symmetric_and_filled():
+    m, _ = _random_sparse_spd(80, 0.03, 9, n_arrow=2)
+    nt, tcolptr, trowidx = tiles.plan(m["n"], m["colptr"], m["rowidx"], np.arange(m["n"]), 8)
+    nb = tiles.neighbors(nt, tcolptr, trowidx)
+    for k in range(nt):
+        for j in nb[k]:
+            assert k in nb[j]
+    assert math.isfinite(float(nt))
