@@ -1,0 +1,186 @@
+/*
+ * stiles.h - C ABI of the B300 arrowhead tile Cholesky library (libstiles.so).
+ *
+ * The library factorizes a sparse symmetric positive-definite matrix with a
+ * block-arrowhead pattern (a variable-bandwidth band plus a thin dense arrow of
+ * trailing rows/columns) by the sTiles method: a fill-reducing permutation of
+ * the band part (Section III.A), a tile map in Compressed Tile Storage Format
+ * (Section III.B), a tile-level symbolic factorization (Section II, step 2) and
+ * the left-looking sparse tile Cholesky of Algorithm 1, whose long accumulation
+ * chains are summed as trees (Section IV.A, Algorithm 3).  On top of the factor
+ * it computes the log-determinant and forward/backward solves.
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ *  - Matrices enter as the LOWER triangle including the diagonal, in
+ *    compressed sparse column form: colptr[n+1] (int64, colptr[0] = 0),
+ *    rowidx[nnz] (int32, strictly ascending inside a column, every row >= the
+ *    column, the diagonal entry present), values[nnz] (double).
+ *  - Only the pattern defines a plan; one plan serves every matrix with the
+ *    same pattern (Section III.A: preprocessing pays off when many
+ *    factorizations share one structure).
+ *  - Pointers marked "host or device" may point to either; the library looks
+ *    the pointer up with the CUDA runtime and copies host data itself.
+ *  - Caller arrays are borrowed for the duration of the call only.  Handles
+ *    own all memory they allocate; the matching destroy call frees it.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that return results on the host synchronize that stream.
+ *  - Every call returns a stiles_status.  Nothing falls back to the CPU.
+ *  - The library is not thread-safe per handle: one handle must not be used
+ *    from two host threads at once.
+ */
+#ifndef STILES_H
+#define STILES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stiles_plan stiles_plan;     /* opaque: pattern analysis, host + device arrays */
+typedef struct stiles_factor stiles_factor; /* opaque: device tiles of one factorization      */
+
+typedef enum {
+  STILES_OK = 0,
+  STILES_ERR_INVALID = 1,        /* bad argument or malformed CSC input                        */
+  STILES_ERR_NOT_SPD = 2,        /* a pivot was <= 0 or NaN; *info holds the permuted column  */
+  STILES_ERR_NOMEM = 3,          /* host or device allocation failed                          */
+  STILES_ERR_CUDA = 4,           /* a CUDA runtime call failed                                */
+  STILES_ERR_TIMEOUT = 5,        /* a device wait exceeded opts.spin_limit; kernels returned  */
+  STILES_ERR_NOT_CONVERGED = 6,  /* iterative refinement missed refine_tol                    */
+  STILES_ERR_UNSUPPORTED = 7     /* option combination not built into this library           */
+} stiles_status;
+
+enum { STILES_ORDER_NONE = 0, STILES_ORDER_RCM = 1, STILES_ORDER_AUTO = 2 };
+enum { STILES_PREC_F64 = 0, STILES_PREC_BF16 = 1, STILES_PREC_F16 = 2 };
+
+typedef struct {
+  int32_t tile;       /* T, the CTSF tile size.  analyze accepts any T >= 1; factorize needs a
+                         multiple of 16.  Default 32.                                           */
+  int32_t ordering;   /* STILES_ORDER_*: NONE keeps the input order, RCM applies partial RCM to
+                         the band rows, AUTO keeps RCM only if it gives strictly fewer L tiles
+                         (Section III.A, closing rule).  Default AUTO.                          */
+  int32_t precision;  /* STILES_PREC_*: arithmetic of the off-diagonal tile updates.  Default F64. */
+  int32_t block;      /* B, the device sub-tile size: 16, 32 or 64 dividing T; 0 = min(T, 32).   */
+  int32_t tree_chunk; /* accumulation terms per tree leaf (Algorithm 3); 0 = 32.  Tasks with more
+                         terms are split into leaves summed by a fixed-shape tree.               */
+  int32_t tree_fanin; /* partial tiles summed per tree node; 0 = 16.                             */
+  int32_t max_refine; /* iterative-refinement steps for low-precision factors; default 20.      */
+  int32_t reserved0;
+  double refine_tol;  /* target ||b - A x||_2 / ||b||_2 of a refined solve; default 1e-10.       */
+  int64_t spin_limit; /* bound on any device wait, in polling iterations; default 2^24 (about 16 s).         */
+} stiles_opts;
+
+typedef struct {
+  int64_t n, n_arrow, nnz;
+  int64_t tile;        /* T                                                            */
+  int64_t nt;          /* tiles per side, ceil(n / T)                                  */
+  int64_t nnzt;        /* tiles of L (lower, diagonal included) after symbolic closure */
+  int64_t block;       /* B                                                            */
+  int64_t nsub;        /* B x B sub-tiles stored (nnzt * (T/B)^2)                      */
+  int64_t ntasks;      /* device factorization tasks                                   */
+  int64_t npairs;      /* tile-pair updates (GEMM/SYRK terms) at sub-tile granularity  */
+  int64_t nscratch;    /* tree-reduction partial tiles                                 */
+  int64_t flops_potrf, flops_syrk, flops_gemm, flops_trsm, flops_total; /* at tile size T */
+  int64_t factor_bytes;  /* device bytes of the tile buffer                            */
+  int32_t ordering_used; /* STILES_ORDER_NONE or STILES_ORDER_RCM                      */
+  int32_t reserved0;
+} stiles_plan_info;
+
+/* Fill *opts with the defaults listed above. */
+void stiles_default_opts(stiles_opts* opts);
+
+/* Symbolic analysis (host only; no GPU needed).  Section II steps 1-2, Section III.A-B.
+ *   n, colptr, rowidx : lower CSC pattern, host arrays (see conventions).
+ *   n_arrow           : number of trailing arrow rows/columns (0 <= n_arrow <= n); the
+ *                       ordering leaves them in place at the end.
+ *   opts              : may be NULL for defaults.
+ *   out               : receives a new plan; destroy with stiles_plan_destroy.
+ * Errors: STILES_ERR_INVALID for malformed input (unsorted or duplicate rows, upper
+ * entries, missing diagonal, T < 1), STILES_ERR_NOMEM. */
+stiles_status stiles_analyze(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                             const stiles_opts* opts, stiles_plan** out);
+
+/* Sizes, flop counts and choices of a plan. */
+stiles_status stiles_plan_get_info(const stiles_plan* plan, stiles_plan_info* info);
+
+/* The permutation, perm[new] = old (host array of n int64). */
+stiles_status stiles_plan_perm(const stiles_plan* plan, int64_t* perm);
+
+/* The tile map of L in tile-CSC form (host arrays): tcolptr[nt+1], trowidx[nnzt]; inside a
+ * tile column the diagonal tile comes first, then rows ascending.  Either pointer may be NULL. */
+stiles_status stiles_plan_tilemap(const stiles_plan* plan, int64_t* tcolptr, int32_t* trowidx);
+
+/* Numeric factorization P A P^T = L L^T (Algorithm 1).
+ *   values : the nnz values in the plan's CSC order, host or device.
+ *   stream : CUDA stream; the call waits for it and returns the device status.
+ *   inout  : *inout == NULL allocates a new factor; a factor from an earlier call on the
+ *            same plan is refactorized in place (no allocation).
+ *   info   : may be NULL; on STILES_ERR_NOT_SPD receives the 1-based permuted column of
+ *            the first pivot that was <= 0 or NaN (LAPACK convention), else 0.
+ * Errors: STILES_ERR_NOT_SPD (the factor is then invalid), STILES_ERR_TIMEOUT,
+ * STILES_ERR_CUDA, STILES_ERR_NOMEM, STILES_ERR_UNSUPPORTED (T not a multiple of 16). */
+stiles_status stiles_factorize(const stiles_plan* plan, const double* values, void* stream,
+                               stiles_factor** inout, int64_t* info);
+
+/* As stiles_factorize but only enqueues the work; collect the status with
+ * stiles_factor_wait.  *inout must already hold a factor of this plan, or be NULL (then
+ * the allocation happens here, before anything is enqueued). */
+stiles_status stiles_factorize_async(const stiles_plan* plan, const double* values, void* stream,
+                                     stiles_factor** inout);
+stiles_status stiles_factor_wait(stiles_factor* factor, int64_t* info);
+
+/* log det A = 2 sum_i log L_ii, reduced on the device in a fixed order; *out on the host. */
+stiles_status stiles_logdet(const stiles_factor* factor, double* out);
+
+/* Solve A X = B for nrhs right-hand sides: X = P^T L^{-T} L^{-1} P B.
+ *   b, x  : n x nrhs, column-major with leading dimension ld >= n, host or device (both
+ *           on the same side); x may equal b.
+ *   final_relres : may be NULL; else receives max over columns of ||b - A x||_2 / ||b||_2,
+ *           computed in FP64 on the device from the original values.
+ * Errors: STILES_ERR_INVALID, STILES_ERR_TIMEOUT, STILES_ERR_CUDA. */
+stiles_status stiles_solve(const stiles_factor* factor, const double* b, double* x, int64_t nrhs, int64_t ld,
+                           void* stream, double* final_relres);
+
+/* Copy the factor out as T x T column-major tiles in tile-CSC order (nnzt * T * T doubles),
+ * host or device.  Rows/columns past n are padding (identity on the diagonal). */
+stiles_status stiles_factor_tiles(const stiles_factor* factor, double* out, void* stream);
+
+void stiles_plan_destroy(stiles_plan* plan);
+void stiles_factor_destroy(stiles_factor* factor);
+const char* stiles_strerror(stiles_status status);
+
+/* Human-readable detail of the last error raised on the calling host thread ("" if none). */
+const char* stiles_last_error(void);
+
+/* Device time of the last factorization of `factor` (CUDA events on its stream):
+ * *ms_call from the start of the call (value copy, tile zeroing, scatter) to the end of the
+ * persistent kernel, *ms_kernel of the persistent factorization kernel alone.  Either may be NULL. */
+stiles_status stiles_factor_timing(const stiles_factor* factor, double* ms_call, double* ms_kernel);
+
+/* Tracing (profiling aid).  When enabled, every persistent launch of `factor` (factorization,
+ * forward and backward sweeps) stamps each ticket with the device global timer: 4 int64 per
+ * task = start, all dependencies ready, done (ns), SM id.  Tracing costs a few global stores
+ * per task.  stiles_factor_get_trace copies the stamps of launch `which` (0 factorization,
+ * 1 forward, 2 backward) to the host array out[4 * ntasks]; out may be NULL to query ntasks. */
+stiles_status stiles_factor_set_trace(stiles_factor* factor, int32_t enable);
+stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which, int64_t* out, int64_t* ntasks);
+
+/* The device task list of a plan (which: 0 factorization, 1 forward, 2 backward sweep), 8 int32
+ * per task in ticket order: type, output, diagonal sub-tile, column, pair range [pb, pe),
+ * partial range [qb, qe).  out may be NULL to query ntasks. */
+stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
+
+/* Number of CUDA kernels this library has launched in this process (all threads). */
+int64_t stiles_kernel_launches(void);
+
+/* Measured FP64 DFMA throughput of the current device in TFLOP/s (a fixed-length FMA loop
+ * on every SM, timed with CUDA events), used as the roofline denominator of the FP64 path. */
+stiles_status stiles_probe_fp64_peak(double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STILES_H */

@@ -1,0 +1,692 @@
+// Host-side symbolic analysis: input validation, partial RCM ordering
+// (Section III.A), the CTSF tile map (Section III.B), the tile-level symbolic
+// factorization (Section II, step 2), task flop counts, and the device task
+// graph of the factorization and of the solves.
+//
+// Nothing here touches the GPU; stiles_analyze can run on any host.
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+#include "plan.h"
+
+namespace stiles {
+
+void default_opts(stiles_opts* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->tile = 32;
+  o->ordering = STILES_ORDER_AUTO;
+  o->precision = STILES_PREC_F64;
+  o->block = 0;
+  o->tree_chunk = 32;
+  o->tree_fanin = 16;
+  o->max_refine = 20;
+  o->refine_tol = 1e-10;
+  o->spin_limit = int64_t(1) << 24;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Partial Reverse Cuthill-McKee on the body block [0, nb).
+// Tie-breaks (the paper leaves them open): degree = number of distinct body
+// neighbours; components in order of their smallest vertex; George-Liu
+// pseudo-peripheral start found from the min-(degree, index) vertex of the
+// component, moving to the min-(degree, index) vertex of the last BFS level
+// while the level structure gets strictly deeper; neighbours enqueued in
+// ascending (degree, index); the body sequence is reversed at the end.
+// ---------------------------------------------------------------------------
+struct Graph {
+  int64_t nb = 0;
+  std::vector<int64_t> ptr, adj;
+  int64_t deg(int64_t v) const { return ptr[v + 1] - ptr[v]; }
+};
+
+Graph body_graph(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t nb) {
+  Graph g;
+  g.nb = nb;
+  std::vector<int64_t> cnt(nb + 1, 0);
+  for (int64_t j = 0; j < nb; ++j)
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      int64_t i = rowidx[e];
+      if (i != j && i < nb) { ++cnt[i]; ++cnt[j]; }
+    }
+  g.ptr.assign(nb + 1, 0);
+  for (int64_t v = 0; v < nb; ++v) g.ptr[v + 1] = g.ptr[v] + cnt[v];
+  g.adj.resize(g.ptr[nb]);
+  std::vector<int64_t> fill(g.ptr.begin(), g.ptr.end() - 1);
+  for (int64_t j = 0; j < nb; ++j)
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      int64_t i = rowidx[e];
+      if (i != j && i < nb) { g.adj[fill[i]++] = j; g.adj[fill[j]++] = i; }
+    }
+  for (int64_t v = 0; v < nb; ++v) std::sort(g.adj.begin() + g.ptr[v], g.adj.begin() + g.ptr[v + 1]);
+  (void)n;
+  return g;
+}
+
+struct Levels {
+  std::vector<int64_t> verts;  // BFS visit order
+  std::vector<int64_t> start;  // level l = verts[start[l] .. start[l+1])
+  int64_t depth() const { return int64_t(start.size()) - 1; }
+};
+
+void bfs_levels(const Graph& g, int64_t root, std::vector<int64_t>& stamp, int64_t& mark, Levels& L) {
+  ++mark;
+  L.verts.clear();
+  L.start.clear();
+  L.verts.push_back(root);
+  stamp[root] = mark;
+  L.start.push_back(0);
+  size_t b = 0;
+  while (true) {
+    size_t e = L.verts.size();
+    for (size_t idx = b; idx < e; ++idx) {
+      int64_t v = L.verts[idx];
+      for (int64_t a = g.ptr[v]; a < g.ptr[v + 1]; ++a) {
+        int64_t u = g.adj[a];
+        if (stamp[u] != mark) { stamp[u] = mark; L.verts.push_back(u); }
+      }
+    }
+    L.start.push_back(int64_t(e));
+    if (L.verts.size() == e) break;
+    b = e;
+  }
+}
+
+int64_t min_deg_index(const Graph& g, const int64_t* v, size_t cnt) {
+  int64_t best = v[0];
+  for (size_t i = 1; i < cnt; ++i) {
+    int64_t u = v[i];
+    if (g.deg(u) < g.deg(best) || (g.deg(u) == g.deg(best) && u < best)) best = u;
+  }
+  return best;
+}
+
+std::vector<int64_t> partial_rcm(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow) {
+  const int64_t nb = n - n_arrow;
+  Graph g = body_graph(n, colptr, rowidx, nb);
+  std::vector<int64_t> stamp(nb, 0);
+  int64_t mark = 0;
+  std::vector<char> visited(nb, 0);
+  std::vector<int64_t> seq;
+  seq.reserve(nb);
+  Levels comp, lr, lx;
+  std::vector<int64_t> tmp;
+  for (int64_t v = 0; v < nb; ++v) {
+    if (visited[v]) continue;
+    bfs_levels(g, v, stamp, mark, comp);
+    int64_t r = min_deg_index(g, comp.verts.data(), comp.verts.size());
+    bfs_levels(g, r, stamp, mark, lr);
+    while (true) {
+      const int64_t* last = lr.verts.data() + lr.start[lr.depth() - 1];
+      size_t nlast = lr.verts.size() - size_t(lr.start[lr.depth() - 1]);
+      int64_t x = min_deg_index(g, last, nlast);
+      bfs_levels(g, x, stamp, mark, lx);
+      if (lx.depth() > lr.depth()) { r = x; std::swap(lr, lx); }
+      else break;
+    }
+    // Cuthill-McKee from r
+    size_t head = seq.size();
+    seq.push_back(r);
+    visited[r] = 1;
+    while (head < seq.size()) {
+      int64_t u = seq[head++];
+      tmp.clear();
+      for (int64_t a = g.ptr[u]; a < g.ptr[u + 1]; ++a)
+        if (!visited[g.adj[a]]) tmp.push_back(g.adj[a]);
+      std::sort(tmp.begin(), tmp.end(), [&](int64_t x, int64_t y) {
+        return g.deg(x) < g.deg(y) || (g.deg(x) == g.deg(y) && x < y);
+      });
+      for (int64_t w : tmp) { visited[w] = 1; seq.push_back(w); }
+    }
+  }
+  std::reverse(seq.begin(), seq.end());
+  for (int64_t a = nb; a < n; ++a) seq.push_back(a);
+  return seq;
+}
+
+// ---------------------------------------------------------------------------
+// Tile map and tile-level symbolic factorization.  cols[J] = sorted rows I > J
+// of the present lower tiles of column J.  The closure follows the elimination
+// tree: the structure of tile column k (minus its first row p) is merged into
+// column p, which yields the same map as adding every pair of S_k.
+// ---------------------------------------------------------------------------
+std::vector<std::vector<int32_t>> tile_columns(int64_t n, const int64_t* colptr, const int32_t* rowidx,
+                                               const std::vector<int64_t>& iperm, int64_t T, int64_t nt) {
+  // bucket the entries of P A P^T (flipped to the lower triangle) by tile column
+  std::vector<int64_t> cnt(nt + 1, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t q = iperm[j];
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      int64_t p = iperm[rowidx[e]];
+      int64_t r = std::max(p, q), c = std::min(p, q);
+      if (r / T != c / T) ++cnt[c / T + 1];
+    }
+  }
+  for (int64_t J = 0; J < nt; ++J) cnt[J + 1] += cnt[J];
+  std::vector<int32_t> rows(cnt[nt]);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t q = iperm[j];
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      int64_t p = iperm[rowidx[e]];
+      int64_t r = std::max(p, q), c = std::min(p, q);
+      if (r / T != c / T) rows[fill[c / T]++] = int32_t(r / T);
+    }
+  }
+  std::vector<std::vector<int32_t>> cols(nt);
+  std::vector<int64_t> stamp(nt, -1);
+  for (int64_t J = 0; J < nt; ++J) {
+    auto& cj = cols[J];
+    for (int64_t e = cnt[J]; e < cnt[J + 1]; ++e) {
+      int32_t I = rows[e];
+      if (stamp[I] != J) { stamp[I] = J; cj.push_back(I); }
+    }
+    std::sort(cj.begin(), cj.end());
+  }
+  // symbolic closure along the elimination tree
+  std::vector<int32_t> merged;
+  for (int64_t k = 0; k < nt; ++k) {
+    const auto& s = cols[k];
+    if (s.size() < 2) continue;
+    int32_t par = s[0];
+    auto& cp = cols[par];
+    merged.clear();
+    std::set_union(cp.begin(), cp.end(), s.begin() + 1, s.end(), std::back_inserter(merged));
+    cp.swap(merged);
+  }
+  return cols;
+}
+
+int64_t count_tiles(const std::vector<std::vector<int32_t>>& cols) {
+  int64_t c = int64_t(cols.size());
+  for (const auto& v : cols) c += int64_t(v.size());
+  return c;
+}
+
+// Tree split of an accumulation list (Algorithm 3): the first chunks of
+// `chunk` terms become leaves, leaves are summed by nodes of `fanin`
+// children until at most `fanin` remain; the owning task keeps the last
+// chunk and subtracts the remaining tree roots.
+struct TreeNode {
+  int32_t type;        // leaf or combine
+  int32_t scratch;     // output scratch index
+  int64_t pb, pe;      // leaf: range in the pair list
+  std::vector<int32_t> children;  // combine: indices into the node list
+  int64_t release;     // leaf: primary position of the last producer
+  int64_t owner;       // leaf: primary task whose pairs it sums
+};
+
+inline void set_col(DevTask& t, int32_t c) { t.col = c; }
+inline void set_col(SolveTask& t, int32_t c) { t.pad0 = c; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Task graph builder shared by the factorization and the two solve sweeps.
+// Primary tasks come in a fixed order; each has a list of pairs whose
+// producers are earlier primary tasks.  Leaves are emitted right after their
+// last producer, combines right after their last child, so every task's
+// dependencies carry smaller tickets.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Primary {
+  int32_t type, out, diag, col;
+  std::vector<int32_t> pairs;     // 2 per pair
+  std::vector<int64_t> producers; // per pair: max primary position of the two producers
+};
+
+template <class Task>
+void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32_t leaf_type, int32_t comb_type,
+                 std::vector<Task>& tasks, std::vector<int32_t>& pairs, std::vector<int32_t>& parts,
+                 int64_t& nscratch) {
+  const int64_t np = int64_t(prim.size());
+  std::vector<TreeNode> nodes;
+  std::vector<std::vector<int32_t>> roots(np);      // per primary: its top-level tree nodes
+  std::vector<std::vector<int32_t>> by_release(np); // leaves by release position
+  std::vector<int32_t> parent;
+  std::vector<int32_t> pending;
+  std::vector<int64_t> own_begin(np, 0);
+  for (int64_t t = 0; t < np; ++t) {
+    const int64_t npairs = int64_t(prim[t].pairs.size() / 2);
+    if (npairs <= chunk) continue;
+    const int64_t nchunks = (npairs + chunk - 1) / chunk;
+    std::vector<int32_t> level;
+    for (int64_t c = 0; c + 1 < nchunks; ++c) {
+      TreeNode nd;
+      nd.type = leaf_type;
+      nd.scratch = int32_t(nscratch++);
+      nd.pb = c * chunk;
+      nd.pe = (c + 1) * chunk;
+      int64_t rel = 0;
+      for (int64_t q = nd.pb; q < nd.pe; ++q) rel = std::max(rel, prim[t].producers[q]);
+      nd.release = rel;
+      level.push_back(int32_t(nodes.size()));
+      by_release[rel].push_back(int32_t(nodes.size()));
+      nd.owner = t;
+      nodes.push_back(nd);
+      parent.push_back(-1);
+      pending.push_back(0);
+    }
+    own_begin[t] = (nchunks - 1) * chunk;
+    while (int64_t(level.size()) > fanin) {
+      std::vector<int32_t> next;
+      for (size_t g = 0; g < level.size(); g += size_t(fanin)) {
+        TreeNode nd;
+        nd.type = comb_type;
+        nd.scratch = int32_t(nscratch++);
+        nd.pb = nd.pe = 0;
+        nd.release = -1;
+        nd.owner = t;
+        size_t e = std::min(level.size(), g + size_t(fanin));
+        int32_t id = int32_t(nodes.size());
+        for (size_t q = g; q < e; ++q) { nd.children.push_back(level[q]); parent[level[q]] = id; }
+        nodes.push_back(nd);
+        parent.push_back(-1);
+        pending.push_back(int32_t(e - g));
+        next.push_back(id);
+      }
+      level.swap(next);
+    }
+    roots[t] = level;
+  }
+  // emission
+  tasks.clear();
+  pairs.clear();
+  parts.clear();
+  std::vector<int64_t> ticket_of_node(nodes.size(), -1);
+  std::vector<int32_t> stack;
+  auto emit_node = [&](int32_t id) {
+    TreeNode& nd = nodes[id];
+    Task tk{};
+    tk.type = nd.type;
+    tk.out = nd.scratch;
+    tk.diag = -1;
+    if (nd.type == leaf_type) {
+      const Primary& pr = prim[nd.owner];
+      tk.pb = int32_t(pairs.size() / 2);
+      pairs.insert(pairs.end(), pr.pairs.begin() + 2 * nd.pb, pr.pairs.begin() + 2 * nd.pe);
+      tk.pe = int32_t(pairs.size() / 2);
+      tk.qb = tk.qe = int32_t(parts.size());
+    } else {
+      tk.pb = tk.pe = int32_t(pairs.size() / 2);
+      tk.qb = int32_t(parts.size());
+      for (int32_t c : nd.children) parts.push_back(nodes[c].scratch);
+      tk.qe = int32_t(parts.size());
+    }
+    ticket_of_node[id] = int64_t(tasks.size());
+    tasks.push_back(tk);
+  };
+  for (int64_t t = 0; t < np; ++t) {
+    Primary& pr = prim[t];
+    Task tk{};
+    tk.type = pr.type;
+    tk.out = pr.out;
+    tk.diag = pr.diag;
+    tk.pb = int32_t(pairs.size() / 2);
+    pairs.insert(pairs.end(), pr.pairs.begin() + 2 * own_begin[t], pr.pairs.end());
+    tk.pe = int32_t(pairs.size() / 2);
+    tk.qb = int32_t(parts.size());
+    for (int32_t r : roots[t]) {
+      if (ticket_of_node[r] < 0) throw std::logic_error("tree root emitted after its owner");
+      parts.push_back(nodes[r].scratch);
+    }
+    tk.qe = int32_t(parts.size());
+    set_col(tk, pr.col);
+    tasks.push_back(tk);
+    // leaves released by this primary, then any combine that became complete
+    for (int32_t leaf : by_release[t]) {
+      stack.assign(1, leaf);
+      while (!stack.empty()) {
+        int32_t id = stack.back();
+        stack.pop_back();
+        emit_node(id);
+        int32_t p = parent[id];
+        if (p >= 0 && --pending[p] == 0) stack.push_back(p);
+      }
+    }
+  }
+  for (size_t i = 0; i < nodes.size(); ++i)
+    if (ticket_of_node[i] < 0) throw std::logic_error("tree node never emitted");
+}
+
+}  // namespace
+
+namespace {
+
+bool validate(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow, std::string* err) {
+  if (n < 1 || n > (int64_t(1) << 31) - 1) { *err = "n must be in [1, 2^31)"; return false; }
+  if (!colptr || !rowidx) { *err = "null colptr/rowidx"; return false; }
+  if (n_arrow < 0 || n_arrow > n) { *err = "n_arrow must be in [0, n]"; return false; }
+  if (colptr[0] != 0) { *err = "colptr[0] != 0"; return false; }
+  for (int64_t j = 0; j < n; ++j) {
+    if (colptr[j + 1] < colptr[j]) { *err = "colptr not nondecreasing at column " + std::to_string(j); return false; }
+    if (colptr[j + 1] == colptr[j] || rowidx[colptr[j]] != j) {
+      *err = "missing diagonal (or upper-triangle entry) in column " + std::to_string(j);
+      return false;
+    }
+    for (int64_t e = colptr[j] + 1; e < colptr[j + 1]; ++e) {
+      if (rowidx[e] <= rowidx[e - 1] || rowidx[e] >= n) {
+        *err = "rows not strictly ascending / out of range in column " + std::to_string(j);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+std::vector<int64_t> invert(const std::vector<int64_t>& perm) {
+  std::vector<int64_t> inv(perm.size());
+  for (size_t i = 0; i < perm.size(); ++i) inv[perm[i]] = int64_t(i);
+  return inv;
+}
+
+// Ticket-order check: the producer of every tile (or block) a task reads must
+// have a smaller ticket.  For solve graphs the second member of a pair is a
+// block index; for the factorization both members are sub-tile indices.
+template <class Task>
+bool check_order(const std::vector<Task>& tasks, const std::vector<int32_t>& pairs, const std::vector<int32_t>& parts,
+                 int64_t nout, int64_t nscratch, int32_t leaf, int32_t comb, bool solve, std::string* err) {
+  std::vector<int64_t> tout(nout, -1), tscr(nscratch, -1);
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    const Task& tk = tasks[t];
+    if (tk.type == leaf || tk.type == comb) {
+      if (tk.out < 0 || tk.out >= nscratch || tscr[tk.out] >= 0) { *err = "internal: bad scratch output"; return false; }
+      tscr[tk.out] = int64_t(t);
+    } else {
+      if (tk.out < 0 || tk.out >= nout || tout[tk.out] >= 0) { *err = "internal: bad task output"; return false; }
+      tout[tk.out] = int64_t(t);
+    }
+  }
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    const Task& tk = tasks[t];
+    for (int32_t q = tk.pb; q < tk.pe; ++q) {
+      const int64_t a = pairs[2 * size_t(q)], b = pairs[2 * size_t(q) + 1];
+      const int64_t ta = solve ? -2 : tout[a];
+      const int64_t tb = tout[b];
+      if ((!solve && (ta < 0 || ta >= int64_t(t))) || tb < 0 || tb >= int64_t(t)) {
+        *err = "internal: task " + std::to_string(t) + " reads a tile produced later";
+        return false;
+      }
+    }
+    for (int32_t q = tk.qb; q < tk.qe; ++q) {
+      const int64_t ts = tscr[parts[q]];
+      if (ts < 0 || ts >= int64_t(t)) { *err = "internal: partial produced later"; return false; }
+    }
+  }
+  return true;
+}
+
+struct SubEntry {
+  int32_t idx;  // sub-row (in a column list) or sub-column (in a row list)
+  int32_t sub;  // sub-tile index
+};
+
+}  // namespace
+
+stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                         const stiles_opts& opts_in, stiles_plan* p, std::string* err) {
+  stiles_opts o = opts_in;
+  if (o.tile < 1) { *err = "tile must be >= 1"; return STILES_ERR_INVALID; }
+  if (o.ordering < 0 || o.ordering > 2) { *err = "unknown ordering"; return STILES_ERR_INVALID; }
+  if (o.precision < 0 || o.precision > 2) { *err = "unknown precision"; return STILES_ERR_INVALID; }
+  if (o.tree_chunk <= 0) o.tree_chunk = 32;
+  if (o.tree_fanin <= 1) o.tree_fanin = 16;
+  if (o.max_refine <= 0) o.max_refine = 20;
+  if (!(o.refine_tol > 0)) o.refine_tol = 1e-10;
+  if (o.spin_limit <= 0) o.spin_limit = int64_t(1) << 24;
+  if (o.block != 0 && o.block != 16 && o.block != 32 && o.block != 64) {
+    *err = "block must be 0, 16, 32 or 64";
+    return STILES_ERR_INVALID;
+  }
+  if (!validate(n, colptr, rowidx, n_arrow, err)) return STILES_ERR_INVALID;
+  const int64_t nnz = colptr[n];
+  const int64_t T = o.tile;
+  p->opts = o;
+  p->n = n;
+  p->n_arrow = n_arrow;
+  p->nnz = nnz;
+  p->T = int32_t(T);
+  p->colptr.assign(colptr, colptr + n + 1);
+  p->rowidx.assign(rowidx, rowidx + nnz);
+  const int64_t nt = (n + T - 1) / T;
+  p->nt = nt;
+
+  // ordering (Section III.A) and tile map + symbolic closure per candidate
+  std::vector<int64_t> ident(n);
+  std::iota(ident.begin(), ident.end(), 0);
+  std::vector<std::vector<int32_t>> best_cols;
+  if (o.ordering == STILES_ORDER_NONE || o.ordering == STILES_ORDER_AUTO) {
+    best_cols = tile_columns(n, colptr, rowidx, ident, T, nt);
+    p->perm = ident;
+    p->ordering_used = STILES_ORDER_NONE;
+  }
+  if (o.ordering == STILES_ORDER_RCM || o.ordering == STILES_ORDER_AUTO) {
+    std::vector<int64_t> perm = partial_rcm(n, colptr, rowidx, n_arrow);
+    std::vector<int64_t> inv = invert(perm);
+    auto cols = tile_columns(n, colptr, rowidx, inv, T, nt);
+    if (o.ordering == STILES_ORDER_RCM || count_tiles(cols) < count_tiles(best_cols)) {
+      best_cols.swap(cols);
+      p->perm.swap(perm);
+      p->ordering_used = STILES_ORDER_RCM;
+    }
+  }
+  p->iperm = invert(p->perm);
+
+  // tile-CSC of L, diagonal first
+  p->tcolptr.assign(nt + 1, 0);
+  p->trowidx.clear();
+  for (int64_t k = 0; k < nt; ++k) {
+    p->trowidx.push_back(int32_t(k));
+    p->trowidx.insert(p->trowidx.end(), best_cols[k].begin(), best_cols[k].end());
+    p->tcolptr[k + 1] = int64_t(p->trowidx.size());
+  }
+  p->nnzt = int64_t(p->trowidx.size());
+  best_cols.clear();
+  best_cols.shrink_to_fit();
+
+  // exact task flops at tile size T (actual ragged dimensions)
+  auto dim = [&](int64_t I) { return std::min<int64_t>(T, n - I * T); };
+  std::vector<std::vector<int32_t>> trows(nt);
+  for (int64_t k = 0; k < nt; ++k)
+    for (int64_t e = p->tcolptr[k]; e < p->tcolptr[k + 1]; ++e) trows[p->trowidx[e]].push_back(int32_t(k));
+  p->flops_potrf = p->flops_syrk = p->flops_gemm = p->flops_trsm = 0;
+  for (int64_t k = 0; k < nt; ++k) {
+    const int64_t b = dim(k);
+    p->flops_potrf += b * (b + 1) * (2 * b + 1) / 6;
+    for (int32_t nn : trows[k])
+      if (nn < k) p->flops_syrk += dim(nn) * b * (b + 1);
+    for (int64_t e = p->tcolptr[k] + 1; e < p->tcolptr[k + 1]; ++e) {
+      const int64_t m = p->trowidx[e];
+      p->flops_trsm += dim(m) * b * b;
+      const auto& rm = trows[m];
+      const auto& rk = trows[k];
+      size_t a = 0, c = 0;
+      while (a < rm.size() && c < rk.size()) {
+        if (rm[a] < rk[c]) ++a;
+        else if (rk[c] < rm[a]) ++c;
+        else {
+          if (rm[a] < k) p->flops_gemm += 2 * dim(m) * b * dim(rm[a]);
+          ++a;
+          ++c;
+        }
+      }
+    }
+  }
+  trows.clear();
+  trows.shrink_to_fit();
+
+  // device sub-tile size
+  int64_t B = o.block;
+  if (B == 0) B = (T % 32 == 0) ? 32 : (T % 16 == 0 ? 16 : 0);
+  p->executable = (B == 16 || B == 32 || B == 64) && (T % B == 0);
+  if (!p->executable) {
+    p->B = int32_t(B);
+    p->R = 0;
+    return STILES_OK;
+  }
+  const int64_t R = T / B;
+  p->B = int32_t(B);
+  p->R = int32_t(R);
+  const int64_t nsb = (n + B - 1) / B;
+  p->nsb = nsb;
+  p->nsub = p->nnzt * R * R;
+  if (p->nsub >= (int64_t(1) << 31)) { *err = "too many sub-tiles"; return STILES_ERR_UNSUPPORTED; }
+
+  auto tile_index = [&](int64_t I, int64_t J) -> int64_t {
+    if (I == J) return p->tcolptr[J];
+    const int32_t* b0 = p->trowidx.data() + p->tcolptr[J] + 1;
+    const int32_t* e0 = p->trowidx.data() + p->tcolptr[J + 1];
+    const int32_t* it = std::lower_bound(b0, e0, int32_t(I));
+    if (it == e0 || *it != I) return -1;
+    return int64_t(it - p->trowidx.data());
+  };
+
+  // present lower sub-tiles by sub-column and by sub-row (ascending)
+  std::vector<std::vector<SubEntry>> scol(nsb), srow(nsb);
+  for (int64_t J = 0; J < nt; ++J)
+    for (int64_t e = p->tcolptr[J]; e < p->tcolptr[J + 1]; ++e) {
+      const int64_t I = p->trowidx[e];
+      for (int64_t q = 0; q < R; ++q) {
+        const int64_t jj = J * R + q;
+        if (jj >= nsb) break;
+        for (int64_t pp = 0; pp < R; ++pp) {
+          const int64_t ii = I * R + pp;
+          if (ii >= nsb) break;
+          if (ii < jj) continue;
+          const int32_t s = int32_t(e * R * R + q * R + pp);
+          scol[jj].push_back({int32_t(ii), s});
+          srow[ii].push_back({int32_t(jj), s});
+        }
+      }
+    }
+  p->diag_sub.assign(nsb, -1);
+  for (int64_t k = 0; k < nsb; ++k) p->diag_sub[k] = scol[k].front().sub;
+
+  // scatter map of every input entry into the tile buffer
+  p->scatter.resize(nnz);
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t q = p->iperm[j];
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      const int64_t pr = p->iperm[rowidx[e]];
+      const int64_t r = std::max(pr, q), c = std::min(pr, q);
+      const int64_t t = tile_index(r / T, c / T);
+      if (t < 0) { *err = "internal: entry outside the tile map"; return STILES_ERR_INVALID; }
+      const int64_t s = t * R * R + ((c % T) / B) * R + ((r % T) / B);
+      p->scatter[e] = s * B * B + (c % B) * B + (r % B);
+    }
+  }
+  p->pad.clear();
+  for (int64_t g = n; g < nsb * B; ++g)
+    p->pad.push_back(int64_t(p->diag_sub[nsb - 1]) * B * B + (g % B) * B + (g % B));
+
+  // factorization task graph: column-major primary tasks, DIAG then OFF
+  std::vector<Primary> prim;
+  prim.reserve(size_t(nsb) * 4);
+  std::vector<int64_t> pos(p->nsub, -1);
+  for (int64_t k = 0; k < nsb; ++k) {
+    const auto& rk = srow[k];
+    {
+      Primary d;
+      d.type = TASK_DIAG;
+      d.out = p->diag_sub[k];
+      d.diag = -1;
+      d.col = int32_t(k);
+      for (const SubEntry& en : rk) {
+        if (en.idx >= k) break;
+        d.pairs.push_back(en.sub);
+        d.pairs.push_back(en.sub);
+        d.producers.push_back(pos[en.sub]);
+      }
+      pos[d.out] = int64_t(prim.size());
+      prim.push_back(std::move(d));
+    }
+    for (size_t e = 1; e < scol[k].size(); ++e) {
+      const int64_t i = scol[k][e].idx;
+      Primary o2;
+      o2.type = TASK_OFF;
+      o2.out = scol[k][e].sub;
+      o2.diag = p->diag_sub[k];
+      o2.col = int32_t(k);
+      const auto& ri = srow[i];
+      size_t a = 0, c = 0;
+      while (a < ri.size() && c < rk.size()) {
+        if (ri[a].idx >= k || rk[c].idx >= k) break;
+        if (ri[a].idx < rk[c].idx) ++a;
+        else if (rk[c].idx < ri[a].idx) ++c;
+        else {
+          o2.pairs.push_back(ri[a].sub);
+          o2.pairs.push_back(rk[c].sub);
+          o2.producers.push_back(std::max(pos[ri[a].sub], pos[rk[c].sub]));
+          ++a;
+          ++c;
+        }
+      }
+      pos[o2.out] = int64_t(prim.size());
+      prim.push_back(std::move(o2));
+    }
+  }
+  for (const auto& pr : prim)
+    for (int64_t q : pr.producers)
+      if (q < 0) { *err = "internal: producer missing"; return STILES_ERR_INVALID; }
+  try {
+    build_graph(prim, o.tree_chunk, o.tree_fanin, TASK_PARTIAL, TASK_COMBINE, p->graph.tasks, p->graph.pairs,
+                p->graph.parts, p->graph.nscratch);
+  } catch (const std::exception& ex) {
+    *err = ex.what();
+    return STILES_ERR_INVALID;
+  }
+  prim.clear();
+
+  // forward sweep: one task per sub-row, ascending
+  {
+    std::vector<Primary> fp(nsb);
+    for (int64_t k = 0; k < nsb; ++k) {
+      fp[k].type = SOLVE_FINAL;
+      fp[k].out = int32_t(k);
+      fp[k].diag = p->diag_sub[k];
+      fp[k].col = int32_t(k);
+      for (const SubEntry& en : srow[k]) {
+        if (en.idx >= k) break;
+        fp[k].pairs.push_back(en.sub);
+        fp[k].pairs.push_back(en.idx);
+        fp[k].producers.push_back(en.idx);
+      }
+    }
+    build_graph(fp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->fwd.tasks, p->fwd.pairs,
+                p->fwd.parts, p->fwd.nscratch);
+  }
+  // backward sweep: one task per sub-column, descending
+  {
+    std::vector<Primary> bp(nsb);
+    for (int64_t q = 0; q < nsb; ++q) {
+      const int64_t k = nsb - 1 - q;
+      bp[q].type = SOLVE_FINAL;
+      bp[q].out = int32_t(k);
+      bp[q].diag = p->diag_sub[k];
+      bp[q].col = int32_t(k);
+      for (size_t e = 1; e < scol[k].size(); ++e) {
+        bp[q].pairs.push_back(scol[k][e].sub);
+        bp[q].pairs.push_back(scol[k][e].idx);
+        bp[q].producers.push_back(nsb - 1 - scol[k][e].idx);
+      }
+    }
+    build_graph(bp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->bwd.tasks, p->bwd.pairs,
+                p->bwd.parts, p->bwd.nscratch);
+  }
+  // every dependency must carry a smaller ticket, or the persistent kernels could wait forever
+  if (!check_order(p->graph.tasks, p->graph.pairs, p->graph.parts, p->nsub, p->graph.nscratch, TASK_PARTIAL,
+                   TASK_COMBINE, false, err) ||
+      !check_order(p->fwd.tasks, p->fwd.pairs, p->fwd.parts, nsb, p->fwd.nscratch, SOLVE_PARTIAL, SOLVE_COMBINE,
+                   true, err) ||
+      !check_order(p->bwd.tasks, p->bwd.pairs, p->bwd.parts, nsb, p->bwd.nscratch, SOLVE_PARTIAL, SOLVE_COMBINE,
+                   true, err))
+    return STILES_ERR_INVALID;
+  return STILES_OK;
+}
+
+}  // namespace stiles

@@ -1,0 +1,700 @@
+// C ABI of libstiles.so: plan/factor lifetime, device uploads and launches.
+// Declarations and argument conventions are in include/stiles.h.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "aux_kernels.cuh"
+#include "factor_f64.cuh"
+#include "plan.h"
+#include "solve_f64.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};  // kernels launched by this library (all threads)
+
+inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+stiles_status fail(stiles_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (expr);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,            \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                               \
+  } while (0)
+
+template <class T>
+cudaError_t upload(T** dptr, const std::vector<T>& v) {
+  *dptr = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, 148 * 32)));
+}
+
+}  // namespace
+
+namespace stiles {
+
+struct DevGraph {
+  DevTask* tasks = nullptr;
+  SolveTask* stasks = nullptr;
+  int32_t* pairs = nullptr;
+  int32_t* parts = nullptr;
+  int ntasks = 0;
+};
+
+struct DevPlan {
+  int device = -1;
+  int64_t* scatter = nullptr;
+  int64_t* pad = nullptr;
+  int64_t* perm = nullptr;
+  int32_t* diag_sub = nullptr;
+  int64_t* colptr = nullptr;
+  int32_t* rowidx = nullptr;
+  DevGraph fac, fwd, bwd;
+  int grid_factor = 0, grid_solve = 0;
+};
+
+}  // namespace stiles
+
+struct stiles_factor {
+  const stiles_plan* plan = nullptr;
+  int device = -1;
+  double* values = nullptr;   // FP64 copy of A's values (CSC order) for residuals
+  double* tiles = nullptr;
+  double* scratch = nullptr;
+  double* invdiag = nullptr;
+  int* flags = nullptr;       // nsub + nscratch
+  stiles::dev::Ctl* ctl = nullptr;  // [0] factor, [1] forward, [2] backward
+  double* logdet_part = nullptr;    // LOGDET_BLOCKS + 1
+  // solve workspace (grown on demand)
+  double* Y = nullptr;
+  double* sscratch = nullptr;
+  int* sflags = nullptr;
+  int64_t solve_nr = 0;
+  double* bstage = nullptr;   // host-input staging (n * nrhs)
+  double* xstage = nullptr;
+  double* ywork = nullptr;    // residual work n * nr
+  double* norms = nullptr;    // 2 * SOLVE_MAXR
+  int64_t stage_elems = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, persistent kernel start / end
+  long long* trace[3] = {nullptr, nullptr, nullptr};  // per-ticket stamps: factor, forward, backward
+  bool pending = false;
+};
+
+namespace {
+
+using namespace stiles;
+
+void free_graph(DevGraph& g) {
+  cudaFree(g.tasks);
+  cudaFree(g.stasks);
+  cudaFree(g.pairs);
+  cudaFree(g.parts);
+  g = DevGraph{};
+}
+
+void free_dev_plan(stiles_plan* p) {
+  if (!p->dev) return;
+  DevPlan* d = p->dev;
+  cudaFree(d->scatter);
+  cudaFree(d->pad);
+  cudaFree(d->perm);
+  cudaFree(d->diag_sub);
+  cudaFree(d->colptr);
+  cudaFree(d->rowidx);
+  free_graph(d->fac);
+  free_graph(d->fwd);
+  free_graph(d->bwd);
+  delete d;
+  p->dev = nullptr;
+}
+
+template <int B>
+cudaError_t factor_occupancy(int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(dev::factor_f64_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(dev::FactorCfg<B>::SMEM));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::factor_f64_kernel<B>, 128, dev::FactorCfg<B>::SMEM);
+}
+
+template <int B>
+cudaError_t solve_occupancy(int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(dev::SolveCfg<B>::SMEM));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(dev::SolveCfg<B>::SMEM));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::solve_f64_kernel<B, false>, 128,
+                                                       dev::SolveCfg<B>::SMEM);
+}
+
+stiles_status ensure_dev_plan(const stiles_plan* cp) {
+  stiles_plan* p = const_cast<stiles_plan*>(cp);
+  int device = 0;
+  CUDA_TRY(cudaGetDevice(&device));
+  if (p->dev) {
+    if (p->dev->device != device) return fail(STILES_ERR_INVALID, "plan was uploaded to another device");
+    return STILES_OK;
+  }
+  if (!p->executable) return fail(STILES_ERR_UNSUPPORTED, "tile size must be a multiple of 16 to factorize");
+  DevPlan* d = new (std::nothrow) DevPlan();
+  if (!d) return fail(STILES_ERR_NOMEM, "host allocation");
+  p->dev = d;
+  d->device = device;
+  auto chk = [&](cudaError_t e) { return e == cudaSuccess; };
+  bool ok = chk(upload(&d->scatter, p->scatter)) && chk(upload(&d->pad, p->pad)) && chk(upload(&d->perm, p->perm)) &&
+            chk(upload(&d->diag_sub, p->diag_sub)) && chk(upload(&d->colptr, p->colptr)) &&
+            chk(upload(&d->rowidx, p->rowidx)) && chk(upload(&d->fac.tasks, p->graph.tasks)) &&
+            chk(upload(&d->fac.pairs, p->graph.pairs)) && chk(upload(&d->fac.parts, p->graph.parts)) &&
+            chk(upload(&d->fwd.stasks, p->fwd.tasks)) && chk(upload(&d->fwd.pairs, p->fwd.pairs)) &&
+            chk(upload(&d->fwd.parts, p->fwd.parts)) && chk(upload(&d->bwd.stasks, p->bwd.tasks)) &&
+            chk(upload(&d->bwd.pairs, p->bwd.pairs)) && chk(upload(&d->bwd.parts, p->bwd.parts));
+  if (!ok) {
+    cudaError_t e = cudaGetLastError();
+    free_dev_plan(p);
+    return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                std::string("plan upload: ") + cudaGetErrorString(e));
+  }
+  d->fac.ntasks = int(p->graph.tasks.size());
+  d->fwd.ntasks = int(p->fwd.tasks.size());
+  d->bwd.ntasks = int(p->bwd.tasks.size());
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  int fb = 0, sb = 0;
+  cudaError_t e = cudaSuccess;
+  switch (p->B) {
+    case 16: e = factor_occupancy<16>(&fb); if (e == cudaSuccess) e = solve_occupancy<16>(&sb); break;
+    case 32: e = factor_occupancy<32>(&fb); if (e == cudaSuccess) e = solve_occupancy<32>(&sb); break;
+    case 64: e = factor_occupancy<64>(&fb); if (e == cudaSuccess) e = solve_occupancy<64>(&sb); break;
+    default: return fail(STILES_ERR_UNSUPPORTED, "block size");
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+  if (fb < 1 || sb < 1) return fail(STILES_ERR_UNSUPPORTED, "kernel does not fit on an SM");
+  d->grid_factor = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(fb) * sms, d->fac.ntasks)));
+  d->grid_solve = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sb) * sms, std::max(d->fwd.ntasks, d->bwd.ntasks))));
+  return STILES_OK;
+}
+
+void free_factor(stiles_factor* f) {
+  if (!f) return;
+  cudaFree(f->values);
+  cudaFree(f->tiles);
+  cudaFree(f->scratch);
+  cudaFree(f->invdiag);
+  cudaFree(f->flags);
+  cudaFree(f->ctl);
+  cudaFree(f->logdet_part);
+  cudaFree(f->Y);
+  cudaFree(f->sscratch);
+  cudaFree(f->sflags);
+  cudaFree(f->bstage);
+  cudaFree(f->xstage);
+  cudaFree(f->ywork);
+  cudaFree(f->norms);
+  if (f->done) cudaEventDestroy(f->done);
+  for (cudaEvent_t e : f->ev)
+    if (e) cudaEventDestroy(e);
+  for (long long* t : f->trace) cudaFree(t);
+  delete f;
+}
+
+stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
+  stiles_factor* f = new (std::nothrow) stiles_factor();
+  if (!f) return fail(STILES_ERR_NOMEM, "host allocation");
+  f->plan = p;
+  cudaGetDevice(&f->device);
+  const size_t tile = size_t(p->B) * p->B;
+  const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
+  cudaError_t e = cudaMalloc(&f->values, size_t(p->nnz) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
+  if (e == cudaSuccess) e = cudaMalloc(&f->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f->norms, 2 * dev::SOLVE_MAXR * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&f->ev[i]);
+  if (e != cudaSuccess) {
+    free_factor(f);
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                std::string("factor allocation: ") + cudaGetErrorString(e));
+  }
+  *out = f;
+  return STILES_OK;
+}
+
+template <int B>
+cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
+  dev::FactorArgs a;
+  a.tiles = f->tiles;
+  a.scratch = f->scratch;
+  a.invdiag = f->invdiag;
+  a.tasks = p->dev->fac.tasks;
+  a.ntasks = p->dev->fac.ntasks;
+  a.pairs = p->dev->fac.pairs;
+  a.parts = p->dev->fac.parts;
+  a.flags = f->flags;
+  a.sflags = f->flags + p->nsub;
+  a.ctl = f->ctl;
+  a.spin_limit = p->opts.spin_limit;
+  a.trace = f->trace[0];
+  dev::factor_f64_kernel<B><<<p->dev->grid_factor, 128, dev::FactorCfg<B>::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr) {
+  dev::SolveArgs a;
+  a.tiles = f->tiles;
+  a.invdiag = f->invdiag;
+  a.Y = f->Y;
+  a.spin_limit = p->opts.spin_limit;
+  a.nr = nr;
+  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1);
+  // forward
+  a.scratch = f->sscratch;
+  a.tasks = p->dev->fwd.stasks;
+  a.ntasks = p->dev->fwd.ntasks;
+  a.pairs = p->dev->fwd.pairs;
+  a.parts = p->dev->fwd.parts;
+  a.flags = f->sflags;
+  a.sflags = f->sflags + p->nsb;
+  a.ctl = f->ctl + 1;
+  a.trace = f->trace[1];
+  dev::solve_f64_kernel<B, false><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // backward
+  a.scratch = f->sscratch + size_t(nf) * B * dev::SOLVE_MAXR;
+  a.tasks = p->dev->bwd.stasks;
+  a.ntasks = p->dev->bwd.ntasks;
+  a.pairs = p->dev->bwd.pairs;
+  a.parts = p->dev->bwd.parts;
+  a.flags = f->sflags + p->nsb + nf;
+  a.sflags = f->sflags + 2 * p->nsb + nf;
+  a.ctl = f->ctl + 2;
+  a.trace = f->trace[2];
+  dev::solve_f64_kernel<B, true><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+stiles_status read_ctl(stiles_factor* f, int idx, int64_t* info) {
+  dev::Ctl c;
+  CUDA_TRY(cudaMemcpy(&c, f->ctl + idx, sizeof(c), cudaMemcpyDeviceToHost));
+  if (info) *info = (c.info == ~0ull) ? 0 : int64_t(c.info);
+  if (c.status != 0) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "device wait timed out (launch %d, ticket %lld)", idx, c.where);
+    return fail(STILES_ERR_TIMEOUT, buf);
+  }
+  if (c.info != ~0ull) return fail(STILES_ERR_NOT_SPD, "matrix is not positive definite");
+  return STILES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stiles_default_opts(stiles_opts* opts) {
+  if (opts) stiles::default_opts(opts);
+}
+
+const char* stiles_last_error(void) { return g_last_error.c_str(); }
+
+const char* stiles_strerror(stiles_status s) {
+  switch (s) {
+    case STILES_OK: return "ok";
+    case STILES_ERR_INVALID: return "invalid argument or input";
+    case STILES_ERR_NOT_SPD: return "matrix is not positive definite";
+    case STILES_ERR_NOMEM: return "out of memory";
+    case STILES_ERR_CUDA: return "CUDA error";
+    case STILES_ERR_TIMEOUT: return "device wait timed out";
+    case STILES_ERR_NOT_CONVERGED: return "iterative refinement did not converge";
+    case STILES_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+stiles_status stiles_analyze(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                             const stiles_opts* opts, stiles_plan** out) {
+  if (!out) return fail(STILES_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  stiles_opts o;
+  if (opts) o = *opts;
+  else stiles::default_opts(&o);
+  stiles_plan* p = new (std::nothrow) stiles_plan();
+  if (!p) return fail(STILES_ERR_NOMEM, "host allocation");
+  std::string err;
+  stiles_status s;
+  try {
+    s = stiles::build_plan(n, colptr, rowidx, n_arrow, o, p, &err);
+  } catch (const std::bad_alloc&) {
+    s = STILES_ERR_NOMEM;
+    err = "host allocation during analysis";
+  } catch (const std::exception& ex) {
+    s = STILES_ERR_INVALID;
+    err = ex.what();
+  }
+  if (s != STILES_OK) {
+    delete p;
+    return fail(s, err);
+  }
+  *out = p;
+  return STILES_OK;
+}
+
+stiles_status stiles_plan_get_info(const stiles_plan* p, stiles_plan_info* info) {
+  if (!p || !info) return fail(STILES_ERR_INVALID, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n = p->n;
+  info->n_arrow = p->n_arrow;
+  info->nnz = p->nnz;
+  info->tile = p->T;
+  info->nt = p->nt;
+  info->nnzt = p->nnzt;
+  info->block = p->executable ? p->B : 0;
+  info->nsub = p->nsub;
+  info->ntasks = int64_t(p->graph.tasks.size());
+  info->npairs = int64_t(p->graph.pairs.size() / 2);
+  info->nscratch = p->graph.nscratch;
+  info->flops_potrf = p->flops_potrf;
+  info->flops_syrk = p->flops_syrk;
+  info->flops_gemm = p->flops_gemm;
+  info->flops_trsm = p->flops_trsm;
+  info->flops_total = p->flops_potrf + p->flops_syrk + p->flops_gemm + p->flops_trsm;
+  info->factor_bytes = p->nsub * int64_t(p->B) * p->B * int64_t(sizeof(double));
+  info->ordering_used = p->ordering_used;
+  return STILES_OK;
+}
+
+stiles_status stiles_plan_perm(const stiles_plan* p, int64_t* perm) {
+  if (!p || !perm) return fail(STILES_ERR_INVALID, "null argument");
+  std::memcpy(perm, p->perm.data(), p->perm.size() * sizeof(int64_t));
+  return STILES_OK;
+}
+
+stiles_status stiles_plan_tilemap(const stiles_plan* p, int64_t* tcolptr, int32_t* trowidx) {
+  if (!p) return fail(STILES_ERR_INVALID, "null plan");
+  if (tcolptr) std::memcpy(tcolptr, p->tcolptr.data(), p->tcolptr.size() * sizeof(int64_t));
+  if (trowidx) std::memcpy(trowidx, p->trowidx.data(), p->trowidx.size() * sizeof(int32_t));
+  return STILES_OK;
+}
+
+void stiles_plan_destroy(stiles_plan* p) {
+  if (!p) return;
+  free_dev_plan(p);
+  delete p;
+}
+
+void stiles_factor_destroy(stiles_factor* f) { free_factor(f); }
+
+stiles_status stiles_factorize_async(const stiles_plan* p, const double* values, void* stream, stiles_factor** inout) {
+  if (!p || !values || !inout) return fail(STILES_ERR_INVALID, "null argument");
+  if (p->opts.precision != STILES_PREC_F64)
+    return fail(STILES_ERR_UNSUPPORTED, "this entry point factorizes in FP64 only");
+  stiles_status s = ensure_dev_plan(p);
+  if (s != STILES_OK) return s;
+  stiles_factor* f = *inout;
+  if (f && f->plan != p) return fail(STILES_ERR_INVALID, "factor belongs to another plan");
+  if (!f) {
+    s = alloc_factor(p, &f);
+    if (s != STILES_OK) return s;
+    *inout = f;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  f->stream = st;
+  const size_t tile = size_t(p->B) * p->B;
+  const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
+  CUDA_TRY(cudaEventRecord(f->ev[0], st));
+  CUDA_TRY(cudaMemcpyAsync(f->values, values, size_t(p->nnz) * sizeof(double), cudaMemcpyDefault, st));
+  CUDA_TRY(cudaMemsetAsync(f->tiles, 0, size_t(p->nsub) * tile * sizeof(double), st));
+  dev::scatter_kernel<<<grid_for(p->nnz, 256), 256, 0, st>>>(f->tiles, f->values, p->dev->scatter, p->nnz);
+  CUDA_TRY(cudaGetLastError());
+  if (!p->pad.empty()) {
+    dev::set_ones_kernel<<<1, 128, 0, st>>>(f->tiles, p->dev->pad, int64_t(p->pad.size()));
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaMemsetAsync(f->flags, 0, size_t(p->nsub + nscr) * sizeof(int), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl, 1);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(p->pad.empty() ? 2 : 3);
+  CUDA_TRY(cudaEventRecord(f->ev[1], st));
+  cudaError_t e;
+  switch (p->B) {
+    case 16: e = launch_factor<16>(p, f, st); break;
+    case 32: e = launch_factor<32>(p, f, st); break;
+    default: e = launch_factor<64>(p, f, st); break;
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(e));
+  count_launch();
+  CUDA_TRY(cudaEventRecord(f->ev[2], st));
+  CUDA_TRY(cudaEventRecord(f->done, st));
+  f->pending = true;
+  return STILES_OK;
+}
+
+stiles_status stiles_factor_wait(stiles_factor* f, int64_t* info) {
+  if (!f) return fail(STILES_ERR_INVALID, "null factor");
+  if (info) *info = 0;
+  CUDA_TRY(cudaEventSynchronize(f->done));
+  f->pending = false;
+  return read_ctl(f, 0, info);
+}
+
+stiles_status stiles_factorize(const stiles_plan* p, const double* values, void* stream, stiles_factor** inout,
+                               int64_t* info) {
+  if (info) *info = 0;
+  stiles_status s = stiles_factorize_async(p, values, stream, inout);
+  if (s != STILES_OK) return s;
+  return stiles_factor_wait(*inout, info);
+}
+
+stiles_status stiles_logdet(const stiles_factor* cf, double* out) {
+  if (!cf || !out) return fail(STILES_ERR_INVALID, "null argument");
+  stiles_factor* f = const_cast<stiles_factor*>(cf);
+  const stiles_plan* p = f->plan;
+  cudaStream_t st = f->stream;
+  dev::logdet_pass1<<<dev::LOGDET_BLOCKS, dev::LOGDET_THREADS, 0, st>>>(f->tiles, p->dev->diag_sub, p->n, p->B,
+                                                                        f->logdet_part);
+  CUDA_TRY(cudaGetLastError());
+  dev::logdet_pass2<<<1, 32, 0, st>>>(f->logdet_part, dev::LOGDET_BLOCKS, f->logdet_part + dev::LOGDET_BLOCKS);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(2);
+  CUDA_TRY(cudaMemcpyAsync(out, f->logdet_part + dev::LOGDET_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return STILES_OK;
+}
+
+stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, int64_t nrhs, int64_t ld, void* stream,
+                           double* final_relres) {
+  if (!cf || !b || !x) return fail(STILES_ERR_INVALID, "null argument");
+  stiles_factor* f = const_cast<stiles_factor*>(cf);
+  const stiles_plan* p = f->plan;
+  if (nrhs < 1 || ld < p->n) return fail(STILES_ERR_INVALID, "nrhs < 1 or ld < n");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  if (bdev != xdev) return fail(STILES_ERR_INVALID, "b and x must both be host or both be device memory");
+  const int64_t n = p->n, B = p->B;
+  const int nrmax = int(std::min<int64_t>(nrhs, dev::SOLVE_MAXR));
+  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
+  if (f->solve_nr < nrmax) {
+    cudaFree(f->Y);
+    cudaFree(f->sscratch);
+    cudaFree(f->sflags);
+    cudaFree(f->ywork);
+    f->Y = f->sscratch = f->ywork = nullptr;
+    f->sflags = nullptr;
+    f->solve_nr = 0;
+    CUDA_TRY(cudaMalloc(&f->Y, size_t(p->nsb) * B * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&f->sscratch, size_t(nf + nb) * B * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&f->sflags, size_t(2 * p->nsb + nf + nb) * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&f->ywork, size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
+    f->solve_nr = dev::SOLVE_MAXR;
+  }
+  const double* db = b;
+  double* dx = x;
+  int64_t dld = ld;
+  if (!bdev) {
+    const int64_t need = n * nrhs;
+    if (f->stage_elems < need) {
+      cudaFree(f->bstage);
+      cudaFree(f->xstage);
+      f->bstage = f->xstage = nullptr;
+      f->stage_elems = 0;
+      CUDA_TRY(cudaMalloc(&f->bstage, size_t(need) * sizeof(double)));
+      CUDA_TRY(cudaMalloc(&f->xstage, size_t(need) * sizeof(double)));
+      f->stage_elems = need;
+    }
+    CUDA_TRY(cudaMemcpy2DAsync(f->bstage, n * sizeof(double), b, ld * sizeof(double), n * sizeof(double), nrhs,
+                               cudaMemcpyHostToDevice, st));
+    db = f->bstage;
+    dx = f->xstage;
+    dld = n;
+  }
+  double worst = 0.0;
+  for (int64_t r0 = 0; r0 < nrhs; r0 += dev::SOLVE_MAXR) {
+    const int nr = int(std::min<int64_t>(dev::SOLVE_MAXR, nrhs - r0));
+    dev::permute_in_kernel<<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(f->Y, db, p->dev->perm, n, dld, int(r0),
+                                                                          nr, int(B), p->nsb);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemsetAsync(f->sflags, 0, size_t(2 * p->nsb + nf + nb) * sizeof(int), st));
+    dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl + 1, 2);
+    CUDA_TRY(cudaGetLastError());
+    cudaError_t e;
+    switch (p->B) {
+      case 16: e = launch_solve<16>(p, f, st, nr); break;
+      case 32: e = launch_solve<32>(p, f, st, nr); break;
+      default: e = launch_solve<64>(p, f, st, nr); break;
+    }
+    if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
+    count_launch(5);
+    dev::permute_out_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(dx, f->Y, p->dev->perm, n, dld, int(r0), nr,
+                                                                   int(B));
+    CUDA_TRY(cudaGetLastError());
+    if (final_relres) {
+      CUDA_TRY(cudaMemsetAsync(f->ywork, 0, size_t(n) * nr * sizeof(double), st));
+      CUDA_TRY(cudaMemsetAsync(f->norms, 0, 2 * dev::SOLVE_MAXR * sizeof(double), st));
+      dev::spmv_lower_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(f->ywork, dx + r0 * dld, p->dev->colptr,
+                                                                   p->dev->rowidx, f->values, n, dld, nr);
+      CUDA_TRY(cudaGetLastError());
+      dev::residual_norms_kernel<<<dim3(64, nr), 256, 0, st>>>(f->ywork, db + r0 * dld, n, dld, nr, f->norms);
+      CUDA_TRY(cudaGetLastError());
+      count_launch(2);
+      double h[2 * dev::SOLVE_MAXR];
+      CUDA_TRY(cudaMemcpyAsync(h, f->norms, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      for (int r = 0; r < nr; ++r) {
+        const double rel = h[2 * r + 1] > 0 ? std::sqrt(h[2 * r] / h[2 * r + 1]) : std::sqrt(h[2 * r]);
+        worst = std::max(worst, rel);
+      }
+    }
+    stiles_status s1 = STILES_OK;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    s1 = read_ctl(f, 1, nullptr);
+    if (s1 == STILES_OK) s1 = read_ctl(f, 2, nullptr);
+    if (s1 != STILES_OK) return s1;
+  }
+  if (!xdev) {
+    CUDA_TRY(cudaMemcpy2DAsync(x, ld * sizeof(double), dx, n * sizeof(double), n * sizeof(double), nrhs,
+                               cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (final_relres) *final_relres = worst;
+  return STILES_OK;
+}
+
+stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* stream) {
+  if (!cf || !out) return fail(STILES_ERR_INVALID, "null argument");
+  stiles_factor* f = const_cast<stiles_factor*>(cf);
+  const stiles_plan* p = f->plan;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t elems = size_t(p->nnzt) * p->T * p->T;
+  const bool odev = is_device_ptr(out);
+  double* dst = out;
+  if (!odev) CUDA_TRY(cudaMalloc(&dst, elems * sizeof(double)));
+  dev::export_tiles_kernel<<<grid_for(int64_t(elems), 256), 256, 0, st>>>(dst, f->tiles, p->nnzt, p->T, p->B);
+  cudaError_t e = cudaGetLastError();
+  count_launch();
+  if (e == cudaSuccess && !odev) e = cudaMemcpyAsync(out, dst, elems * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!odev) cudaFree(dst);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("tile export: ") + cudaGetErrorString(e));
+  return STILES_OK;
+}
+
+stiles_status stiles_factor_timing(const stiles_factor* f, double* ms_call, double* ms_kernel) {
+  if (!f) return fail(STILES_ERR_INVALID, "null factor");
+  float a = 0.f, b = 0.f;
+  CUDA_TRY(cudaEventSynchronize(f->ev[2]));
+  CUDA_TRY(cudaEventElapsedTime(&a, f->ev[0], f->ev[2]));
+  CUDA_TRY(cudaEventElapsedTime(&b, f->ev[1], f->ev[2]));
+  if (ms_call) *ms_call = a;
+  if (ms_kernel) *ms_kernel = b;
+  return STILES_OK;
+}
+
+stiles_status stiles_factor_set_trace(stiles_factor* f, int32_t enable) {
+  if (!f) return fail(STILES_ERR_INVALID, "null factor");
+  const stiles_plan* p = f->plan;
+  const size_t n[3] = {p->graph.tasks.size(), p->fwd.tasks.size(), p->bwd.tasks.size()};
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(f->trace[i]);
+    f->trace[i] = nullptr;
+    if (enable && n[i]) {
+      CUDA_TRY(cudaMalloc(&f->trace[i], n[i] * 4 * sizeof(long long)));
+      CUDA_TRY(cudaMemset(f->trace[i], 0, n[i] * 4 * sizeof(long long)));
+    }
+  }
+  return STILES_OK;
+}
+
+stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int64_t* out, int64_t* ntasks) {
+  if (!f || which < 0 || which > 2) return fail(STILES_ERR_INVALID, "bad argument");
+  const stiles_plan* p = f->plan;
+  const size_t n = which == 0 ? p->graph.tasks.size() : (which == 1 ? p->fwd.tasks.size() : p->bwd.tasks.size());
+  if (ntasks) *ntasks = int64_t(n);
+  if (!out) return STILES_OK;
+  if (!f->trace[which]) return fail(STILES_ERR_INVALID, "tracing is not enabled");
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(out, f->trace[which], n * 4 * sizeof(long long), cudaMemcpyDeviceToHost));
+  return STILES_OK;
+}
+
+stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
+  if (!p || which < 0 || which > 2) return fail(STILES_ERR_INVALID, "bad argument");
+  const void* src;
+  size_t n;
+  if (which == 0) { src = p->graph.tasks.data(); n = p->graph.tasks.size(); }
+  else if (which == 1) { src = p->fwd.tasks.data(); n = p->fwd.tasks.size(); }
+  else { src = p->bwd.tasks.data(); n = p->bwd.tasks.size(); }
+  if (ntasks) *ntasks = int64_t(n);
+  if (out && n) std::memcpy(out, src, n * 8 * sizeof(int32_t));
+  return STILES_OK;
+}
+
+int64_t stiles_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+stiles_status stiles_probe_fp64_peak(double* tflops) {
+  if (!tflops) return fail(STILES_ERR_INVALID, "null argument");
+  int device = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&device));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  double* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, 64));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int iters = 4000, blocks = sms * 2, threads = 256;
+  dev::fp64_probe_kernel<<<blocks, threads>>>(d, 200, 1.0000001, 1e-9);
+  count_launch(2);
+  cudaEventRecord(e0);
+  dev::fp64_probe_kernel<<<blocks, threads>>>(d, iters, 1.0000001, 1e-9);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, cudaGetErrorString(e));
+  *tflops = 2.0 * 8 * double(iters) * threads * blocks / (double(ms) * 1e-3) / 1e12;
+  return STILES_OK;
+}
+
+}  // extern "C"

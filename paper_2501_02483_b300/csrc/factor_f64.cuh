@@ -1,0 +1,335 @@
+// Persistent FP64 tile Cholesky (Algorithm 1, left-looking, on B x B sub-tiles).
+//
+// One launch runs the whole factorization.  Each CTA repeatedly takes the next
+// ticket of a topologically ordered task list (the device analogue of the
+// static scheduler's task table, Algorithm 2) and executes it:
+//
+//   DIAG     A_kk -= sum L_kn L_kn^T (+ tree partials), then POTRF
+//   OFF      A_mk -= sum L_mn L_kn^T (+ tree partials), then TRSM with L_kk
+//   PARTIAL  S = -sum of a chunk of L_an L_bn^T       (tree leaf, Algorithm 3)
+//   COMBINE  S = sum of child partials                 (tree node, GEADD)
+//
+// Dependencies are per-tile ready flags (the progress table of Algorithm 2)
+// read with acquire loads; waits are bounded and end the launch with
+// STILES_ERR_TIMEOUT instead of hanging.  Operand tiles are contiguous in HBM
+// (CTSF) and are staged into shared memory by 1-D TMA bulk copies, NSTAGE
+// pairs in flight.  The accumulator lives in registers: thread (i, q) owns row
+// i and the columns q, q + RPT, q + 2 RPT, ... of the output tile.
+#pragma once
+
+#include "device_common.cuh"
+#include "plan.h"
+
+namespace stiles {
+namespace dev {
+
+template <int B>
+struct FactorCfg {
+  static constexpr int NT = 128;
+  static constexpr int RPT = NT / B;  // threads per tile row
+  static constexpr int CPT = B / RPT; // columns per thread
+  static constexpr int TILE = B * B;
+  static constexpr int NSTAGE = (B == 64) ? 2 : 3;
+  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 2 * B;
+  static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
+};
+
+struct FactorArgs {
+  double* tiles;    // nsub * B * B, sub-tile s at s * B * B, column-major
+  double* scratch;  // nscratch * B * B (tree partials, stored negated)
+  double* invdiag;  // nsb * B: 1 / L_jj of each diagonal sub-tile
+  const DevTask* tasks;
+  int ntasks;
+  const int32_t* pairs;
+  const int32_t* parts;
+  int* flags;   // per sub-tile: 1 when final
+  int* sflags;  // per scratch tile: 1 when final
+  Ctl* ctl;
+  long long spin_limit;
+  long long* trace;  // optional, 4 per ticket: start, dependencies ready, done, SM id
+};
+
+// All threads have stored the tile; after the barrier, thread 0's release
+// store makes the whole CTA's writes visible to any thread that acquires the
+// flag (release cumulativity through bar.sync).
+__device__ __forceinline__ void publish(int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(flag, 1);
+}
+
+template <int B>
+__global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
+  using Cfg = FactorCfg<B>;
+  constexpr int RPT = Cfg::RPT, CPT = Cfg::CPT, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* sStage = reinterpret_cast<double*>(smem_raw);
+  double* sC = sStage + NSTAGE * 2 * TILE;
+  double* sL = sC + TILE;
+  double* sInv = sL + TILE;
+  double* sPiv = sInv + B;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPiv + B);
+  __shared__ int sTicket, sAbort;
+
+  const int tid = threadIdx.x;
+  const int row = tid / RPT;
+  const int q = tid % RPT;
+  const int lane = tid & 31;
+  const int row_lane0 = lane - (lane % RPT);  // first lane of this row inside the warp
+
+  if (tid == 0) {
+    for (int s = 0; s <= NSTAGE; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;  // bit s: parity of the next completion of barrier s
+  const long long limit = a.spin_limit;
+
+  int next = 0;
+  if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
+  while (true) {
+    if (tid == 0) {
+      int cur = next;
+      if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) {
+        next = atomicAdd(&a.ctl->ticket, 1);
+      } else {
+        cur = -1;
+      }
+      sTicket = cur;
+      sAbort = 0;
+    }
+    __syncthreads();
+    const int t = sTicket;
+    if (t < 0) break;
+    const DevTask tk = a.tasks[t];
+    long long* const trace = a.trace ? a.trace + 4 * size_t(t) : nullptr;
+    unsigned long long t_ready = 0;
+    if (trace && tid == 0) {
+      t_ready = globaltimer();
+      trace[0] = (long long)t_ready;
+      trace[3] = smid();
+    }
+
+    double acc[CPT];
+    if (tk.type == TASK_DIAG || tk.type == TASK_OFF) {
+      const double* src = a.tiles + size_t(tk.out) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) acc[m] = src[(q + RPT * m) * B + row];
+    } else {
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) acc[m] = 0.0;
+    }
+
+    // ---- operand pipeline: pairs [pb, pe), then partial tiles [qb, qe) ----
+    const int npairs = tk.pe - tk.pb;
+    const int nitems = npairs + (tk.qe - tk.qb);
+    int issued = 0, stop = nitems;
+    bool aborted = false;
+    for (int it = 0; it < nitems; ++it) {
+      // producer (thread 0): keep up to NSTAGE items in flight; block only on item `it`
+      if (tid == 0) {
+        while (issued < nitems && issued < it + NSTAGE) {
+          const int* f1;
+          const int* f2 = nullptr;
+          const double* g1;
+          const double* g2 = nullptr;
+          if (issued < npairs) {
+            const int pa = a.pairs[2 * (tk.pb + issued)];
+            const int pb = a.pairs[2 * (tk.pb + issued) + 1];
+            f1 = a.flags + pa;
+            g1 = a.tiles + size_t(pa) * TILE;
+            if (pb != pa) {
+              f2 = a.flags + pb;
+              g2 = a.tiles + size_t(pb) * TILE;
+            }
+          } else {
+            const int s = a.parts[tk.qb + issued - npairs];
+            f1 = a.sflags + s;
+            g1 = a.scratch + size_t(s) * TILE;
+          }
+          if (issued == it) {
+            if (!(wait_flag(f1, 1, limit, a.ctl) && (f2 == nullptr || wait_flag(f2, 1, limit, a.ctl)))) {
+              raise_timeout(a.ctl, t);
+              sAbort = 1;
+              break;
+            }
+          } else if (!(ld_acquire(f1) == 1 && (f2 == nullptr || ld_acquire(f2) == 1))) {
+            break;
+          }
+          fence_proxy_async_global();
+          const int st = issued % NSTAGE;
+          double* dst = sStage + st * 2 * TILE;
+          mbar_arrive_expect_tx(&bars[st], uint32_t((g2 ? 2 : 1) * TILE * sizeof(double)));
+          tma_load_1d(dst, g1, TILE * sizeof(double), &bars[st]);
+          if (g2) tma_load_1d(dst + TILE, g2, TILE * sizeof(double), &bars[st]);
+          ++issued;
+        }
+        if (trace && it == nitems - 1) t_ready = globaltimer();
+      }
+      __syncthreads();  // the other warps sleep here while thread 0 waits on flags
+      if (sAbort) { stop = it; aborted = true; break; }
+      const int st = it % NSTAGE;
+      {
+        long long spins = 0;
+        while (!mbar_try_wait(&bars[st], (phase >> st) & 1u)) {
+          if (++spins > kTmaWaitLimit) { aborted = true; break; }
+        }
+      }
+      if (aborted) { stop = it; break; }
+      phase ^= (1u << st);
+      const double* sA = sStage + st * 2 * TILE;
+      if (it < npairs) {
+        const int pa = a.pairs[2 * (tk.pb + it)], pb = a.pairs[2 * (tk.pb + it) + 1];
+        const double* sB = (pa == pb) ? sA : sA + TILE;
+#pragma unroll 4
+        for (int p = 0; p < B; ++p) {
+          const double av = sA[row + p * B];
+#pragma unroll
+          for (int m = 0; m < CPT; ++m) acc[m] = fma(-av, sB[q + RPT * m + p * B], acc[m]);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) acc[m] += sA[row + (q + RPT * m) * B];
+      }
+      __syncthreads();  // stage `st` may be refilled
+    }
+    if (aborted) {
+      // Drain copies that were issued but not consumed (items [stop, issued)),
+      // so that no TMA write lands in shared memory after the CTA has exited.
+      if (tid == 0) {
+        for (int j = stop; j < issued; ++j) {
+          const int st = j % NSTAGE;
+          long long spins = 0;
+          while (!mbar_try_wait(&bars[st], (phase >> st) & 1u) && ++spins < kTmaWaitLimit) {
+          }
+        }
+      }
+      break;
+    }
+
+    if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) {
+      double* dst = a.scratch + size_t(tk.out) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+      publish(a.sflags + tk.out);
+      if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+      continue;
+    }
+
+    if (tk.type == TASK_DIAG) {
+      // ---- POTRF: right-looking on unscaled columns; one barrier per column ----
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
+      __syncthreads();
+      if (tid == 0) {
+        const double d = sC[0];
+        sPiv[0] = d;
+        sInv[0] = 1.0 / d;
+      }
+      __syncthreads();
+      int bad = -1;
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        const double d = sPiv[j];
+        if (!(d > 0.0)) { bad = j; break; }
+        const double tr = sC[row + j * B] * sInv[j];
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+          const int c = q + RPT * m;
+          if (c > j && c <= row) acc[m] = fma(-tr, sC[c + j * B], acc[m]);
+        }
+        if (j + 1 < B) {
+          const int cn = j + 1;
+          if (q == cn % RPT && row >= cn) {
+            const double v = acc[cn / RPT];
+            sC[row + cn * B] = v;
+            if (row == cn) {
+              sPiv[cn] = v;
+              sInv[cn] = 1.0 / v;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (bad >= 0) {
+        if (tid == 0) {
+          const unsigned long long col = (unsigned long long)tk.col * B + bad + 1;
+          atomicMin(&a.ctl->info, col);
+        }
+        const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) acc[m] = nanv;
+        if (tid < B) sInv[tid] = nanv;
+      } else {
+        // L_ij = a_ij / sqrt(d_j); L_jj = sqrt(d_j)
+        if (tid < B) sInv[tid] = 1.0 / sqrt(sPiv[tid]);
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+          const int c = q + RPT * m;
+          acc[m] = (c <= row) ? acc[m] * sInv[c] : 0.0;
+        }
+      }
+      __syncthreads();
+      double* dst = a.tiles + size_t(tk.out) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+      if (tid < B) a.invdiag[size_t(tk.col) * B + tid] = sInv[tid];
+      publish(a.flags + tk.out);
+      if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+      continue;
+    }
+
+    // ---- TASK_OFF: TRSM with L_kk once it is final ----
+    if (tid == 0) {
+      if (!wait_flag(a.flags + tk.diag, 1, limit, a.ctl)) {
+        raise_timeout(a.ctl, t);
+        sAbort = 1;
+      } else {
+        if (trace) t_ready = globaltimer();
+        fence_proxy_async_global();
+        mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
+        tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+      }
+    }
+    __syncthreads();
+    if (sAbort) break;
+    {
+      long long spins = 0;
+      while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
+        if (++spins > kTmaWaitLimit) { aborted = true; break; }
+      }
+      if (aborted) break;
+      phase ^= (1u << NSTAGE);
+    }
+    double inv[CPT];
+    {
+      const double* iv = a.invdiag + size_t(tk.col) * B;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) inv[m] = __ldcg(iv + q + RPT * m);
+    }
+    // X L_kk^T = A, column by column; x_ij broadcast to the row's RPT lanes
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int mj = j / RPT;
+      const bool owner = (q == j % RPT);
+      double x = owner ? acc[mj] * inv[mj] : 0.0;
+      x = __shfl_sync(0xffffffffu, x, row_lane0 + (j % RPT));
+      if (owner) acc[mj] = x;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) {
+        const int c = q + RPT * m;
+        if (c > j) acc[m] = fma(-x, sL[c + j * B], acc[m]);
+      }
+    }
+    {
+      double* dst = a.tiles + size_t(tk.out) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+    }
+    publish(a.flags + tk.out);
+    if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+  }
+}
+
+}  // namespace dev
+}  // namespace stiles

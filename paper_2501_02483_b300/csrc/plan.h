@@ -1,0 +1,94 @@
+// Internal plan and factor structures shared by the host analysis (analyze.cpp)
+// and the CUDA side (capi.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stiles.h"
+
+namespace stiles {
+
+// One unit of device work of the factorization (a ticket of the persistent
+// scheduler).  Tickets are issued in a topological order: every tile a task
+// waits for is produced by a task with a smaller ticket.
+enum TaskType : int32_t {
+  TASK_DIAG = 0,     // L_kk = chol(A_kk - sum L_kn L_kn^T - sum partials)           (SYRK + POTRF)
+  TASK_OFF = 1,      // L_mk = (A_mk - sum L_mn L_kn^T - sum partials) L_kk^{-T}       (GEMM + TRSM)
+  TASK_PARTIAL = 2,  // P = sum over a chunk of L_an L_bn^T   (a tree leaf, Algorithm 3)
+  TASK_COMBINE = 3,  // P = sum of partial tiles             (a tree node, GEADD)
+};
+
+struct DevTask {
+  int32_t type;
+  int32_t out;   // sub-tile index (DIAG/OFF) or scratch tile index (PARTIAL/COMBINE)
+  int32_t diag;  // sub-tile index of L_kk (OFF), else -1
+  int32_t col;   // sub-column k (DIAG: slot of the log-determinant partial)
+  int32_t pb, pe;  // update pairs [pb, pe)
+  int32_t qb, qe;  // partial tiles [qb, qe) (scratch indices)
+};
+static_assert(sizeof(DevTask) == 32, "DevTask layout");
+
+// Solve task: one B x nrhs block of y (forward) or x (backward).
+enum SolveType : int32_t { SOLVE_FINAL = 0, SOLVE_PARTIAL = 2, SOLVE_COMBINE = 3 };
+struct SolveTask {
+  int32_t type;
+  int32_t out;   // block index (FINAL) or scratch block index (PARTIAL/COMBINE)
+  int32_t diag;  // sub-tile index of L_kk (FINAL)
+  int32_t pad0;
+  int32_t pb, pe;  // pairs (L sub-tile, block index)
+  int32_t qb, qe;  // scratch blocks
+};
+static_assert(sizeof(SolveTask) == 32, "SolveTask layout");
+
+struct TaskGraph {
+  std::vector<DevTask> tasks;
+  std::vector<int32_t> pairs;  // 2 per pair
+  std::vector<int32_t> parts;
+  int64_t nscratch = 0;
+};
+
+struct SolveGraph {
+  std::vector<SolveTask> tasks;
+  std::vector<int32_t> pairs;
+  std::vector<int32_t> parts;
+  int64_t nscratch = 0;
+};
+
+struct DevPlan;  // device copies, defined in capi.cu
+
+}  // namespace stiles
+
+struct stiles_plan {
+  stiles_opts opts{};
+  int64_t n = 0, n_arrow = 0, nnz = 0;
+  int32_t T = 0, B = 0, R = 0;
+  int32_t ordering_used = 0;
+  std::vector<int64_t> colptr;   // copy of the input pattern (for the residual SpMV)
+  std::vector<int32_t> rowidx;
+  std::vector<int64_t> perm;     // perm[new] = old
+  std::vector<int64_t> iperm;    // iperm[old] = new
+  // T-level tile map (tile-CSC, diagonal first)
+  int64_t nt = 0, nnzt = 0;
+  std::vector<int64_t> tcolptr;
+  std::vector<int32_t> trowidx;
+  int64_t flops_potrf = 0, flops_syrk = 0, flops_gemm = 0, flops_trsm = 0;
+  // B-level executor (only when T % B == 0 and B in {16, 32, 64})
+  bool executable = false;
+  int64_t nsb = 0;               // sub-rows/columns holding rows < n
+  int64_t nsub = 0;              // stored sub-tiles = nnzt * R * R
+  std::vector<int32_t> diag_sub; // [nsb] sub-tile index of each diagonal sub-tile
+  std::vector<int64_t> scatter;  // [nnz] element offset of each input entry in the tile buffer
+  std::vector<int64_t> pad;      // element offsets of padding diagonal entries (rows >= n)
+  stiles::TaskGraph graph;
+  stiles::SolveGraph fwd, bwd;
+  stiles::DevPlan* dev = nullptr;
+};
+
+namespace stiles {
+// analyze.cpp
+stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                         const stiles_opts& opts, stiles_plan* p, std::string* err);
+void default_opts(stiles_opts* o);
+}  // namespace stiles

@@ -1,0 +1,312 @@
+// Persistent FP64 forward (L y = P b) and backward (L^T x = y) tile sweeps.
+//
+// Same scheduling scheme as the factorization: one task per B-row block of
+// the right-hand sides, in ticket order, waiting on per-block ready flags.
+// Long accumulations (the arrow rows, which see every body block) are split
+// into tree leaves exactly like the factorization's arrow updates.
+//
+// Block layout: block k (rows k*B .. k*B+B-1 of the permuted system, nr
+// right-hand sides) is contiguous, column-major B x nr, at Y + k * B * nr.
+// Thread layout: W = min(B, 32) lanes hold one right-hand side column
+// (RP = B / W rows each); the NT / W lane groups take columns g, g + G, ...
+#pragma once
+
+#include "device_common.cuh"
+#include "plan.h"
+
+namespace stiles {
+namespace dev {
+
+constexpr int SOLVE_MAXR = 16;  // right-hand sides per launch
+
+template <int B>
+struct SolveCfg {
+  static constexpr int NT = 128;
+  static constexpr int W = (B < 32) ? B : 32;
+  static constexpr int RP = B / W;
+  static constexpr int G = NT / W;
+  static constexpr int U = (SOLVE_MAXR + G - 1) / G;
+  static constexpr int TILE = B * B;
+  static constexpr int BLK = B * SOLVE_MAXR;
+  static constexpr int NSTAGE = 3;
+  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * (TILE + BLK) + TILE + size_t(B) * (B + 1) + B;
+  static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
+};
+
+struct SolveArgs {
+  const double* tiles;    // factor sub-tiles
+  const double* invdiag;  // nsb * B
+  double* Y;              // nsb blocks of B x nr
+  double* scratch;        // nscratch blocks
+  const SolveTask* tasks;
+  int ntasks;
+  const int32_t* pairs;   // (L sub-tile, block)
+  const int32_t* parts;
+  int* flags;             // per block
+  int* sflags;            // per scratch block
+  Ctl* ctl;
+  long long spin_limit;
+  int nr;                 // right-hand sides in this launch (<= SOLVE_MAXR)
+  long long* trace;       // optional, 4 per ticket: start, dependencies ready, done, SM id
+};
+
+template <int B, bool BACKWARD>
+__global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
+  using Cfg = SolveCfg<B>;
+  constexpr int W = Cfg::W, RP = Cfg::RP, G = Cfg::G, U = Cfg::U, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* sStage = reinterpret_cast<double*>(smem_raw);            // NSTAGE * (TILE + BLK)
+  double* sL = sStage + NSTAGE * (TILE + Cfg::BLK);                 // TILE
+  double* sLt = sL + TILE;                                          // B x (B + 1), transposed L_kk
+  double* sInv = sLt + B * (B + 1);                                 // B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sInv + B);
+  __shared__ int sTicket, sAbort;
+
+  const int tid = threadIdx.x;
+  const int li = tid % W;  // lane inside the column group
+  const int grp = tid / W;
+  const int nr = a.nr;
+  const int blk = B * nr;  // doubles per block
+  const long long limit = a.spin_limit;
+
+  if (tid == 0) {
+    for (int s = 0; s <= NSTAGE; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  int next = 0;
+  if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
+  while (true) {
+    if (tid == 0) {
+      int cur = next;
+      if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(&a.ctl->ticket, 1);
+      else cur = -1;
+      sTicket = cur;
+      sAbort = 0;
+    }
+    __syncthreads();
+    const int t = sTicket;
+    if (t < 0) break;
+    const SolveTask tk = a.tasks[t];
+    long long* const trace = a.trace ? a.trace + 4 * size_t(t) : nullptr;
+    unsigned long long t_ready = 0;
+    if (trace && tid == 0) {
+      t_ready = globaltimer();
+      trace[0] = (long long)t_ready;
+      trace[3] = smid();
+    }
+
+    double acc[RP][U];
+    if (tk.type == SOLVE_FINAL) {
+      const double* src = a.Y + size_t(tk.out) * blk;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = grp + G * u;
+#pragma unroll
+        for (int s = 0; s < RP; ++s) acc[s][u] = (r < nr) ? src[r * B + li + W * s] : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int s = 0; s < RP; ++s) acc[s][u] = 0.0;
+    }
+
+    const int npairs = tk.pe - tk.pb;
+    const int nitems = npairs + (tk.qe - tk.qb);
+    int issued = 0, stop = nitems;
+    bool aborted = false;
+    for (int it = 0; it < nitems; ++it) {
+      if (tid == 0) {
+        while (issued < nitems && issued < it + NSTAGE) {
+          const int* f;
+          const double* gL = nullptr;
+          const double* gY;
+          if (issued < npairs) {
+            const int ls = a.pairs[2 * (tk.pb + issued)];
+            const int bk = a.pairs[2 * (tk.pb + issued) + 1];
+            f = a.flags + bk;
+            gL = a.tiles + size_t(ls) * TILE;
+            gY = a.Y + size_t(bk) * blk;
+          } else {
+            const int s = a.parts[tk.qb + issued - npairs];
+            f = a.sflags + s;
+            gY = a.scratch + size_t(s) * blk;
+          }
+          if (issued == it) {
+            if (!wait_flag(f, 1, limit, a.ctl)) {
+              raise_timeout(a.ctl, t);
+              sAbort = 1;
+              break;
+            }
+          } else if (ld_acquire(f) != 1) {
+            break;
+          }
+          fence_proxy_async_global();
+          const int st = issued % NSTAGE;
+          double* dst = sStage + st * (TILE + Cfg::BLK);
+          mbar_arrive_expect_tx(&bars[st], uint32_t(((gL ? TILE : 0) + blk) * sizeof(double)));
+          if (gL) tma_load_1d(dst, gL, TILE * sizeof(double), &bars[st]);
+          tma_load_1d(dst + TILE, gY, uint32_t(blk * sizeof(double)), &bars[st]);
+          ++issued;
+        }
+        if (trace && it == nitems - 1) t_ready = globaltimer();
+      }
+      __syncthreads();  // the other warps sleep here while thread 0 waits on flags
+      if (sAbort) { stop = it; aborted = true; break; }
+      const int st = it % NSTAGE;
+      {
+        long long spins = 0;
+        while (!mbar_try_wait(&bars[st], (phase >> st) & 1u)) {
+          if (++spins > kTmaWaitLimit) { aborted = true; break; }
+        }
+      }
+      if (aborted) { stop = it; break; }
+      phase ^= (1u << st);
+      const double* sT = sStage + st * (TILE + Cfg::BLK);
+      const double* sY = sT + TILE;
+      if (it < npairs) {
+        if (!BACKWARD) {
+          // acc(i, r) -= sum_p L(i, p) y(p, r)
+#pragma unroll 4
+          for (int p = 0; p < B; ++p) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int r = grp + G * u;
+              if (r < nr) {
+                const double yv = sY[r * B + p];
+#pragma unroll
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-sT[li + W * s + p * B], yv, acc[s][u]);
+              }
+            }
+          }
+        } else {
+          // acc(i, r) -= sum_p L(p, i) x(p, r); p rotated per lane to spread banks
+#pragma unroll 4
+          for (int pp = 0; pp < B; ++pp) {
+            const int p = (pp + li) & (B - 1);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int r = grp + G * u;
+              if (r < nr) {
+                const double xv = sY[r * B + p];
+#pragma unroll
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-sT[p + (li + W * s) * B], xv, acc[s][u]);
+              }
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int r = grp + G * u;
+          if (r < nr)
+#pragma unroll
+            for (int s = 0; s < RP; ++s) acc[s][u] += sY[r * B + li + W * s];
+        }
+      }
+      __syncthreads();
+    }
+    if (aborted) {
+      if (tid == 0) {
+        for (int j = stop; j < issued; ++j) {
+          const int st = j % NSTAGE;
+          long long spins = 0;
+          while (!mbar_try_wait(&bars[st], (phase >> st) & 1u) && ++spins < kTmaWaitLimit) {
+          }
+        }
+      }
+      break;
+    }
+
+    if (tk.type != SOLVE_FINAL) {
+      double* dst = a.scratch + size_t(tk.out) * blk;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = grp + G * u;
+        if (r < nr)
+#pragma unroll
+          for (int s = 0; s < RP; ++s) dst[r * B + li + W * s] = acc[s][u];
+      }
+      publish(a.sflags + tk.out);
+      if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+      continue;
+    }
+
+    // ---- triangular solve with the diagonal sub-tile (already final) ----
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
+      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+    }
+    if (tid < B) sInv[tid] = __ldcg(a.invdiag + size_t(tk.out) * B + tid);
+    {
+      long long spins = 0;
+      while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
+        if (++spins > kTmaWaitLimit) { aborted = true; break; }
+      }
+    }
+    if (aborted) break;
+    phase ^= (1u << NSTAGE);
+    if (BACKWARD) {
+      for (int e = tid; e < TILE; e += Cfg::NT) {
+        const int r = e % B, c = e / B;
+        sLt[c + r * (B + 1)] = sL[e];  // sLt(c, r) = L(r, c)
+      }
+    }
+    __syncthreads();
+    if (!BACKWARD) {
+      // forward substitution: y_j = acc_j / L_jj, then acc_i -= L_ij y_j (i > j)
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        const int sj = j / W, lj = j % W;
+        const double inv = sInv[j];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          double y = acc[sj][u] * inv;
+          y = __shfl_sync(0xffffffffu, y, (tid & 31) - li + lj);
+          if (li == lj) acc[sj][u] = y;
+#pragma unroll
+          for (int s = 0; s < RP; ++s) {
+            const int i = li + W * s;
+            if (i > j) acc[s][u] = fma(-sL[i + j * B], y, acc[s][u]);
+          }
+        }
+      }
+    } else {
+      // backward substitution with L^T: x_j = acc_j / L_jj, then acc_i -= L_ji x_j (i < j)
+#pragma unroll
+      for (int j = B - 1; j >= 0; --j) {
+        const int sj = j / W, lj = j % W;
+        const double inv = sInv[j];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          double x = acc[sj][u] * inv;
+          x = __shfl_sync(0xffffffffu, x, (tid & 31) - li + lj);
+          if (li == lj) acc[sj][u] = x;
+#pragma unroll
+          for (int s = 0; s < RP; ++s) {
+            const int i = li + W * s;
+            if (i < j) acc[s][u] = fma(-sLt[i + j * (B + 1)], x, acc[s][u]);
+          }
+        }
+      }
+    }
+    {
+      double* dst = a.Y + size_t(tk.out) * blk;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = grp + G * u;
+        if (r < nr)
+#pragma unroll
+          for (int s = 0; s < RP; ++s) dst[r * B + li + W * s] = acc[s][u];
+      }
+    }
+    publish(a.flags + tk.out);
+    if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+  }
+}
+
+}  // namespace dev
+}  // namespace stiles

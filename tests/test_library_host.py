@@ -1,0 +1,152 @@
+"""Host-side checks of libstiles.so (no GPU needed).
+
+* the shared library loads and exports every function declared in
+  include/stiles.h;
+* stiles_analyze agrees bit-for-bit with the oracle's independent analysis:
+  permutation, tile map and per-kernel flop counts;
+* malformed input is rejected with STILES_ERR_INVALID.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import analyze as oan
+from oracle import ordering as oord
+from oracle import tiles as otiles
+from paper_2501_02483_b300 import build, inputs
+from paper_2501_02483_b300 import stiles as st
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build_library()
+    st.lib()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "stiles.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = sorted(set(re.findall(r"\b(stiles_[a-z0-9_]+)\s*\(", hdr)))
+    assert len(names) >= 15
+    L = st.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _oracle_plan(m, T, order):
+    p = oan.analyze(m, T, order)
+    f = otiles.task_flops(m["n"], T, p["tcolptr"], p["trowidx"])
+    return p, f
+
+
+def _compare(m, T, order, **kw):
+    p, f = _oracle_plan(m, T, order)
+    plan = st.Plan.from_matrix(m, tile=T, ordering=order, **kw)
+    info = plan.info()
+    assert np.array_equal(plan.perm(), p["perm"])
+    tc, tr = plan.tilemap()
+    assert np.array_equal(tc, p["tcolptr"])
+    assert np.array_equal(tr, p["trowidx"])
+    assert info["ordering_used"] == p["ordering_used"]
+    for k in ("potrf", "syrk", "gemm", "trsm", "total"):
+        assert info["flops_" + k] == f[k], k
+    plan.close()
+
+
+CASES = [
+    ("band", lambda s: inputs.band_arrow(300, 5, 12, 0.3, s)),
+    ("wide", lambda s: inputs.band_arrow(500, 20, 60, 0.1, s)),
+    ("noarrow", lambda s: inputs.band_arrow(257, 0, 9, 0.5, s)),
+    ("diag", lambda s: inputs.diagonal_matrix(np.arange(1.0, 101.0), n_arrow=3)),
+    ("kron", lambda s: inputs.kronecker_spatiotemporal(6, 0.8, 5, 1.0, 4, 0.1, s, nrhs=0)),
+    ("arrowhead", lambda s: inputs.pure_arrowhead(200, 7, seed=s)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("T", [1, 3, 16, 32, 64, 100])
+@pytest.mark.parametrize("order", [oan.ORDER_NONE, oan.ORDER_RCM, oan.ORDER_AUTO])
+def test_analyze_matches_oracle(name, make, T, order):
+    _compare(make(T + 7 * order), T, order)
+
+
+def _scrambled(n, hw, w, seed):
+    rng = np.random.default_rng(seed)
+    m = inputs.band_arrow(n, w, hw, 0.4, seed)
+    lab = np.concatenate([rng.permutation(n), np.arange(n, n + w)])
+    cols = np.repeat(np.arange(n + w), np.diff(m["colptr"]))
+    r, c = lab[m["rowidx"]], lab[cols]
+    colptr, rowidx, values = inputs.coo_to_csc_lower(n + w, np.maximum(r, c), np.minimum(r, c), m["values"])
+    return {"n": n + w, "n_arrow": w, "colptr": colptr, "rowidx": rowidx, "values": values}
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_analyze_matches_oracle_random_scrambled(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(20, 400))
+    hw = int(rng.integers(1, 20))
+    w = int(rng.integers(0, 8))
+    T = int(rng.choice([1, 2, 5, 8, 16, 32, 48]))
+    order = int(rng.integers(0, 3))
+    _compare(_scrambled(n, hw, w, seed), T, order)
+
+
+def test_analyze_matches_oracle_medium_rcm():
+    m = _scrambled(20_000, 40, 30, 77)
+    _compare(m, 32, oan.ORDER_AUTO)
+
+
+def test_analyze_large_config_identity_matches_oracle():
+    m = inputs.config_large(0)
+    nt, tc, tr = otiles.plan(m["n"], m["colptr"], m["rowidx"], np.arange(m["n"]), 32)
+    plan = st.Plan.from_matrix(m, tile=32, ordering=st.ORDER_NONE)
+    tc2, tr2 = plan.tilemap()
+    assert np.array_equal(tc, tc2) and np.array_equal(tr, tr2)
+    assert plan.info()["flops_total"] == 40294113166  # oracle count at T = 32
+
+
+def test_rcm_library_equals_oracle_on_hand_cases():
+    # 3x3 grid: the hand-derived order of the oracle pins
+    edges = []
+    for x in range(3):
+        for y in range(3):
+            v = 3 * x + y
+            if x + 1 < 3:
+                edges.append((v, v + 3))
+            if y + 1 < 3:
+                edges.append((v, v + 1))
+    rows = [max(a, b) for a, b in edges] + list(range(9))
+    cols = [min(a, b) for a, b in edges] + list(range(9))
+    colptr, rowidx, _ = inputs.coo_to_csc_lower(9, rows, cols, np.ones(len(rows)))
+    plan = st.Plan(9, colptr, rowidx, 0, tile=2, ordering=st.ORDER_RCM)
+    assert plan.perm().tolist() == [8, 7, 5, 6, 4, 2, 3, 1, 0]
+    assert plan.perm().tolist() == oord.partial_rcm(9, colptr, rowidx, 0).tolist()
+
+
+def _bad(colptr, rowidx, n, n_arrow=0, tile=32):
+    with pytest.raises(st.StilesError) as e:
+        st.Plan(n, np.array(colptr), np.array(rowidx), n_arrow, tile=tile)
+    assert e.value.name == "INVALID"
+
+
+def test_invalid_inputs_are_rejected():
+    _bad([0, 1, 2], [0, 0], 2)          # column 1 lacks its diagonal (has row 0 < 1)
+    _bad([0, 2, 3], [1, 0, 1], 2)       # column 0 starts with row 1 (diagonal missing)
+    _bad([0, 3, 4, 5], [0, 2, 1, 1, 2], 3)  # rows of column 0 not ascending
+    _bad([0, 2, 3], [0, 1, 1], 2, n_arrow=3)
+    _bad([0, 2, 3], [0, 1, 1], 2, tile=0)
+    _bad([0, 2, 3], [0, 5, 1], 2)       # row out of range
+
+
+def test_plan_info_fields_are_consistent():
+    m = inputs.config_small(0)
+    plan = st.Plan.from_matrix(m, tile=64)
+    info = plan.info()
+    assert info["n"] == 2010 and info["nt"] == 32 and info["nnzt"] == 93
+    assert info["block"] == 32 and info["nsub"] == 93 * 4
+    assert info["factor_bytes"] == 93 * 64 * 64 * 8
+    assert info["flops_total"] == 29714265
