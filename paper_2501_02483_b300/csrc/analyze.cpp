@@ -669,7 +669,8 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       bp[q].out = int32_t(k);
       bp[q].diag = p->diag_sub[k];
       bp[q].col = int32_t(k);
-      for (size_t e = 1; e < scol[k].size(); ++e) {
+      // farthest block first: x_{k+1}, produced last, is consumed last
+      for (size_t e = scol[k].size(); e-- > 1;) {
         bp[q].pairs.push_back(scol[k][e].sub);
         bp[q].pairs.push_back(scol[k][e].idx);
         bp[q].producers.push_back(nsb - 1 - scol[k][e].idx);

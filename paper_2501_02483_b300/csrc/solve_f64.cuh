@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
         for (int s = 0; s < RP; ++s) acc[s][u] = 0.0;
     }
 
+    // the diagonal sub-tile does not depend on this sweep: fetch it first
+    if (tk.type == SOLVE_FINAL && tid == 0) {
+      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
+      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+    }
     const int npairs = tk.pe - tk.pb;
     const int nitems = npairs + (tk.qe - tk.qb);
     int issued = 0, stop = nitems;
@@ -217,6 +222,11 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
           while (!mbar_try_wait(&bars[st], (phase >> st) & 1u) && ++spins < kTmaWaitLimit) {
           }
         }
+        if (tk.type == SOLVE_FINAL) {
+          long long spins = 0;
+          while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u) && ++spins < kTmaWaitLimit) {
+          }
+        }
       }
       break;
     }
@@ -235,11 +245,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
       continue;
     }
 
-    // ---- triangular solve with the diagonal sub-tile (already final) ----
-    if (tid == 0) {
-      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
-      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
-    }
+    // ---- triangular solve with the diagonal sub-tile (prefetched above) ----
     if (tid < B) sInv[tid] = __ldcg(a.invdiag + size_t(tk.out) * B + tid);
     {
       long long spins = 0;
@@ -256,6 +262,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
       }
     }
     __syncthreads();
+    const int warp_grp0 = (tid & ~31) / W;  // first column group of this warp (warp-uniform guard)
     if (!BACKWARD) {
       // forward substitution: y_j = acc_j / L_jj, then acc_i -= L_ij y_j (i > j)
 #pragma unroll
@@ -264,6 +271,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
         const double inv = sInv[j];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+          if (warp_grp0 + G * u >= nr) break;
           double y = acc[sj][u] * inv;
           y = __shfl_sync(0xffffffffu, y, (tid & 31) - li + lj);
           if (li == lj) acc[sj][u] = y;
@@ -282,6 +290,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
         const double inv = sInv[j];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+          if (warp_grp0 + G * u >= nr) break;
           double x = acc[sj][u] * inv;
           x = __shfl_sync(0xffffffffu, x, (tid & 31) - li + lj);
           if (li == lj) acc[sj][u] = x;
