@@ -175,6 +175,27 @@ stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t*
 /* Number of CUDA kernels this library has launched in this process (all threads). */
 int64_t stiles_kernel_launches(void);
 
+/* log det A from factor tiles the caller already holds, allocating no device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- a process that has handed its whole HBM budget to its own pool or arena,
+ * or code running where a cudaMalloc would block the device or is not allowed.
+ *   tiles   : device, the T x T column-major tiles of L in tile-CSC order, as written by
+ *             stiles_factor_tiles (caller-owned).
+ *   tcolptr : device int64[ceil(n/T) + 1], the plan's tile column pointers (the diagonal tile of
+ *             column k is tile tcolptr[k]).
+ *   n, tile : matrix order and T.
+ *   out     : device double; receives 2 sum_i log L_ii once the stream reaches this work.
+ *   stream  : cudaStream_t as void* (NULL = legacy default stream); the call does not wait.
+ * Scratch is one static device array inside the library holding ceil(n/T) <= 65,536 partial
+ * sums (512 KB per device, held until the library is unloaded); larger problems return
+ * STILES_ERR_INVALID before any launch.  The first call on each device looks up that array's
+ * device address with the device current, so make it before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialized by the caller; each call rewrites all the entries it reads.  Errors:
+ * STILES_ERR_INVALID (null pointer, n < 1, tile < 1, too many tile columns), STILES_ERR_CUDA. */
+stiles_status stiles_logdet_tiles_noalloc(const double* tiles, const int64_t* tcolptr, int64_t n, int32_t tile,
+                                          double* out, void* stream);
+
 /* Measured FP64 DFMA throughput of the current device in TFLOP/s (a fixed-length FMA loop
  * on every SM, timed with CUDA events), used as the roofline denominator of the FP64 path. */
 stiles_status stiles_probe_fp64_peak(double* tflops);
