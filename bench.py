@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--ordering", choices=["none", "rcm", "auto"], default="auto")
+    ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="auto")
     ap.add_argument("--sweep", default="32,64,128,256,512", help="tile sizes timed briefly; '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=60_000)
@@ -192,7 +192,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build_library()
-    order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO}[args.ordering]
+    order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[args.ordering]
 
     m = workload(args, seed=rank)
     t0 = time.perf_counter()

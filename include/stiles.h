@@ -52,7 +52,7 @@ typedef enum {
   STILES_ERR_UNSUPPORTED = 7     /* option combination not built into this library           */
 } stiles_status;
 
-enum { STILES_ORDER_NONE = 0, STILES_ORDER_RCM = 1, STILES_ORDER_AUTO = 2 };
+enum { STILES_ORDER_NONE = 0, STILES_ORDER_RCM = 1, STILES_ORDER_AUTO = 2, STILES_ORDER_ND = 3 };
 enum { STILES_PREC_F64 = 0, STILES_PREC_BF16 = 1, STILES_PREC_F16 = 2 };
 
 typedef struct {
@@ -60,7 +60,11 @@ typedef struct {
                          multiple of 16.  Default 32.                                           */
   int32_t ordering;   /* STILES_ORDER_*: NONE keeps the input order, RCM applies partial RCM to
                          the band rows, AUTO keeps RCM only if it gives strictly fewer L tiles
-                         (Section III.A, closing rule).  Default AUTO.                          */
+                         (Section III.A, closing rule).  ND is one level of the adaptable nested
+                         dissection of Section III.A: a separator as wide as the bandwidth, cut
+                         at the middle of the band and moved to the end (ahead of the arrow),
+                         with the second part reversed; it adds a little fill and splits the
+                         elimination into two independent chains.  Default AUTO.                */
   int32_t precision;  /* STILES_PREC_*: arithmetic of the off-diagonal tile updates.  Default F64. */
   int32_t block;      /* B, the device sub-tile size: 16, 32 or 64 dividing T; 0 = min(T, 32).   */
   int32_t tree_chunk; /* accumulation terms per tree leaf (Algorithm 3); 0 = 32.  Tasks with more

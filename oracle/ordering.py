@@ -29,7 +29,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["body_graph", "level_structure", "pseudo_peripheral", "cuthill_mckee", "partial_rcm",
-           "identity_perm"]
+           "identity_perm", "adaptable_nd"]
 
 
 def identity_perm(n):
@@ -125,3 +125,33 @@ def partial_rcm(n, colptr, rowidx, n_arrow):
         seq.extend(cuthill_mckee(indptr, indices, deg, start, visited))
     body = np.array(seq[::-1], dtype=np.int64)
     return np.concatenate([body, np.arange(nb, n, dtype=np.int64)])
+
+
+def adaptable_nd(n, colptr, rowidx, n_arrow):
+    """One level of the adaptable nested dissection of Section III.A.
+
+    The paper's recipe: take a separator as wide as the bandwidth and move it
+    towards the end of the matrix, ahead of the arrow.  Reading used here:
+
+    * the body [0, nb) is split at mid = nb // 2;
+    * the separator S = [mid, s_end) holds every row that some body column
+      left of mid reaches: s_end = 1 + max{i : (i, j) stored, j < mid <= i < nb}
+      (S is empty when nothing crosses mid);
+    * new order: [0, mid), then [s_end, nb) reversed, then S, then the arrow.
+
+    Reversing the second part makes both parts touch the separator with their
+    last rows, so eliminating either part adds no fill between the separator
+    and the part's interior, and the two parts are independent chains.
+    """
+    nb = n - n_arrow
+    if nb < 2:
+        return identity_perm(n)
+    mid = nb // 2
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr))
+    rows = rowidx.astype(np.int64)
+    cross = (cols < mid) & (rows >= mid) & (rows < nb)
+    s_end = int(rows[cross].max()) + 1 if np.any(cross) else mid
+    left = np.arange(0, mid, dtype=np.int64)
+    right = np.arange(nb - 1, s_end - 1, -1, dtype=np.int64)
+    sep = np.arange(mid, s_end, dtype=np.int64)
+    return np.concatenate([left, right, sep, np.arange(nb, n, dtype=np.int64)])

@@ -149,6 +149,35 @@ std::vector<int64_t> partial_rcm(int64_t n, const int64_t* colptr, const int32_t
 }
 
 // ---------------------------------------------------------------------------
+// Adaptable nested dissection, one level (Section III.A): split the body at
+// mid = nb / 2, take as separator every row in [mid, nb) that a column left of
+// mid reaches, and order [0, mid), then the rest of the body reversed, then the
+// separator, then the arrow.  Both parts meet the separator with their last
+// rows, so they are independent elimination chains.
+// ---------------------------------------------------------------------------
+std::vector<int64_t> adaptable_nd(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow) {
+  const int64_t nb = n - n_arrow;
+  std::vector<int64_t> perm;
+  perm.reserve(n);
+  if (nb < 2) {
+    for (int64_t i = 0; i < n; ++i) perm.push_back(i);
+    return perm;
+  }
+  const int64_t mid = nb / 2;
+  int64_t s_end = mid;
+  for (int64_t j = 0; j < mid; ++j)
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+      const int64_t i = rowidx[e];
+      if (i >= mid && i < nb) s_end = std::max(s_end, i + 1);
+    }
+  for (int64_t i = 0; i < mid; ++i) perm.push_back(i);
+  for (int64_t i = nb - 1; i >= s_end; --i) perm.push_back(i);
+  for (int64_t i = mid; i < s_end; ++i) perm.push_back(i);
+  for (int64_t i = nb; i < n; ++i) perm.push_back(i);
+  return perm;
+}
+
+// ---------------------------------------------------------------------------
 // Tile map and tile-level symbolic factorization.  cols[J] = sorted rows I > J
 // of the present lower tiles of column J.  The closure follows the elimination
 // tree: the structure of tile column k (minus its first row p) is merged into
@@ -432,7 +461,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
                          const stiles_opts& opts_in, stiles_plan* p, std::string* err) {
   stiles_opts o = opts_in;
   if (o.tile < 1) { *err = "tile must be >= 1"; return STILES_ERR_INVALID; }
-  if (o.ordering < 0 || o.ordering > 2) { *err = "unknown ordering"; return STILES_ERR_INVALID; }
+  if (o.ordering < 0 || o.ordering > 3) { *err = "unknown ordering"; return STILES_ERR_INVALID; }
   if (o.precision < 0 || o.precision > 2) { *err = "unknown precision"; return STILES_ERR_INVALID; }
   if (o.tree_chunk <= 0) o.tree_chunk = 32;
   if (o.tree_fanin <= 1) o.tree_fanin = 16;
@@ -464,6 +493,12 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
     best_cols = tile_columns(n, colptr, rowidx, ident, T, nt);
     p->perm = ident;
     p->ordering_used = STILES_ORDER_NONE;
+  }
+  if (o.ordering == STILES_ORDER_ND) {
+    // chosen for parallelism (two independent chains), not by the fill rule
+    p->perm = adaptable_nd(n, colptr, rowidx, n_arrow);
+    best_cols = tile_columns(n, colptr, rowidx, invert(p->perm), T, nt);
+    p->ordering_used = STILES_ORDER_ND;
   }
   if (o.ordering == STILES_ORDER_RCM || o.ordering == STILES_ORDER_AUTO) {
     std::vector<int64_t> perm = partial_rcm(n, colptr, rowidx, n_arrow);
@@ -584,11 +619,23 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   for (int64_t g = n; g < nsb * B; ++g)
     p->pad.push_back(int64_t(p->diag_sub[nsb - 1]) * B * B + (g % B) * B + (g % B));
 
-  // factorization task graph: column-major primary tasks, DIAG then OFF
+  // Sub-columns in order of their elimination-tree level (leaves first), ties by
+  // index: a topological order in which independent subtrees (e.g. the two parts
+  // of a nested dissection) interleave, so their chains run at the same time.
+  std::vector<int64_t> level(nsb, 0), corder(nsb);
+  for (int64_t k = 0; k < nsb; ++k)
+    if (scol[k].size() > 1) {
+      const int64_t par = scol[k][1].idx;
+      level[par] = std::max(level[par], level[k] + 1);
+    }
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(), [&](int64_t a, int64_t b) { return level[a] < level[b]; });
+
+  // factorization task graph: columns in level order, DIAG then OFF
   std::vector<Primary> prim;
   prim.reserve(size_t(nsb) * 4);
   std::vector<int64_t> pos(p->nsub, -1);
-  for (int64_t k = 0; k < nsb; ++k) {
+  for (int64_t k : corder) {
     const auto& rk = srow[k];
     {
       Primary d;
@@ -644,17 +691,20 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
 
   // forward sweep: one task per sub-row, ascending
   {
+    std::vector<int64_t> rank(nsb);  // position of each block's task in the sweep
+    for (int64_t q = 0; q < nsb; ++q) rank[corder[q]] = q;
     std::vector<Primary> fp(nsb);
-    for (int64_t k = 0; k < nsb; ++k) {
-      fp[k].type = SOLVE_FINAL;
-      fp[k].out = int32_t(k);
-      fp[k].diag = p->diag_sub[k];
-      fp[k].col = int32_t(k);
+    for (int64_t q = 0; q < nsb; ++q) {
+      const int64_t k = corder[q];
+      fp[q].type = SOLVE_FINAL;
+      fp[q].out = int32_t(k);
+      fp[q].diag = p->diag_sub[k];
+      fp[q].col = int32_t(k);
       for (const SubEntry& en : srow[k]) {
         if (en.idx >= k) break;
-        fp[k].pairs.push_back(en.sub);
-        fp[k].pairs.push_back(en.idx);
-        fp[k].producers.push_back(en.idx);
+        fp[q].pairs.push_back(en.sub);
+        fp[q].pairs.push_back(en.idx);
+        fp[q].producers.push_back(rank[en.idx]);
       }
     }
     build_graph(fp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->fwd.tasks, p->fwd.pairs,
@@ -662,9 +712,11 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   }
   // backward sweep: one task per sub-column, descending
   {
+    std::vector<int64_t> rank(nsb);  // backward sweep: reverse level order
+    for (int64_t q = 0; q < nsb; ++q) rank[corder[nsb - 1 - q]] = q;
     std::vector<Primary> bp(nsb);
     for (int64_t q = 0; q < nsb; ++q) {
-      const int64_t k = nsb - 1 - q;
+      const int64_t k = corder[nsb - 1 - q];
       bp[q].type = SOLVE_FINAL;
       bp[q].out = int32_t(k);
       bp[q].diag = p->diag_sub[k];
@@ -673,7 +725,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       for (size_t e = scol[k].size(); e-- > 1;) {
         bp[q].pairs.push_back(scol[k][e].sub);
         bp[q].pairs.push_back(scol[k][e].idx);
-        bp[q].producers.push_back(nsb - 1 - scol[k][e].idx);
+        bp[q].producers.push_back(rank[scol[k][e].idx]);
       }
     }
     build_graph(bp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->bwd.tasks, p->bwd.pairs,

@@ -69,7 +69,7 @@ CASES = [
 
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("T", [1, 3, 16, 32, 64, 100])
-@pytest.mark.parametrize("order", [oan.ORDER_NONE, oan.ORDER_RCM, oan.ORDER_AUTO])
+@pytest.mark.parametrize("order", [oan.ORDER_NONE, oan.ORDER_RCM, oan.ORDER_AUTO, oan.ORDER_ND])
 def test_analyze_matches_oracle(name, make, T, order):
     _compare(make(T + 7 * order), T, order)
 
@@ -91,7 +91,7 @@ def test_analyze_matches_oracle_random_scrambled(seed):
     hw = int(rng.integers(1, 20))
     w = int(rng.integers(0, 8))
     T = int(rng.choice([1, 2, 5, 8, 16, 32, 48]))
-    order = int(rng.integers(0, 3))
+    order = int(rng.integers(0, 4))
     _compare(_scrambled(n, hw, w, seed), T, order)
 
 
@@ -150,3 +150,24 @@ def test_plan_info_fields_are_consistent():
     assert info["block"] == 32 and info["nsub"] == 93 * 4
     assert info["factor_bytes"] == 93 * 64 * 64 * 8
     assert info["flops_total"] == 29714265
+
+
+def test_analyze_large_config_nd_matches_oracle():
+    m = inputs.config_large(0)
+    p = oan.analyze(m, 16, oan.ORDER_ND)
+    plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_ND)
+    assert np.array_equal(plan.perm(), p["perm"])
+    tc, tr = plan.tilemap()
+    assert np.array_equal(tc, p["tcolptr"]) and np.array_equal(tr, p["trowidx"])
+
+
+def test_task_order_is_topological_and_interleaves_nd_parts():
+    """Tickets follow elimination-tree levels: with the adaptable ND the two
+    halves' diagonal tasks alternate instead of running one after the other."""
+    m = inputs.band_arrow(4000, 10, 20, 0.5, 2)
+    plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_ND)
+    tasks = plan.tasks(0)
+    diag_cols = tasks[tasks[:, 0] == 0, 3]
+    half = 2000 // 16
+    first = diag_cols[:40]
+    assert np.any(first < half) and np.any((first >= half) & (first < 2 * half))

@@ -131,3 +131,32 @@ def test_rcm_reduces_bandwidth_of_scrambled_band():
     bw_after = int(np.max(np.abs(inv[rowidx] - inv[cc])))
     assert bw_before > 100
     assert bw_after <= 15
+
+
+def test_adaptable_nd_on_a_path():
+    # path 0..9, mid = 5: separator {5} (column 4 reaches row 5); right part 9..6 reversed
+    n, colptr, rowidx = _graph_matrix(10, [(i, i + 1) for i in range(9)], n_arrow=2)
+    perm = ordering.adaptable_nd(n, colptr, rowidx, 2).tolist()
+    assert perm == [0, 1, 2, 3, 4, 9, 8, 7, 6, 5, 10, 11]
+
+
+def test_adaptable_nd_band_separator_width_and_independence():
+    m = inputs.band_arrow(1000, 7, 12, 1.0, 0)  # full band of half-width 12
+    perm = ordering.adaptable_nd(m["n"], m["colptr"], m["rowidx"], 7)
+    assert sorted(perm.tolist()) == list(range(m["n"]))
+    # separator = rows 500..511 (12 rows), just before the arrow
+    assert perm[1000 - 12:1000].tolist() == list(range(500, 512))
+    # no stored entry joins the two parts
+    inv = np.empty(m["n"], dtype=int)
+    inv[perm] = np.arange(m["n"])
+    cols = np.repeat(np.arange(m["n"]), np.diff(m["colptr"]))
+    r, c = inv[m["rowidx"]], inv[cols]
+    body = (r < 1000 - 12) & (c < 1000 - 12)
+    part = lambda x: x >= 500
+    assert not np.any(body & (part(r) != part(c)))
+
+
+def test_adaptable_nd_no_crossing_entries():
+    # two disconnected blocks: nothing crosses mid, separator empty
+    n, colptr, rowidx = _graph_matrix(8, [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 7)])
+    assert ordering.adaptable_nd(n, colptr, rowidx, 0).tolist() == [0, 1, 2, 3, 7, 6, 5, 4]
