@@ -48,7 +48,7 @@ METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set res
 # profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
 # changed after the capture.
 TRAFFIC = {("factor_f64_v2", 16, 16): 1.285e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
-KERNEL_TAG = "factor_f64_v2"
+KERNEL_TAG = "factor_f64_v4"
 
 
 def parse():
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="auto")
+    ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="nd")
     ap.add_argument("--sweep", default="32,64,128,256,512", help="tile sizes timed briefly; '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=60_000)

@@ -71,7 +71,8 @@ typedef struct {
                          terms are split into leaves summed by a fixed-shape tree.               */
   int32_t tree_fanin; /* partial tiles summed per tree node; 0 = 16.                             */
   int32_t max_refine; /* iterative-refinement steps for low-precision factors; default 20.      */
-  int32_t reserved0;
+  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent kernels; 0 = as many as fit.  Fewer
+                         CTAs leave the critical-path task more of its SM's FP64 pipes.          */
   double refine_tol;  /* target ||b - A x||_2 / ||b||_2 of a refined solve; default 1e-10.       */
   int64_t spin_limit; /* bound on any device wait, in polling iterations; default 2^24 (about 16 s).         */
 } stiles_opts;
@@ -171,9 +172,12 @@ stiles_status stiles_factor_timing(const stiles_factor* factor, double* ms_call,
 stiles_status stiles_factor_set_trace(stiles_factor* factor, int32_t enable);
 stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which, int64_t* out, int64_t* ntasks);
 
-/* The device task list of a plan (which: 0 factorization, 1 forward, 2 backward sweep), 8 int32
- * per task in ticket order: type, output, diagonal sub-tile, column, pair range [pb, pe),
- * partial range [qb, qe).  out may be NULL to query ntasks. */
+/* The device task list of a plan (which: 0 factorization, 1 forward, 2 backward sweep) in ticket
+ * order.  Factorization tasks are 16 int32: type (0 DIAG, 1 OFF, 2 tree leaf, 3 tree node,
+ * 4 CHAIN), output, diagonal sub-tile, column, pair range [pb, pe), partial range [qb, qe),
+ * second output, its column, its pair range, its partial range, 2 unused.  Solve tasks are
+ * 8 int32: type (0 block, 2 leaf, 3 node), output block, diagonal sub-tile, column, pair
+ * range, partial range.  out may be NULL to query ntasks. */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */

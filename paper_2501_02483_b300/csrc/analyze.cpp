@@ -249,6 +249,9 @@ struct TreeNode {
   int64_t owner;       // leaf: primary task whose pairs it sums
 };
 
+constexpr int kTargetShift = 30;  // bit of a pair/partial index naming the CHAIN accumulator
+constexpr int32_t kIndexMask = (1 << 30) - 1;
+
 inline void set_col(DevTask& t, int32_t c) { t.col = c; }
 inline void set_col(SolveTask& t, int32_t c) { t.pad0 = c; }
 
@@ -263,11 +266,31 @@ inline void set_col(SolveTask& t, int32_t c) { t.pad0 = c; }
 // ---------------------------------------------------------------------------
 namespace {
 
+struct PairList {
+  std::vector<int32_t> pairs;      // 2 per pair
+  std::vector<int64_t> producers;  // per pair: max primary position of the two producers
+};
+
 struct Primary {
   int32_t type, out, diag, col;
-  std::vector<int32_t> pairs;     // 2 per pair
-  std::vector<int64_t> producers; // per pair: max primary position of the two producers
+  int32_t out2 = -1, col2 = -1;    // CHAIN: second output
+  PairList list[2];                // list[1] only for CHAIN
 };
+
+inline void set_second(DevTask& t, const Primary& p, int32_t pb, int32_t pe, int32_t qb, int32_t qe) {
+  t.out2 = p.out2;
+  t.col2 = p.col2;
+  t.pb2 = pb;
+  t.pe2 = pe;
+  t.qb2 = qb;
+  t.qe2 = qe;
+}
+inline void set_second(SolveTask&, const Primary&, int32_t, int32_t, int32_t, int32_t) {}
+inline void clear_second(DevTask& t) {
+  t.out2 = t.col2 = -1;
+  t.pb2 = t.pe2 = t.qb2 = t.qe2 = 0;
+}
+inline void clear_second(SolveTask&) {}
 
 template <class Task>
 void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32_t leaf_type, int32_t comb_type,
@@ -275,54 +298,62 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
                  int64_t& nscratch) {
   const int64_t np = int64_t(prim.size());
   std::vector<TreeNode> nodes;
-  std::vector<std::vector<int32_t>> roots(np);      // per primary: its top-level tree nodes
-  std::vector<std::vector<int32_t>> by_release(np); // leaves by release position
+  std::vector<int32_t> node_list;                     // which list of its owner a node belongs to
+  std::vector<std::vector<int32_t>> roots(2 * np);    // per (primary, list): top-level tree nodes
+  std::vector<std::vector<int32_t>> by_release(np);   // leaves by release position
   std::vector<int32_t> parent;
   std::vector<int32_t> pending;
-  std::vector<int64_t> own_begin(np, 0);
-  for (int64_t t = 0; t < np; ++t) {
-    const int64_t npairs = int64_t(prim[t].pairs.size() / 2);
-    if (npairs <= chunk) continue;
-    const int64_t nchunks = (npairs + chunk - 1) / chunk;
-    std::vector<int32_t> level;
-    for (int64_t c = 0; c + 1 < nchunks; ++c) {
-      TreeNode nd;
-      nd.type = leaf_type;
-      nd.scratch = int32_t(nscratch++);
-      nd.pb = c * chunk;
-      nd.pe = (c + 1) * chunk;
-      int64_t rel = 0;
-      for (int64_t q = nd.pb; q < nd.pe; ++q) rel = std::max(rel, prim[t].producers[q]);
-      nd.release = rel;
-      level.push_back(int32_t(nodes.size()));
-      by_release[rel].push_back(int32_t(nodes.size()));
-      nd.owner = t;
-      nodes.push_back(nd);
-      parent.push_back(-1);
-      pending.push_back(0);
-    }
-    own_begin[t] = (nchunks - 1) * chunk;
-    while (int64_t(level.size()) > fanin) {
-      std::vector<int32_t> next;
-      for (size_t g = 0; g < level.size(); g += size_t(fanin)) {
+  std::vector<int64_t> own_begin(2 * np, 0);
+  for (int64_t t = 0; t < np; ++t)
+    for (int l = 0; l < 2; ++l) {
+      const PairList& pl = prim[t].list[l];
+      const int64_t npairs = int64_t(pl.pairs.size() / 2);
+      if (npairs <= chunk) continue;
+      const int64_t nchunks = (npairs + chunk - 1) / chunk;
+      std::vector<int32_t> level;
+      for (int64_t c = 0; c + 1 < nchunks; ++c) {
         TreeNode nd;
-        nd.type = comb_type;
+        nd.type = leaf_type;
         nd.scratch = int32_t(nscratch++);
-        nd.pb = nd.pe = 0;
-        nd.release = -1;
+        nd.pb = c * chunk;
+        nd.pe = (c + 1) * chunk;
+        int64_t rel = 0;
+        for (int64_t q = nd.pb; q < nd.pe; ++q) rel = std::max(rel, pl.producers[q]);
+        nd.release = rel;
         nd.owner = t;
-        size_t e = std::min(level.size(), g + size_t(fanin));
-        int32_t id = int32_t(nodes.size());
-        for (size_t q = g; q < e; ++q) { nd.children.push_back(level[q]); parent[level[q]] = id; }
+        level.push_back(int32_t(nodes.size()));
+        by_release[rel].push_back(int32_t(nodes.size()));
         nodes.push_back(nd);
+        node_list.push_back(l);
         parent.push_back(-1);
-        pending.push_back(int32_t(e - g));
-        next.push_back(id);
+        pending.push_back(0);
       }
-      level.swap(next);
+      own_begin[2 * t + l] = (nchunks - 1) * chunk;
+      while (int64_t(level.size()) > fanin) {
+        std::vector<int32_t> next;
+        for (size_t g = 0; g < level.size(); g += size_t(fanin)) {
+          TreeNode nd;
+          nd.type = comb_type;
+          nd.scratch = int32_t(nscratch++);
+          nd.pb = nd.pe = 0;
+          nd.release = -1;
+          nd.owner = t;
+          const size_t e = std::min(level.size(), g + size_t(fanin));
+          const int32_t id = int32_t(nodes.size());
+          for (size_t q = g; q < e; ++q) {
+            nd.children.push_back(level[q]);
+            parent[level[q]] = id;
+          }
+          nodes.push_back(nd);
+          node_list.push_back(l);
+          parent.push_back(-1);
+          pending.push_back(int32_t(e - g));
+          next.push_back(id);
+        }
+        level.swap(next);
+      }
+      roots[2 * t + l] = level;
     }
-    roots[t] = level;
-  }
   // emission
   tasks.clear();
   pairs.clear();
@@ -335,10 +366,11 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
     tk.type = nd.type;
     tk.out = nd.scratch;
     tk.diag = -1;
+    clear_second(tk);
     if (nd.type == leaf_type) {
-      const Primary& pr = prim[nd.owner];
+      const PairList& pl = prim[nd.owner].list[node_list[id]];
       tk.pb = int32_t(pairs.size() / 2);
-      pairs.insert(pairs.end(), pr.pairs.begin() + 2 * nd.pb, pr.pairs.begin() + 2 * nd.pe);
+      pairs.insert(pairs.end(), pl.pairs.begin() + 2 * nd.pb, pl.pairs.begin() + 2 * nd.pe);
       tk.pe = int32_t(pairs.size() / 2);
       tk.qb = tk.qe = int32_t(parts.size());
     } else {
@@ -350,31 +382,55 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
     ticket_of_node[id] = int64_t(tasks.size());
     tasks.push_back(tk);
   };
+  // The primary's own terms of both lists are merged in the order their producers
+  // run, each tagged with its target accumulator (bit 30 of the first index), so a
+  // late term never holds back terms that are ready; tree roots (older sums) and
+  // own terms share that encoding.
+  struct OwnItem {
+    int64_t prod;
+    int32_t a, b;
+  };
+  std::vector<OwnItem> own;
   for (int64_t t = 0; t < np; ++t) {
     Primary& pr = prim[t];
     Task tk{};
     tk.type = pr.type;
     tk.out = pr.out;
     tk.diag = pr.diag;
+    own.clear();
+    const int nl = pr.out2 >= 0 ? 2 : 1;
+    for (int l = 0; l < nl; ++l) {
+      const PairList& pl = pr.list[l];
+      for (size_t q = size_t(own_begin[2 * t + l]); q < pl.producers.size(); ++q)
+        own.push_back(OwnItem{pl.producers[q], pl.pairs[2 * q] | (l << kTargetShift), pl.pairs[2 * q + 1]});
+    }
+    if (nl == 2)
+      std::stable_sort(own.begin(), own.end(), [](const OwnItem& x, const OwnItem& y) { return x.prod < y.prod; });
     tk.pb = int32_t(pairs.size() / 2);
-    pairs.insert(pairs.end(), pr.pairs.begin() + 2 * own_begin[t], pr.pairs.end());
+    for (const OwnItem& it : own) {
+      pairs.push_back(it.a);
+      pairs.push_back(it.b);
+    }
     tk.pe = int32_t(pairs.size() / 2);
     tk.qb = int32_t(parts.size());
-    for (int32_t r : roots[t]) {
-      if (ticket_of_node[r] < 0) throw std::logic_error("tree root emitted after its owner");
-      parts.push_back(nodes[r].scratch);
-    }
+    for (int l = 0; l < nl; ++l)
+      for (int32_t r : roots[2 * t + l]) {
+        if (ticket_of_node[r] < 0) throw std::logic_error("tree root emitted after its owner");
+        parts.push_back(nodes[r].scratch | (l << kTargetShift));
+      }
     tk.qe = int32_t(parts.size());
+    if (pr.out2 >= 0) set_second(tk, pr, 0, 0, 0, 0);
+    else clear_second(tk);
     set_col(tk, pr.col);
     tasks.push_back(tk);
     // leaves released by this primary, then any combine that became complete
     for (int32_t leaf : by_release[t]) {
       stack.assign(1, leaf);
       while (!stack.empty()) {
-        int32_t id = stack.back();
+        const int32_t id = stack.back();
         stack.pop_back();
         emit_node(id);
-        int32_t p = parent[id];
+        const int32_t p = parent[id];
         if (p >= 0 && --pending[p] == 0) stack.push_back(p);
       }
     }
@@ -414,6 +470,12 @@ std::vector<int64_t> invert(const std::vector<int64_t>& perm) {
   return inv;
 }
 
+struct Second {
+  int32_t out = -1, pb = 0, pe = 0, qb = 0, qe = 0;
+};
+inline Second second_of(const DevTask& t) { return Second{t.out2, t.pb2, t.pe2, t.qb2, t.qe2}; }
+inline Second second_of(const SolveTask&) { return Second{}; }
+
 // Ticket-order check: the producer of every tile (or block) a task reads must
 // have a smaller ticket.  For solve graphs the second member of a pair is a
 // block index; for the factorization both members are sub-tile indices.
@@ -429,12 +491,16 @@ bool check_order(const std::vector<Task>& tasks, const std::vector<int32_t>& pai
     } else {
       if (tk.out < 0 || tk.out >= nout || tout[tk.out] >= 0) { *err = "internal: bad task output"; return false; }
       tout[tk.out] = int64_t(t);
+      const Second s2 = second_of(tk);
+      if (s2.out >= 0) {
+        if (s2.out >= nout || tout[s2.out] >= 0) { *err = "internal: bad second output"; return false; }
+        tout[s2.out] = int64_t(t);
+      }
     }
   }
-  for (size_t t = 0; t < tasks.size(); ++t) {
-    const Task& tk = tasks[t];
-    for (int32_t q = tk.pb; q < tk.pe; ++q) {
-      const int64_t a = pairs[2 * size_t(q)], b = pairs[2 * size_t(q) + 1];
+  auto check_range = [&](size_t t, int32_t pb, int32_t pe, int32_t qb, int32_t qe) {
+    for (int32_t q = pb; q < pe; ++q) {
+      const int64_t a = pairs[2 * size_t(q)] & kIndexMask, b = pairs[2 * size_t(q) + 1];
       const int64_t ta = solve ? -2 : tout[a];
       const int64_t tb = tout[b];
       if ((!solve && (ta < 0 || ta >= int64_t(t))) || tb < 0 || tb >= int64_t(t)) {
@@ -442,9 +508,23 @@ bool check_order(const std::vector<Task>& tasks, const std::vector<int32_t>& pai
         return false;
       }
     }
-    for (int32_t q = tk.qb; q < tk.qe; ++q) {
-      const int64_t ts = tscr[parts[q]];
-      if (ts < 0 || ts >= int64_t(t)) { *err = "internal: partial produced later"; return false; }
+    for (int32_t q = qb; q < qe; ++q) {
+      const int64_t ts = tscr[parts[q] & kIndexMask];
+      if (ts < 0 || ts >= int64_t(t)) {
+        *err = "internal: partial produced later";
+        return false;
+      }
+    }
+    return true;
+  };
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    const Task& tk = tasks[t];
+    if (!check_range(t, tk.pb, tk.pe, tk.qb, tk.qe)) return false;
+    const Second s2 = second_of(tk);
+    if (s2.out >= 0 && !check_range(t, s2.pb, s2.pe, s2.qb, s2.qe)) return false;
+    if (!solve && tk.diag >= 0 && (tout[tk.diag] < 0 || tout[tk.diag] >= int64_t(t))) {
+      *err = "internal: diagonal tile produced later";
+      return false;
     }
   }
   return true;
@@ -570,7 +650,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   const int64_t nsb = (n + B - 1) / B;
   p->nsb = nsb;
   p->nsub = p->nnzt * R * R;
-  if (p->nsub >= (int64_t(1) << 31)) { *err = "too many sub-tiles"; return STILES_ERR_UNSUPPORTED; }
+  if (p->nsub >= (int64_t(1) << 30)) { *err = "too many sub-tiles"; return STILES_ERR_UNSUPPORTED; }
 
   auto tile_index = [&](int64_t I, int64_t J) -> int64_t {
     if (I == J) return p->tcolptr[J];
@@ -637,7 +717,40 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   std::vector<int64_t> pos(p->nsub, -1);
   for (int64_t k : corder) {
     const auto& rk = srow[k];
-    {
+    // Chain step: when tile (k, k-1) exists, its TRSM and the SYRK term it feeds
+    // into (k, k) run in the same task as POTRF(k) (no flag handoff in between).
+    const bool chained = k > 0 && rk.size() >= 2 && rk[rk.size() - 2].idx == k - 1;
+    if (chained) {
+      const auto& rp = srow[k - 1];
+      Primary c;
+      c.type = TASK_CHAIN;
+      c.out = rk[rk.size() - 2].sub;  // (k, k-1)
+      c.diag = p->diag_sub[k - 1];
+      c.col = int32_t(k - 1);
+      c.out2 = p->diag_sub[k];
+      c.col2 = int32_t(k);
+      size_t a2 = 0, b2 = 0;  // OFF part: n < k-1 common to rows k and k-1
+      while (a2 < rk.size() && b2 < rp.size()) {
+        if (rk[a2].idx >= k - 1 || rp[b2].idx >= k - 1) break;
+        if (rk[a2].idx < rp[b2].idx) ++a2;
+        else if (rp[b2].idx < rk[a2].idx) ++b2;
+        else {
+          c.list[0].pairs.push_back(rk[a2].sub);
+          c.list[0].pairs.push_back(rp[b2].sub);
+          c.list[0].producers.push_back(std::max(pos[rk[a2].sub], pos[rp[b2].sub]));
+          ++a2;
+          ++b2;
+        }
+      }
+      for (const SubEntry& en : rk) {  // DIAG part: n < k-1 (n = k-1 is applied in the task)
+        if (en.idx >= k - 1) break;
+        c.list[1].pairs.push_back(en.sub);
+        c.list[1].pairs.push_back(en.sub);
+        c.list[1].producers.push_back(pos[en.sub]);
+      }
+      pos[c.out] = pos[c.out2] = int64_t(prim.size());
+      prim.push_back(std::move(c));
+    } else {
       Primary d;
       d.type = TASK_DIAG;
       d.out = p->diag_sub[k];
@@ -645,15 +758,16 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       d.col = int32_t(k);
       for (const SubEntry& en : rk) {
         if (en.idx >= k) break;
-        d.pairs.push_back(en.sub);
-        d.pairs.push_back(en.sub);
-        d.producers.push_back(pos[en.sub]);
+        d.list[0].pairs.push_back(en.sub);
+        d.list[0].pairs.push_back(en.sub);
+        d.list[0].producers.push_back(pos[en.sub]);
       }
       pos[d.out] = int64_t(prim.size());
       prim.push_back(std::move(d));
     }
     for (size_t e = 1; e < scol[k].size(); ++e) {
       const int64_t i = scol[k][e].idx;
+      if (i == k + 1) continue;  // tile (k+1, k) belongs to the chain step of column k+1
       Primary o2;
       o2.type = TASK_OFF;
       o2.out = scol[k][e].sub;
@@ -666,9 +780,9 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
         if (ri[a].idx < rk[c].idx) ++a;
         else if (rk[c].idx < ri[a].idx) ++c;
         else {
-          o2.pairs.push_back(ri[a].sub);
-          o2.pairs.push_back(rk[c].sub);
-          o2.producers.push_back(std::max(pos[ri[a].sub], pos[rk[c].sub]));
+          o2.list[0].pairs.push_back(ri[a].sub);
+          o2.list[0].pairs.push_back(rk[c].sub);
+          o2.list[0].producers.push_back(std::max(pos[ri[a].sub], pos[rk[c].sub]));
           ++a;
           ++c;
         }
@@ -678,8 +792,9 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
     }
   }
   for (const auto& pr : prim)
-    for (int64_t q : pr.producers)
-      if (q < 0) { *err = "internal: producer missing"; return STILES_ERR_INVALID; }
+    for (int l = 0; l < 2; ++l)
+      for (int64_t q : pr.list[l].producers)
+        if (q < 0) { *err = "internal: producer missing"; return STILES_ERR_INVALID; }
   try {
     build_graph(prim, o.tree_chunk, o.tree_fanin, TASK_PARTIAL, TASK_COMBINE, p->graph.tasks, p->graph.pairs,
                 p->graph.parts, p->graph.nscratch);
@@ -702,9 +817,9 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       fp[q].col = int32_t(k);
       for (const SubEntry& en : srow[k]) {
         if (en.idx >= k) break;
-        fp[q].pairs.push_back(en.sub);
-        fp[q].pairs.push_back(en.idx);
-        fp[q].producers.push_back(rank[en.idx]);
+        fp[q].list[0].pairs.push_back(en.sub);
+        fp[q].list[0].pairs.push_back(en.idx);
+        fp[q].list[0].producers.push_back(rank[en.idx]);
       }
     }
     build_graph(fp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->fwd.tasks, p->fwd.pairs,
@@ -723,14 +838,15 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       bp[q].col = int32_t(k);
       // farthest block first: x_{k+1}, produced last, is consumed last
       for (size_t e = scol[k].size(); e-- > 1;) {
-        bp[q].pairs.push_back(scol[k][e].sub);
-        bp[q].pairs.push_back(scol[k][e].idx);
-        bp[q].producers.push_back(rank[scol[k][e].idx]);
+        bp[q].list[0].pairs.push_back(scol[k][e].sub);
+        bp[q].list[0].pairs.push_back(scol[k][e].idx);
+        bp[q].list[0].producers.push_back(rank[scol[k][e].idx]);
       }
     }
     build_graph(bp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->bwd.tasks, p->bwd.pairs,
                 p->bwd.parts, p->bwd.nscratch);
   }
+  if (p->graph.nscratch >= (int64_t(1) << 30)) { *err = "too many tree partials"; return STILES_ERR_UNSUPPORTED; }
   // every dependency must carry a smaller ticket, or the persistent kernels could wait forever
   if (!check_order(p->graph.tasks, p->graph.pairs, p->graph.parts, p->nsub, p->graph.nscratch, TASK_PARTIAL,
                    TASK_COMBINE, false, err) ||

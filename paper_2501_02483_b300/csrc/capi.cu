@@ -204,6 +204,10 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
   if (fb < 1 || sb < 1) return fail(STILES_ERR_UNSUPPORTED, "kernel does not fit on an SM");
+  if (p->opts.ctas_per_sm > 0) {
+    fb = std::min(fb, int(p->opts.ctas_per_sm));
+    sb = std::min(sb, int(p->opts.ctas_per_sm));
+  }
   d->grid_factor = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(fb) * sms, d->fac.ntasks)));
   d->grid_solve = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sb) * sms, std::max(d->fwd.ntasks, d->bwd.ntasks))));
   return STILES_OK;
@@ -664,7 +668,8 @@ stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* ou
   else if (which == 1) { src = p->fwd.tasks.data(); n = p->fwd.tasks.size(); }
   else { src = p->bwd.tasks.data(); n = p->bwd.tasks.size(); }
   if (ntasks) *ntasks = int64_t(n);
-  if (out && n) std::memcpy(out, src, n * 8 * sizeof(int32_t));
+  const size_t width = which == 0 ? sizeof(DevTask) : sizeof(SolveTask);
+  if (out && n) std::memcpy(out, src, n * width);
   return STILES_OK;
 }
 

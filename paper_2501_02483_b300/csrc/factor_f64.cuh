@@ -6,6 +6,8 @@
 //
 //   DIAG     A_kk -= sum L_kn L_kn^T (+ tree partials), then POTRF
 //   OFF      A_mk -= sum L_mn L_kn^T (+ tree partials), then TRSM with L_kk
+//   CHAIN    OFF(k, k-1) and DIAG(k) together: TRSM of (k, k-1), publish it,
+//            apply its SYRK term to (k, k) from shared memory, POTRF(k)
 //   PARTIAL  S = -sum of a chunk of L_an L_bn^T       (tree leaf, Algorithm 3)
 //   COMBINE  S = sum of child partials                 (tree node, GEADD)
 //
@@ -30,9 +32,14 @@ struct FactorCfg {
   static constexpr int CPT = B / RPT; // columns per thread
   static constexpr int TILE = B * B;
   static constexpr int NSTAGE = (B == 64) ? 2 : 3;
-  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 2 * B;
+  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 3 * B;
   static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
+
+// Bit 30 of a pair's first index / of a partial index selects the accumulator
+// of a CHAIN task (0: the off-diagonal tile, 1: the diagonal tile).
+constexpr int kTargetShift = 30;
+constexpr int kIndexMask = (1 << 30) - 1;
 
 struct FactorArgs {
   double* tiles;    // nsub * B * B, sub-tile s at s * B * B, column-major
@@ -57,6 +64,95 @@ __device__ __forceinline__ void publish(int* flag) {
   if (threadIdx.x == 0) st_release(flag, 1);
 }
 
+// POTRF of the tile held in `acc` (row-quad layout), in place, using sC as the
+// shared copy of the unscaled columns.  Right-looking: step j subtracts
+// a_ij a_cj / d_j from every (i, c) with j < c <= i; the owner of the next
+// pivot publishes it and its reciprocal, so each step costs one barrier.
+// The reciprocal square roots of the pivots (for the final scaling) are taken
+// by a warp other than the next pivot's owner, off the dependency chain.
+// Returns the first bad pivot (<= 0 or NaN) or -1; sInv receives 1/L_jj.
+template <int B>
+__device__ __forceinline__ int potrf_tile(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
+                                          double* sRs, int row, int q, int tid) {
+  constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
+  constexpr int RPW = 32 / RPT;  // tile rows per warp
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
+  __syncthreads();
+  if (tid == 0) {
+    const double d = sC[0];
+    sPiv[0] = d;
+    sInv[0] = 1.0 / d;
+  }
+  __syncthreads();
+  int bad = -1;
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    const double d = sPiv[j];
+    // d > 0 and not NaN, tested on the bit pattern (an FP64 compare would occupy
+    // the FP64 pipe on the dependency chain): positive, at most +inf
+    const long long bits = __double_as_longlong(d);
+    if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) { bad = j; break; }
+    if (lane == 0 && warp == (((j + 1) / RPW) + 2) % 4) sRs[j] = rsqrt(d);
+    const double tr = sC[row + j * B] * sInv[j];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      if (c > j && c <= row) acc[m] = fma(-tr, sC[c + j * B], acc[m]);
+    }
+    if (j + 1 < B) {
+      const int cn = j + 1;
+      if (q == cn % RPT && row >= cn) {
+        const double v = acc[cn / RPT];
+        sC[row + cn * B] = v;
+        if (row == cn) {
+          sPiv[cn] = v;
+          sInv[cn] = 1.0 / v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (bad >= 0) {
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = nanv;
+    if (tid < B) sInv[tid] = nanv;
+  } else {
+    // L_ic = a_ic * rsqrt(d_c) below the diagonal, L_cc = d_c * rsqrt(d_c)
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      acc[m] = (c <= row) ? acc[m] * sRs[c] : 0.0;
+    }
+    if (tid < B) sInv[tid] = sRs[tid];
+  }
+  __syncthreads();
+  return bad;
+}
+
+// X L^T = acc, column by column (inv = 1/L_jj of this thread's columns); the
+// solved x_ij is broadcast to the row's RPT lanes with a shuffle.
+template <int B>
+__device__ __forceinline__ void trsm_rows(double (&acc)[FactorCfg<B>::CPT], const double (&inv)[FactorCfg<B>::CPT],
+                                          const double* sL, int q, int row_lane0) {
+  constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    const int mj = j / RPT;
+    const bool owner = (q == j % RPT);
+    double x = owner ? acc[mj] * inv[mj] : 0.0;
+    x = __shfl_sync(0xffffffffu, x, row_lane0 + (j % RPT));
+    if (owner) acc[mj] = x;
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      if (c > j) acc[m] = fma(-x, sL[c + j * B], acc[m]);
+    }
+  }
+}
+
 template <int B>
 __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   using Cfg = FactorCfg<B>;
@@ -67,7 +163,8 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   double* sL = sC + TILE;
   double* sInv = sL + TILE;
   double* sPiv = sInv + B;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sPiv + B);
+  double* sRs = sPiv + B;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sRs + B);
   __shared__ int sTicket, sAbort;
 
   const int tid = threadIdx.x;
@@ -108,20 +205,32 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       trace[0] = (long long)t_ready;
       trace[3] = smid();
     }
+    const bool chain = tk.type == TASK_CHAIN;
 
-    double acc[CPT];
-    if (tk.type == TASK_DIAG || tk.type == TASK_OFF) {
+    // accumulators: acc1 for `out`, acc2 for `out2` (CHAIN only)
+    double acc1[CPT], acc2[CPT];
+    if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) {
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) acc1[m] = 0.0;
+    } else {
       const double* src = a.tiles + size_t(tk.out) * TILE;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) acc[m] = src[(q + RPT * m) * B + row];
+      for (int m = 0; m < CPT; ++m) acc1[m] = src[(q + RPT * m) * B + row];
+    }
+    if (chain) {
+      const double* src = a.tiles + size_t(tk.out2) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) acc2[m] = src[(q + RPT * m) * B + row];
     } else {
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) acc[m] = 0.0;
+      for (int m = 0; m < CPT; ++m) acc2[m] = 0.0;
     }
 
-    // ---- operand pipeline: pairs [pb, pe), then partial tiles [qb, qe) ----
-    const int npairs = tk.pe - tk.pb;
-    const int nitems = npairs + (tk.qe - tk.qb);
+    // ---- operand pipeline: partial tiles [qb, qe) (older sums) first, then pairs
+    // [pb, pe) in the order their producers run; bit 30 of the first index names
+    // the accumulator (acc2 = the diagonal tile of a CHAIN task) ----
+    const int nq = tk.qe - tk.qb;
+    const int nitems = nq + (tk.pe - tk.pb);
     int issued = 0, stop = nitems;
     bool aborted = false;
     for (int it = 0; it < nitems; ++it) {
@@ -132,19 +241,20 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
           const int* f2 = nullptr;
           const double* g1;
           const double* g2 = nullptr;
-          if (issued < npairs) {
-            const int pa = a.pairs[2 * (tk.pb + issued)];
-            const int pb = a.pairs[2 * (tk.pb + issued) + 1];
+          if (issued < nq) {
+            const int s = a.parts[tk.qb + issued] & kIndexMask;
+            f1 = a.sflags + s;
+            g1 = a.scratch + size_t(s) * TILE;
+          } else {
+            const int pidx = tk.pb + issued - nq;
+            const int pa = a.pairs[2 * pidx] & kIndexMask;
+            const int pb = a.pairs[2 * pidx + 1];
             f1 = a.flags + pa;
             g1 = a.tiles + size_t(pa) * TILE;
             if (pb != pa) {
               f2 = a.flags + pb;
               g2 = a.tiles + size_t(pb) * TILE;
             }
-          } else {
-            const int s = a.parts[tk.qb + issued - npairs];
-            f1 = a.sflags + s;
-            g1 = a.scratch + size_t(s) * TILE;
           }
           if (issued == it) {
             if (!(wait_flag(f1, 1, limit, a.ctl) && (f2 == nullptr || wait_flag(f2, 1, limit, a.ctl)))) {
@@ -177,18 +287,33 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       if (aborted) { stop = it; break; }
       phase ^= (1u << st);
       const double* sA = sStage + st * 2 * TILE;
-      if (it < npairs) {
-        const int pa = a.pairs[2 * (tk.pb + it)], pb = a.pairs[2 * (tk.pb + it) + 1];
-        const double* sB = (pa == pb) ? sA : sA + TILE;
-#pragma unroll 4
-        for (int p = 0; p < B; ++p) {
-          const double av = sA[row + p * B];
+      if (it < nq) {
+        if ((a.parts[tk.qb + it] >> kTargetShift) == 0) {
 #pragma unroll
-          for (int m = 0; m < CPT; ++m) acc[m] = fma(-av, sB[q + RPT * m + p * B], acc[m]);
+          for (int m = 0; m < CPT; ++m) acc1[m] += sA[row + (q + RPT * m) * B];
+        } else {
+#pragma unroll
+          for (int m = 0; m < CPT; ++m) acc2[m] += sA[row + (q + RPT * m) * B];
         }
       } else {
+        const int pidx = tk.pb + it - nq;
+        const int raw = a.pairs[2 * pidx];
+        const double* sB = ((raw & kIndexMask) == a.pairs[2 * pidx + 1]) ? sA : sA + TILE;
+        if ((raw >> kTargetShift) == 0) {
+#pragma unroll 4
+          for (int p = 0; p < B; ++p) {
+            const double av = sA[row + p * B];
 #pragma unroll
-        for (int m = 0; m < CPT; ++m) acc[m] += sA[row + (q + RPT * m) * B];
+            for (int m = 0; m < CPT; ++m) acc1[m] = fma(-av, sB[q + RPT * m + p * B], acc1[m]);
+          }
+        } else {
+#pragma unroll 4
+          for (int p = 0; p < B; ++p) {
+            const double av = sA[row + p * B];
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sB[q + RPT * m + p * B], acc2[m]);
+          }
+        }
       }
       __syncthreads();  // stage `st` may be refilled
     }
@@ -209,77 +334,25 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) {
       double* dst = a.scratch + size_t(tk.out) * TILE;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
       publish(a.sflags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
 
     if (tk.type == TASK_DIAG) {
-      // ---- POTRF: right-looking on unscaled columns; one barrier per column ----
-#pragma unroll
-      for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
-      __syncthreads();
-      if (tid == 0) {
-        const double d = sC[0];
-        sPiv[0] = d;
-        sInv[0] = 1.0 / d;
-      }
-      __syncthreads();
-      int bad = -1;
-#pragma unroll
-      for (int j = 0; j < B; ++j) {
-        const double d = sPiv[j];
-        if (!(d > 0.0)) { bad = j; break; }
-        const double tr = sC[row + j * B] * sInv[j];
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) {
-          const int c = q + RPT * m;
-          if (c > j && c <= row) acc[m] = fma(-tr, sC[c + j * B], acc[m]);
-        }
-        if (j + 1 < B) {
-          const int cn = j + 1;
-          if (q == cn % RPT && row >= cn) {
-            const double v = acc[cn / RPT];
-            sC[row + cn * B] = v;
-            if (row == cn) {
-              sPiv[cn] = v;
-              sInv[cn] = 1.0 / v;
-            }
-          }
-        }
-        __syncthreads();
-      }
-      if (bad >= 0) {
-        if (tid == 0) {
-          const unsigned long long col = (unsigned long long)tk.col * B + bad + 1;
-          atomicMin(&a.ctl->info, col);
-        }
-        const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) acc[m] = nanv;
-        if (tid < B) sInv[tid] = nanv;
-      } else {
-        // L_ij = a_ij / sqrt(d_j); L_jj = sqrt(d_j)
-        if (tid < B) sInv[tid] = 1.0 / sqrt(sPiv[tid]);
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) {
-          const int c = q + RPT * m;
-          acc[m] = (c <= row) ? acc[m] * sInv[c] : 0.0;
-        }
-      }
-      __syncthreads();
+      const int bad = potrf_tile<B>(acc1, sC, sPiv, sInv, sRs, row, q, tid);
+      if (bad >= 0 && tid == 0) atomicMin(&a.ctl->info, (unsigned long long)tk.col * B + bad + 1);
       double* dst = a.tiles + size_t(tk.out) * TILE;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
       if (tid < B) a.invdiag[size_t(tk.col) * B + tid] = sInv[tid];
       publish(a.flags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
 
-    // ---- TASK_OFF: TRSM with L_kk once it is final ----
+    // ---- OFF and CHAIN: TRSM of `out` with L_kk once it is final ----
     if (tid == 0) {
       if (!wait_flag(a.flags + tk.diag, 1, limit, a.ctl)) {
         raise_timeout(a.ctl, t);
@@ -307,26 +380,38 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
       for (int m = 0; m < CPT; ++m) inv[m] = __ldcg(iv + q + RPT * m);
     }
-    // X L_kk^T = A, column by column; x_ij broadcast to the row's RPT lanes
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      const int mj = j / RPT;
-      const bool owner = (q == j % RPT);
-      double x = owner ? acc[mj] * inv[mj] : 0.0;
-      x = __shfl_sync(0xffffffffu, x, row_lane0 + (j % RPT));
-      if (owner) acc[mj] = x;
-#pragma unroll
-      for (int m = 0; m < CPT; ++m) {
-        const int c = q + RPT * m;
-        if (c > j) acc[m] = fma(-x, sL[c + j * B], acc[m]);
-      }
-    }
+    trsm_rows<B>(acc1, inv, sL, q, row_lane0);
     {
       double* dst = a.tiles + size_t(tk.out) * TILE;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc[m];
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
     }
-    publish(a.flags + tk.out);
+    if (!chain) {
+      publish(a.flags + tk.out);
+      if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
+      continue;
+    }
+    // CHAIN: publish L_{k,k-1} and keep it in shared memory for the SYRK term;
+    // sL is reused once every warp has finished reading L_kk in the TRSM
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) sL[(q + RPT * m) * B + row] = acc1[m];
+    publish(a.flags + tk.out);  // includes the barrier that makes sL visible to the CTA
+#pragma unroll 4
+    for (int p = 0; p < B; ++p) {
+      const double av = sL[row + p * B];
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
+    }
+    const int bad = potrf_tile<B>(acc2, sC, sPiv, sInv, sRs, row, q, tid);
+    if (bad >= 0 && tid == 0) atomicMin(&a.ctl->info, (unsigned long long)tk.col2 * B + bad + 1);
+    {
+      double* dst = a.tiles + size_t(tk.out2) * TILE;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc2[m];
+    }
+    if (tid < B) a.invdiag[size_t(tk.col2) * B + tid] = sInv[tid];
+    publish(a.flags + tk.out2);
     if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
   }
 }

@@ -18,17 +18,27 @@ enum TaskType : int32_t {
   TASK_OFF = 1,      // L_mk = (A_mk - sum L_mn L_kn^T - sum partials) L_kk^{-T}       (GEMM + TRSM)
   TASK_PARTIAL = 2,  // P = sum over a chunk of L_an L_bn^T   (a tree leaf, Algorithm 3)
   TASK_COMBINE = 3,  // P = sum of partial tiles             (a tree node, GEADD)
+  TASK_CHAIN = 4,    // OFF(k, k-1) then DIAG(k) in one CTA: the diagonal chain step
 };
 
+// For TASK_CHAIN the first output is the OFF tile (k, k-1) (diag = L_{k-1,k-1},
+// col = k-1) and the second the diagonal tile (k, k) (col2 = k); the SYRK term
+// with L_{k,k-1} is applied from shared memory.  The terms of both tiles share
+// one list, ordered by when their producers run; bit 30 of a pair's first index
+// (or of a partial index) marks the terms of the diagonal tile.
 struct DevTask {
   int32_t type;
-  int32_t out;   // sub-tile index (DIAG/OFF) or scratch tile index (PARTIAL/COMBINE)
-  int32_t diag;  // sub-tile index of L_kk (OFF), else -1
-  int32_t col;   // sub-column k (DIAG: slot of the log-determinant partial)
-  int32_t pb, pe;  // update pairs [pb, pe)
-  int32_t qb, qe;  // partial tiles [qb, qe) (scratch indices)
+  int32_t out;   // sub-tile index (DIAG/OFF/CHAIN) or scratch tile index (PARTIAL/COMBINE)
+  int32_t diag;  // sub-tile index of L_kk (OFF, CHAIN), else -1
+  int32_t col;   // sub-column of `out` (slot of the 1/L_jj vector of its diagonal)
+  int32_t pb, pe;  // update pairs [pb, pe) into `out`
+  int32_t qb, qe;  // partial tiles [qb, qe) (scratch indices) into `out`
+  int32_t out2;    // CHAIN: the diagonal sub-tile, else -1
+  int32_t col2;    // CHAIN: its sub-column
+  int32_t pb2, pe2, qb2, qe2;  // unused (CHAIN terms for `out2` are tagged inside [pb, pe) / [qb, qe))
+  int32_t pad0, pad1;
 };
-static_assert(sizeof(DevTask) == 32, "DevTask layout");
+static_assert(sizeof(DevTask) == 64, "DevTask layout");
 
 // Solve task: one B x nrhs block of y (forward) or x (backward).
 enum SolveType : int32_t { SOLVE_FINAL = 0, SOLVE_PARTIAL = 2, SOLVE_COMBINE = 3 };

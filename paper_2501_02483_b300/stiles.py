@@ -31,7 +31,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstiles.s
 class Opts(ctypes.Structure):
     _fields_ = [("tile", c_int32), ("ordering", c_int32), ("precision", c_int32), ("block", c_int32),
                 ("tree_chunk", c_int32), ("tree_fanin", c_int32), ("max_refine", c_int32),
-                ("reserved0", c_int32), ("refine_tol", c_double), ("spin_limit", c_int64)]
+                ("ctas_per_sm", c_int32), ("refine_tol", c_double), ("spin_limit", c_int64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -131,7 +131,7 @@ class Plan:
     """Symbolic analysis of one pattern (stiles_analyze)."""
 
     def __init__(self, n, colptr, rowidx, n_arrow=0, tile=32, ordering=ORDER_AUTO, precision=PREC_F64, block=0,
-                 tree_chunk=0, tree_fanin=0, spin_limit=0, refine_tol=0.0, max_refine=0):
+                 tree_chunk=0, tree_fanin=0, spin_limit=0, refine_tol=0.0, max_refine=0, ctas_per_sm=0):
         L = lib()
         o = default_opts()
         o.tile, o.ordering, o.precision, o.block = tile, ordering, precision, block
@@ -145,6 +145,7 @@ class Plan:
             o.refine_tol = refine_tol
         if max_refine:
             o.max_refine = max_refine
+        o.ctas_per_sm = ctas_per_sm
         self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
         self._rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
         h = c_void_p()
@@ -179,10 +180,10 @@ class Plan:
         return tc, tr
 
     def tasks(self, which=0):
-        """Device task list (ticket order) as an int32 array of shape (ntasks, 8)."""
+        """Device task list (ticket order): int32 (ntasks, 16) for the factorization, (ntasks, 8) for a sweep."""
         n = c_int64(0)
         _check(lib().stiles_plan_tasks(self._h, which, None, ctypes.byref(n)))
-        out = np.empty((n.value, 8), dtype=np.int32)
+        out = np.empty((n.value, 16 if which == 0 else 8), dtype=np.int32)
         _check(lib().stiles_plan_tasks(self._h, which, _ptr(out), ctypes.byref(n)))
         return out
 
