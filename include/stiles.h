@@ -140,6 +140,9 @@ stiles_status stiles_factor_wait(stiles_factor* factor, int64_t* info);
 stiles_status stiles_logdet(const stiles_factor* factor, double* out);
 
 /* Solve A X = B for nrhs right-hand sides: X = P^T L^{-T} L^{-1} P B.
+ * For a BF16/FP16 factor the solve refines in FP64: x <- x + solve(b - A x) with the residual
+ * from the original FP64 values, until ||b - A x||_2 / ||b||_2 <= opts.refine_tol for every
+ * column or opts.max_refine steps (then STILES_ERR_NOT_CONVERGED, x holding the last iterate).
  *   b, x  : n x nrhs, column-major with leading dimension ld >= n, host or device (both
  *           on the same side); x may equal b.
  *   final_relres : may be NULL; else receives max over columns of ||b - A x||_2 / ||b||_2,
@@ -147,6 +150,11 @@ stiles_status stiles_logdet(const stiles_factor* factor, double* out);
  * Errors: STILES_ERR_INVALID, STILES_ERR_TIMEOUT, STILES_ERR_CUDA. */
 stiles_status stiles_solve(const stiles_factor* factor, const double* b, double* x, int64_t nrhs, int64_t ld,
                            void* stream, double* final_relres);
+
+/* Refinement steps the last stiles_solve on this factor needed (largest over its right-hand-side
+ * chunks): 0 for FP64 factors; for BF16/FP16 factors the number of x <- x + solve(b - A x)
+ * corrections after the first solve.  -1 for a NULL factor. */
+int32_t stiles_factor_refine_iters(const stiles_factor* factor);
 
 /* Copy the factor out as T x T column-major tiles in tile-CSC order (nnzt * T * T doubles),
  * host or device.  Rows/columns past n are padding (identity on the diagonal). */

@@ -635,9 +635,13 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   trows.clear();
   trows.shrink_to_fit();
 
-  // device sub-tile size
+  // device sub-tile size (the mixed-precision kernel works on 64-wide sub-tiles)
   int64_t B = o.block;
-  if (B == 0) B = (T % 32 == 0) ? 32 : (T % 16 == 0 ? 16 : 0);
+  if (o.precision != STILES_PREC_F64) {
+    B = (o.block == 0 || o.block == 64) ? 64 : 0;
+  } else if (B == 0) {
+    B = (T % 32 == 0) ? 32 : (T % 16 == 0 ? 16 : 0);
+  }
   p->executable = (B == 16 || B == 32 || B == 64) && (T % B == 0);
   if (!p->executable) {
     p->B = int32_t(B);

@@ -19,9 +19,37 @@ __global__ void scatter_kernel(double* __restrict__ tiles, const double* __restr
     tiles[__ldg(map + e)] = __ldg(values + e);
 }
 
-__global__ void set_ones_kernel(double* __restrict__ tiles, const int64_t* __restrict__ offs, int64_t n) {
+// Mixed-precision factor: the values are rounded to FP32 on the way into the tiles.
+__global__ void scatter_f32_kernel(float* __restrict__ tiles, const double* __restrict__ values,
+                                   const int64_t* __restrict__ map, int64_t nnz) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    tiles[__ldg(map + e)] = float(__ldg(values + e));
+}
+
+template <typename T>
+__global__ void set_ones_kernel(T* __restrict__ tiles, const int64_t* __restrict__ offs, int64_t n) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) tiles[offs[i]] = 1.0;
+  if (i < n) tiles[offs[i]] = T(1);
+}
+
+// x += d (n x nr blocks, leading dimensions ldx / n)
+__global__ void axpy_cols_kernel(double* __restrict__ x, const double* __restrict__ d, int64_t n, int64_t ldx, int nr) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * nr; e += stride) {
+    const int64_t r = e / n, i = e % n;
+    x[i + r * ldx] += d[i + r * n];
+  }
+}
+
+// r = b - y (y: n x nr, ld n; b: ld ldb; r: ld n)
+__global__ void sub_cols_kernel(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ y,
+                                int64_t n, int64_t ldb, int nr) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * nr; e += stride) {
+    const int64_t c = e / n, i = e % n;
+    r[i + c * n] = b[i + c * ldb] - y[i + c * n];
+  }
 }
 
 __global__ void init_ctl_kernel(Ctl* ctl, int count) {
@@ -54,6 +82,23 @@ __global__ void logdet_pass1(const double* __restrict__ tiles, const int32_t* __
     const double l = tiles[int64_t(diag_sub[k]) * B * B + j * B + j];
     s += 2.0 * log(l);
   }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// The same reduction over a vector of the factor's diagonal entries (mixed-precision factors).
+__global__ void logdet_vec_pass1(const double* __restrict__ ldiag, int64_t n, double* __restrict__ partial) {
+  __shared__ double red[LOGDET_THREADS];
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = int64_t(blockIdx.x) * per;
+  const int64_t hi = min(n, lo + per);
+  double s = 0.0;
+  for (int64_t g = lo + threadIdx.x; g < hi; g += blockDim.x) s += 2.0 * log(ldiag[g]);
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -150,7 +195,8 @@ __global__ void residual_norms_kernel(const double* __restrict__ y, const double
 }
 
 // Export T x T column-major tiles from the sub-tile layout (R = T / B).
-__global__ void export_tiles_kernel(double* __restrict__ out, const double* __restrict__ tiles, int64_t nnzt, int T, int B) {
+template <typename TF>
+__global__ void export_tiles_kernel(double* __restrict__ out, const TF* __restrict__ tiles, int64_t nnzt, int T, int B) {
   const int64_t TT = int64_t(T) * T;
   const int R = T / B;
   const int64_t total = nnzt * TT;
@@ -160,7 +206,7 @@ __global__ void export_tiles_kernel(double* __restrict__ out, const double* __re
     const int64_t w = e % TT;
     const int c = int(w / T), r = int(w % T);
     const int64_t s = t * R * R + int64_t(c / B) * R + (r / B);
-    out[e] = tiles[s * B * B + int64_t(c % B) * B + (r % B)];
+    out[e] = double(tiles[s * B * B + int64_t(c % B) * B + (r % B)]);
   }
 }
 

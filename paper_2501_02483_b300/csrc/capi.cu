@@ -14,6 +14,7 @@
 
 #include "aux_kernels.cuh"
 #include "factor_f64.cuh"
+#include "factor_lp.cuh"
 #include "plan.h"
 #include "solve_f64.cuh"
 
@@ -90,10 +91,18 @@ struct DevPlan {
 struct stiles_factor {
   const stiles_plan* plan = nullptr;
   int device = -1;
+  bool lp = false;            // mixed precision (BF16/FP16 updates, FP32 tiles, FP64 diagonal)
   double* values = nullptr;   // FP64 copy of A's values (CSC order) for residuals
-  double* tiles = nullptr;
+  double* tiles = nullptr;    // FP64 path
   double* scratch = nullptr;
   double* invdiag = nullptr;
+  float* tiles32 = nullptr;   // mixed-precision path
+  uint16_t* tiles16 = nullptr;
+  float* scratch32 = nullptr;
+  float* invdiag32 = nullptr;
+  double* ldiag = nullptr;
+  double* irwork = nullptr;   // refinement: correction and residual, 2 * n * SOLVE_MAXR
+  int last_refine_iters = 0;
   int* flags = nullptr;       // nsub + nscratch
   stiles::dev::Ctl* ctl = nullptr;  // [0] factor, [1] forward, [2] backward
   double* logdet_part = nullptr;    // LOGDET_BLOCKS + 1
@@ -150,15 +159,15 @@ cudaError_t factor_occupancy(int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::factor_f64_kernel<B>, 128, dev::FactorCfg<B>::SMEM);
 }
 
-template <int B>
+template <int B, typename TF>
 cudaError_t solve_occupancy(int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(dev::SolveCfg<B>::SMEM));
+  cudaError_t e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, false, TF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::SolveCfg<B>::SMEM));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, true, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(dev::SolveCfg<B>::SMEM));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::solve_f64_kernel<B, false>, 128,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::solve_f64_kernel<B, false, TF>, 128,
                                                        dev::SolveCfg<B>::SMEM);
 }
 
@@ -196,10 +205,16 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   int fb = 0, sb = 0;
   cudaError_t e = cudaSuccess;
-  switch (p->B) {
-    case 16: e = factor_occupancy<16>(&fb); if (e == cudaSuccess) e = solve_occupancy<16>(&sb); break;
-    case 32: e = factor_occupancy<32>(&fb); if (e == cudaSuccess) e = solve_occupancy<32>(&sb); break;
-    case 64: e = factor_occupancy<64>(&fb); if (e == cudaSuccess) e = solve_occupancy<64>(&sb); break;
+  if (p->opts.precision != STILES_PREC_F64) {
+    e = cudaFuncSetAttribute(dev::factor_lp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::LP_SMEM));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, dev::factor_lp_kernel, 128, dev::LP_SMEM);
+    // each resident CTA holds 128 TMEM columns of the SM's 512
+    fb = std::min(fb, 4);
+    if (e == cudaSuccess) e = solve_occupancy<64, float>(&sb);
+  } else switch (p->B) {
+    case 16: e = factor_occupancy<16>(&fb); if (e == cudaSuccess) e = solve_occupancy<16, double>(&sb); break;
+    case 32: e = factor_occupancy<32>(&fb); if (e == cudaSuccess) e = solve_occupancy<32, double>(&sb); break;
+    case 64: e = factor_occupancy<64>(&fb); if (e == cudaSuccess) e = solve_occupancy<64, double>(&sb); break;
     default: return fail(STILES_ERR_UNSUPPORTED, "block size");
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
@@ -219,6 +234,12 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->tiles);
   cudaFree(f->scratch);
   cudaFree(f->invdiag);
+  cudaFree(f->tiles32);
+  cudaFree(f->tiles16);
+  cudaFree(f->scratch32);
+  cudaFree(f->invdiag32);
+  cudaFree(f->ldiag);
+  cudaFree(f->irwork);
   cudaFree(f->flags);
   cudaFree(f->ctl);
   cudaFree(f->logdet_part);
@@ -243,10 +264,19 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
   cudaGetDevice(&f->device);
   const size_t tile = size_t(p->B) * p->B;
   const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
+  f->lp = p->opts.precision != STILES_PREC_F64;
   cudaError_t e = cudaMalloc(&f->values, size_t(p->nnz) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
+  if (!f->lp) {
+    if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
+  } else {
+    if (e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->tiles16, size_t(p->nsub) * tile * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&f->scratch32, size_t(nscr) * tile * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->invdiag32, size_t(p->nsb) * p->B * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->ldiag, size_t(p->nsb) * p->B * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
   if (e == cudaSuccess) e = cudaMalloc(&f->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double));
@@ -282,11 +312,33 @@ cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s
   return cudaGetLastError();
 }
 
-template <int B>
-cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr) {
-  dev::SolveArgs a;
-  a.tiles = f->tiles;
-  a.invdiag = f->invdiag;
+cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
+  dev::LPArgs a;
+  a.tiles32 = f->tiles32;
+  a.tiles16 = f->tiles16;
+  a.scratch = f->scratch32;
+  a.invdiag32 = f->invdiag32;
+  a.ldiag = f->ldiag;
+  a.tasks = p->dev->fac.tasks;
+  a.ntasks = p->dev->fac.ntasks;
+  a.pairs = p->dev->fac.pairs;
+  a.parts = p->dev->fac.parts;
+  a.flags = f->flags;
+  a.sflags = f->flags + p->nsub;
+  a.ctl = f->ctl;
+  a.spin_limit = p->opts.spin_limit;
+  a.trace = f->trace[0];
+  a.fp16 = p->opts.precision == STILES_PREC_F16 ? 1 : 0;
+  dev::factor_lp_kernel<<<p->dev->grid_factor, 128, dev::LP_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int B, typename TF>
+cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr, const TF* tiles,
+                         const TF* invdiag) {
+  dev::SolveArgs<TF> a;
+  a.tiles = tiles;
+  a.invdiag = invdiag;
   a.Y = f->Y;
   a.spin_limit = p->opts.spin_limit;
   a.nr = nr;
@@ -301,7 +353,7 @@ cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s,
   a.sflags = f->sflags + p->nsb;
   a.ctl = f->ctl + 1;
   a.trace = f->trace[1];
-  dev::solve_f64_kernel<B, false><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  dev::solve_f64_kernel<B, false, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // backward
@@ -314,7 +366,7 @@ cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s,
   a.sflags = f->sflags + 2 * p->nsb + nf;
   a.ctl = f->ctl + 2;
   a.trace = f->trace[2];
-  dev::solve_f64_kernel<B, true><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  dev::solve_f64_kernel<B, true, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -430,8 +482,6 @@ void stiles_factor_destroy(stiles_factor* f) { free_factor(f); }
 
 stiles_status stiles_factorize_async(const stiles_plan* p, const double* values, void* stream, stiles_factor** inout) {
   if (!p || !values || !inout) return fail(STILES_ERR_INVALID, "null argument");
-  if (p->opts.precision != STILES_PREC_F64)
-    return fail(STILES_ERR_UNSUPPORTED, "this entry point factorizes in FP64 only");
   stiles_status s = ensure_dev_plan(p);
   if (s != STILES_OK) return s;
   stiles_factor* f = *inout;
@@ -447,12 +497,22 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
   CUDA_TRY(cudaEventRecord(f->ev[0], st));
   CUDA_TRY(cudaMemcpyAsync(f->values, values, size_t(p->nnz) * sizeof(double), cudaMemcpyDefault, st));
-  CUDA_TRY(cudaMemsetAsync(f->tiles, 0, size_t(p->nsub) * tile * sizeof(double), st));
-  dev::scatter_kernel<<<grid_for(p->nnz, 256), 256, 0, st>>>(f->tiles, f->values, p->dev->scatter, p->nnz);
-  CUDA_TRY(cudaGetLastError());
-  if (!p->pad.empty()) {
-    dev::set_ones_kernel<<<1, 128, 0, st>>>(f->tiles, p->dev->pad, int64_t(p->pad.size()));
+  if (!f->lp) {
+    CUDA_TRY(cudaMemsetAsync(f->tiles, 0, size_t(p->nsub) * tile * sizeof(double), st));
+    dev::scatter_kernel<<<grid_for(p->nnz, 256), 256, 0, st>>>(f->tiles, f->values, p->dev->scatter, p->nnz);
     CUDA_TRY(cudaGetLastError());
+    if (!p->pad.empty()) {
+      dev::set_ones_kernel<double><<<1, 128, 0, st>>>(f->tiles, p->dev->pad, int64_t(p->pad.size()));
+      CUDA_TRY(cudaGetLastError());
+    }
+  } else {
+    CUDA_TRY(cudaMemsetAsync(f->tiles32, 0, size_t(p->nsub) * tile * sizeof(float), st));
+    dev::scatter_f32_kernel<<<grid_for(p->nnz, 256), 256, 0, st>>>(f->tiles32, f->values, p->dev->scatter, p->nnz);
+    CUDA_TRY(cudaGetLastError());
+    if (!p->pad.empty()) {
+      dev::set_ones_kernel<float><<<1, 128, 0, st>>>(f->tiles32, p->dev->pad, int64_t(p->pad.size()));
+      CUDA_TRY(cudaGetLastError());
+    }
   }
   CUDA_TRY(cudaMemsetAsync(f->flags, 0, size_t(p->nsub + nscr) * sizeof(int), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl, 1);
@@ -460,7 +520,8 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   count_launch(p->pad.empty() ? 2 : 3);
   CUDA_TRY(cudaEventRecord(f->ev[1], st));
   cudaError_t e;
-  switch (p->B) {
+  if (f->lp) e = launch_factor_lp(p, f, st);
+  else switch (p->B) {
     case 16: e = launch_factor<16>(p, f, st); break;
     case 32: e = launch_factor<32>(p, f, st); break;
     default: e = launch_factor<64>(p, f, st); break;
@@ -494,8 +555,11 @@ stiles_status stiles_logdet(const stiles_factor* cf, double* out) {
   stiles_factor* f = const_cast<stiles_factor*>(cf);
   const stiles_plan* p = f->plan;
   cudaStream_t st = f->stream;
-  dev::logdet_pass1<<<dev::LOGDET_BLOCKS, dev::LOGDET_THREADS, 0, st>>>(f->tiles, p->dev->diag_sub, p->n, p->B,
-                                                                        f->logdet_part);
+  if (f->lp)
+    dev::logdet_vec_pass1<<<dev::LOGDET_BLOCKS, dev::LOGDET_THREADS, 0, st>>>(f->ldiag, p->n, f->logdet_part);
+  else
+    dev::logdet_pass1<<<dev::LOGDET_BLOCKS, dev::LOGDET_THREADS, 0, st>>>(f->tiles, p->dev->diag_sub, p->n, p->B,
+                                                                          f->logdet_part);
   CUDA_TRY(cudaGetLastError());
   dev::logdet_pass2<<<1, 32, 0, st>>>(f->logdet_part, dev::LOGDET_BLOCKS, f->logdet_part + dev::LOGDET_BLOCKS);
   CUDA_TRY(cudaGetLastError());
@@ -504,6 +568,73 @@ stiles_status stiles_logdet(const stiles_factor* cf, double* out) {
   CUDA_TRY(cudaStreamSynchronize(st));
   return STILES_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// One forward + backward sweep for right-hand-side columns [r0, r0 + nr) of
+// `rhs` (leading dimension rld), result into the same columns of `out`.
+stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t st, const double* rhs, int64_t rld,
+                          double* out, int64_t old_, int r0, int nr) {
+  const int64_t n = p->n, B = p->B;
+  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
+  dev::permute_in_kernel<<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(f->Y, rhs, p->dev->perm, n, rld, r0, nr,
+                                                                        int(B), p->nsb);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(f->sflags, 0, size_t(2 * p->nsb + nf + nb) * sizeof(int), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl + 1, 2);
+  CUDA_TRY(cudaGetLastError());
+  cudaError_t e;
+  if (f->lp) e = launch_solve<64, float>(p, f, st, nr, f->tiles32, f->invdiag32);
+  else switch (p->B) {
+    case 16: e = launch_solve<16, double>(p, f, st, nr, f->tiles, f->invdiag); break;
+    case 32: e = launch_solve<32, double>(p, f, st, nr, f->tiles, f->invdiag); break;
+    default: e = launch_solve<64, double>(p, f, st, nr, f->tiles, f->invdiag); break;
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
+  dev::permute_out_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(out, f->Y, p->dev->perm, n, old_, r0, nr, int(B));
+  CUDA_TRY(cudaGetLastError());
+  count_launch(5);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  stiles_status s1 = read_ctl(f, 1, nullptr);
+  if (s1 == STILES_OK) s1 = read_ctl(f, 2, nullptr);
+  return s1;
+}
+
+// FP64 residual of columns [r0, r0 + nr): optionally r = b - A x into rout
+// (leading dimension n), and the largest ||b - A x|| / ||b|| of the chunk.
+stiles_status residual_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t st, const double* x, int64_t ldx,
+                             const double* b, int64_t ldb, int r0, int nr, double* rout, double* worst) {
+  const int64_t n = p->n;
+  CUDA_TRY(cudaMemsetAsync(f->ywork, 0, size_t(n) * nr * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(f->norms, 0, 2 * dev::SOLVE_MAXR * sizeof(double), st));
+  dev::spmv_lower_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(f->ywork, x + r0 * ldx, p->dev->colptr,
+                                                               p->dev->rowidx, f->values, n, ldx, nr);
+  CUDA_TRY(cudaGetLastError());
+  dev::residual_norms_kernel<<<dim3(64, nr), 256, 0, st>>>(f->ywork, b + r0 * ldb, n, ldb, nr, f->norms);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(2);
+  if (rout) {
+    dev::sub_cols_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(rout, b + r0 * ldb, f->ywork, n, ldb, nr);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  double h[2 * dev::SOLVE_MAXR];
+  CUDA_TRY(cudaMemcpyAsync(h, f->norms, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  double w = 0.0;
+  for (int r = 0; r < nr; ++r) {
+    const double rel = h[2 * r + 1] > 0 ? std::sqrt(h[2 * r] / h[2 * r + 1]) : std::sqrt(h[2 * r]);
+    w = std::max(w, rel);
+  }
+  *worst = w;
+  return STILES_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, int64_t nrhs, int64_t ld, void* stream,
                            double* final_relres) {
@@ -515,9 +646,8 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
   const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
   if (bdev != xdev) return fail(STILES_ERR_INVALID, "b and x must both be host or both be device memory");
   const int64_t n = p->n, B = p->B;
-  const int nrmax = int(std::min<int64_t>(nrhs, dev::SOLVE_MAXR));
   const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
-  if (f->solve_nr < nrmax) {
+  if (f->solve_nr < dev::SOLVE_MAXR) {
     cudaFree(f->Y);
     cudaFree(f->sscratch);
     cudaFree(f->sflags);
@@ -531,6 +661,7 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
     CUDA_TRY(cudaMalloc(&f->ywork, size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
     f->solve_nr = dev::SOLVE_MAXR;
   }
+  if (f->lp && !f->irwork) CUDA_TRY(cudaMalloc(&f->irwork, 2 * size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
   const double* db = b;
   double* dx = x;
   int64_t dld = ld;
@@ -552,47 +683,43 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
     dld = n;
   }
   double worst = 0.0;
+  bool converged = true;
+  f->last_refine_iters = 0;
   for (int64_t r0 = 0; r0 < nrhs; r0 += dev::SOLVE_MAXR) {
     const int nr = int(std::min<int64_t>(dev::SOLVE_MAXR, nrhs - r0));
-    dev::permute_in_kernel<<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(f->Y, db, p->dev->perm, n, dld, int(r0),
-                                                                          nr, int(B), p->nsb);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemsetAsync(f->sflags, 0, size_t(2 * p->nsb + nf + nb) * sizeof(int), st));
-    dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl + 1, 2);
-    CUDA_TRY(cudaGetLastError());
-    cudaError_t e;
-    switch (p->B) {
-      case 16: e = launch_solve<16>(p, f, st, nr); break;
-      case 32: e = launch_solve<32>(p, f, st, nr); break;
-      default: e = launch_solve<64>(p, f, st, nr); break;
-    }
-    if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
-    count_launch(5);
-    dev::permute_out_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(dx, f->Y, p->dev->perm, n, dld, int(r0), nr,
-                                                                   int(B));
-    CUDA_TRY(cudaGetLastError());
-    if (final_relres) {
-      CUDA_TRY(cudaMemsetAsync(f->ywork, 0, size_t(n) * nr * sizeof(double), st));
-      CUDA_TRY(cudaMemsetAsync(f->norms, 0, 2 * dev::SOLVE_MAXR * sizeof(double), st));
-      dev::spmv_lower_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(f->ywork, dx + r0 * dld, p->dev->colptr,
-                                                                   p->dev->rowidx, f->values, n, dld, nr);
-      CUDA_TRY(cudaGetLastError());
-      dev::residual_norms_kernel<<<dim3(64, nr), 256, 0, st>>>(f->ywork, db + r0 * dld, n, dld, nr, f->norms);
-      CUDA_TRY(cudaGetLastError());
-      count_launch(2);
-      double h[2 * dev::SOLVE_MAXR];
-      CUDA_TRY(cudaMemcpyAsync(h, f->norms, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CUDA_TRY(cudaStreamSynchronize(st));
-      for (int r = 0; r < nr; ++r) {
-        const double rel = h[2 * r + 1] > 0 ? std::sqrt(h[2 * r] / h[2 * r + 1]) : std::sqrt(h[2 * r]);
-        worst = std::max(worst, rel);
+    if (!f->lp) {
+      stiles_status s1 = solve_chunk(p, f, st, db, dld, dx, dld, int(r0), nr);
+      if (s1 != STILES_OK) return s1;
+      if (final_relres) {
+        double w = 0.0;
+        s1 = residual_chunk(p, f, st, dx, dld, db, dld, int(r0), nr, nullptr, &w);
+        if (s1 != STILES_OK) return s1;
+        worst = std::max(worst, w);
       }
+      continue;
     }
-    stiles_status s1 = STILES_OK;
-    CUDA_TRY(cudaStreamSynchronize(st));
-    s1 = read_ctl(f, 1, nullptr);
-    if (s1 == STILES_OK) s1 = read_ctl(f, 2, nullptr);
+    // Mixed-precision factor: iterative refinement with FP64 residuals,
+    // x <- x + solve(b - A x), until ||b - A x|| / ||b|| <= refine_tol.
+    double* dwork = f->irwork;                  // correction, n x nr
+    double* rwork = f->irwork + size_t(n) * dev::SOLVE_MAXR;  // residual, n x nr
+    stiles_status s1 = solve_chunk(p, f, st, db, dld, dx, dld, int(r0), nr);
     if (s1 != STILES_OK) return s1;
+    double w = 0.0;
+    int it = 0;
+    for (;;) {
+      s1 = residual_chunk(p, f, st, dx, dld, db, dld, int(r0), nr, rwork, &w);
+      if (s1 != STILES_OK) return s1;
+      if (!(w > p->opts.refine_tol) || it >= p->opts.max_refine) break;
+      s1 = solve_chunk(p, f, st, rwork, n, dwork, n, 0, nr);
+      if (s1 != STILES_OK) return s1;
+      dev::axpy_cols_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(dx + r0 * dld, dwork, n, dld, nr);
+      CUDA_TRY(cudaGetLastError());
+      count_launch();
+      ++it;
+    }
+    f->last_refine_iters = std::max(f->last_refine_iters, it);
+    if (w > p->opts.refine_tol || w != w) converged = false;
+    worst = std::max(worst, w);
   }
   if (!xdev) {
     CUDA_TRY(cudaMemcpy2DAsync(x, ld * sizeof(double), dx, n * sizeof(double), n * sizeof(double), nrhs,
@@ -600,8 +727,11 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
     CUDA_TRY(cudaStreamSynchronize(st));
   }
   if (final_relres) *final_relres = worst;
+  if (!converged) return fail(STILES_ERR_NOT_CONVERGED, "iterative refinement did not reach refine_tol");
   return STILES_OK;
 }
+
+int32_t stiles_factor_refine_iters(const stiles_factor* f) { return f ? f->last_refine_iters : -1; }
 
 stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* stream) {
   if (!cf || !out) return fail(STILES_ERR_INVALID, "null argument");
@@ -612,7 +742,10 @@ stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* st
   const bool odev = is_device_ptr(out);
   double* dst = out;
   if (!odev) CUDA_TRY(cudaMalloc(&dst, elems * sizeof(double)));
-  dev::export_tiles_kernel<<<grid_for(int64_t(elems), 256), 256, 0, st>>>(dst, f->tiles, p->nnzt, p->T, p->B);
+  if (f->lp)
+    dev::export_tiles_kernel<float><<<grid_for(int64_t(elems), 256), 256, 0, st>>>(dst, f->tiles32, p->nnzt, p->T, p->B);
+  else
+    dev::export_tiles_kernel<double><<<grid_for(int64_t(elems), 256), 256, 0, st>>>(dst, f->tiles, p->nnzt, p->T, p->B);
   cudaError_t e = cudaGetLastError();
   count_launch();
   if (e == cudaSuccess && !odev) e = cudaMemcpyAsync(out, dst, elems * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -157,7 +157,7 @@ template <int B>
 __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   using Cfg = FactorCfg<B>;
   constexpr int RPT = Cfg::RPT, CPT = Cfg::CPT, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   double* sStage = reinterpret_cast<double*>(smem_raw);
   double* sC = sStage + NSTAGE * 2 * TILE;
   double* sL = sC + TILE;

@@ -33,9 +33,10 @@ struct SolveCfg {
   static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
 
+template <typename TF>
 struct SolveArgs {
-  const double* tiles;    // factor sub-tiles
-  const double* invdiag;  // nsb * B
+  const TF* tiles;        // factor sub-tiles (FP64, or FP32 for a mixed-precision factor)
+  const TF* invdiag;      // nsb * B
   double* Y;              // nsb blocks of B x nr
   double* scratch;        // nscratch blocks
   const SolveTask* tasks;
@@ -50,14 +51,14 @@ struct SolveArgs {
   long long* trace;       // optional, 4 per ticket: start, dependencies ready, done, SM id
 };
 
-template <int B, bool BACKWARD>
-__global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
+template <int B, bool BACKWARD, typename TF>
+__global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
   using Cfg = SolveCfg<B>;
   constexpr int W = Cfg::W, RP = Cfg::RP, G = Cfg::G, U = Cfg::U, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   double* sStage = reinterpret_cast<double*>(smem_raw);            // NSTAGE * (TILE + BLK)
-  double* sL = sStage + NSTAGE * (TILE + Cfg::BLK);                 // TILE
-  double* sLt = sL + TILE;                                          // B x (B + 1), transposed L_kk
+  TF* sL = reinterpret_cast<TF*>(sStage + NSTAGE * (TILE + Cfg::BLK));  // TILE (room for doubles)
+  double* sLt = sStage + NSTAGE * (TILE + Cfg::BLK) + TILE;            // B x (B + 1), transposed L_kk
   double* sInv = sLt + B * (B + 1);                                 // B
   uint64_t* bars = reinterpret_cast<uint64_t*>(sInv + B);
   __shared__ int sTicket, sAbort;
@@ -116,8 +117,8 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
 
     // the diagonal sub-tile does not depend on this sweep: fetch it first
     if (tk.type == SOLVE_FINAL && tid == 0) {
-      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
-      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(TF)));
+      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(TF), &bars[NSTAGE]);
     }
     const int npairs = tk.pe - tk.pb;
     const int nitems = npairs + (tk.qe - tk.qb);
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
       if (tid == 0) {
         while (issued < nitems && issued < it + NSTAGE) {
           const int* f;
-          const double* gL = nullptr;
+          const TF* gL = nullptr;
           const double* gY;
           if (issued < npairs) {
             const int ls = a.pairs[2 * (tk.pb + issued)];
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
           fence_proxy_async_global();
           const int st = issued % NSTAGE;
           double* dst = sStage + st * (TILE + Cfg::BLK);
-          mbar_arrive_expect_tx(&bars[st], uint32_t(((gL ? TILE : 0) + blk) * sizeof(double)));
-          if (gL) tma_load_1d(dst, gL, TILE * sizeof(double), &bars[st]);
+          mbar_arrive_expect_tx(&bars[st], uint32_t((gL ? TILE * sizeof(TF) : 0) + blk * sizeof(double)));
+          if (gL) tma_load_1d(dst, gL, TILE * sizeof(TF), &bars[st]);
           tma_load_1d(dst + TILE, gY, uint32_t(blk * sizeof(double)), &bars[st]);
           ++issued;
         }
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
       }
       if (aborted) { stop = it; break; }
       phase ^= (1u << st);
-      const double* sT = sStage + st * (TILE + Cfg::BLK);
-      const double* sY = sT + TILE;
+      const TF* sT = reinterpret_cast<const TF*>(sStage + st * (TILE + Cfg::BLK));
+      const double* sY = sStage + st * (TILE + Cfg::BLK) + TILE;
       if (it < npairs) {
         if (!BACKWARD) {
           // acc(i, r) -= sum_p L(i, p) y(p, r)
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
               if (r < nr) {
                 const double yv = sY[r * B + p];
 #pragma unroll
-                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-sT[li + W * s + p * B], yv, acc[s][u]);
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-double(sT[li + W * s + p * B]), yv, acc[s][u]);
               }
             }
           }
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
               if (r < nr) {
                 const double xv = sY[r * B + p];
 #pragma unroll
-                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-sT[p + (li + W * s) * B], xv, acc[s][u]);
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-double(sT[p + (li + W * s) * B]), xv, acc[s][u]);
               }
             }
           }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
     }
 
     // ---- triangular solve with the diagonal sub-tile (prefetched above) ----
-    if (tid < B) sInv[tid] = __ldcg(a.invdiag + size_t(tk.out) * B + tid);
+    if (tid < B) sInv[tid] = double(__ldcg(a.invdiag + size_t(tk.out) * B + tid));
     {
       long long spins = 0;
       while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
     if (BACKWARD) {
       for (int e = tid; e < TILE; e += Cfg::NT) {
         const int r = e % B, c = e / B;
-        sLt[c + r * (B + 1)] = sL[e];  // sLt(c, r) = L(r, c)
+        sLt[c + r * (B + 1)] = double(sL[e]);  // sLt(c, r) = L(r, c)
       }
     }
     __syncthreads();
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs a) {
 #pragma unroll
           for (int s = 0; s < RP; ++s) {
             const int i = li + W * s;
-            if (i > j) acc[s][u] = fma(-sL[i + j * B], y, acc[s][u]);
+            if (i > j) acc[s][u] = fma(-double(sL[i + j * B]), y, acc[s][u]);
           }
         }
       }

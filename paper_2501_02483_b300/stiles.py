@@ -77,6 +77,8 @@ def lib():
         L.stiles_factor_set_trace.argtypes = [P, c_int32]
         L.stiles_factor_get_trace.argtypes = [P, c_int32, P, POINTER(c_int64)]
         L.stiles_plan_tasks.argtypes = [P, c_int32, P, POINTER(c_int64)]
+        L.stiles_factor_refine_iters.argtypes = [P]
+        L.stiles_factor_refine_iters.restype = c_int32
         L.stiles_kernel_launches.argtypes = []
         L.stiles_kernel_launches.restype = c_int64
         for name in ("stiles_analyze", "stiles_plan_get_info", "stiles_plan_perm", "stiles_plan_tilemap",
@@ -254,6 +256,10 @@ class Factor:
         a, b = c_double(0.0), c_double(0.0)
         _check(lib().stiles_factor_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def refine_iters(self):
+        """Refinement steps of the last solve (0 for FP64 factors)."""
+        return int(lib().stiles_factor_refine_iters(self._h))
 
     def set_trace(self, enable=True):
         """Stamp every device task with the global timer (needs a factorization first)."""
