@@ -40,6 +40,7 @@ extern "C" {
 
 typedef struct stiles_plan stiles_plan;     /* opaque: pattern analysis, host + device arrays */
 typedef struct stiles_factor stiles_factor; /* opaque: device tiles of one factorization      */
+typedef struct stiles_batch stiles_batch;   /* opaque: many factorizations in one launch      */
 
 typedef enum {
   STILES_OK = 0,
@@ -211,6 +212,35 @@ int64_t stiles_kernel_launches(void);
  * STILES_ERR_INVALID (null pointer, n < 1, tile < 1, too many tile columns), STILES_ERR_CUDA. */
 stiles_status stiles_logdet_tiles_noalloc(const double* tiles, const int64_t* tcolptr, int64_t n, int32_t tile,
                                           double* out, void* stream);
+
+/* Batched factorization (Appendix A: many independent factorizations run concurrently).
+ * stiles_batch_create: device arrays for `count` plans (same precision and block size; any sizes
+ *   and patterns), one merged ticket list interleaving their task lists in proportion to their
+ *   lengths (each matrix keeps its own topological order), and a CUDA graph of the per-call work
+ *   (tile zeroing, scatter, one persistent kernel).  The plans must outlive the batch.
+ * stiles_batch_factorize: values[i] = the nnz values of matrix i, host or device; the call copies
+ *   them in, replays the graph on a private stream ordered after `stream`, waits, and reports per
+ *   matrix: statuses[i] (OK, NOT_SPD, TIMEOUT) and infos[i] (first bad permuted column, 1-based,
+ *   else 0); either array may be NULL.  Returns the first failure or OK.
+ * stiles_batch_factor: a borrowed factor handle of matrix `index` for stiles_logdet, stiles_solve
+ *   and stiles_factor_tiles; it lives until the batch is destroyed (do not destroy it).
+ * stiles_batch_logdet: all log-determinants in one launch, out[count] on the host. */
+stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count, stiles_batch** out);
+stiles_status stiles_batch_factorize(stiles_batch* batch, const double* const* values, void* stream,
+                                     stiles_status* statuses, int64_t* infos);
+stiles_status stiles_batch_factor(const stiles_batch* batch, int32_t index, stiles_factor** out);
+stiles_status stiles_batch_logdet(stiles_batch* batch, double* out, void* stream);
+void stiles_batch_destroy(stiles_batch* batch);
+
+/* Tile-size autotuner (Section IV.B and Appendix B: the tile size trades the extra flops of
+ * padded tiles against the parallelism of the task graph).  For each candidate in tiles[ntiles]
+ * the pattern is analysed with opts (opts->tile ignored); candidates whose task flops exceed 4x
+ * the smallest are skipped, the others are factorized from `values` (host or device) and timed
+ * with CUDA events on `stream` (best of two).  *best_tile receives the fastest; ms[i] (may be
+ * NULL) its time per candidate, -1 when skipped or failed. */
+stiles_status stiles_autotune(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                              const stiles_opts* opts, const int32_t* tiles, int32_t ntiles, const double* values,
+                              void* stream, int32_t* best_tile, double* ms);
 
 /* Measured FP64 DFMA throughput of the current device in TFLOP/s (a fixed-length FMA loop
  * on every SM, timed with CUDA events), used as the roofline denominator of the FP64 path. */

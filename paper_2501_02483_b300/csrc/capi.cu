@@ -120,6 +120,8 @@ struct stiles_factor {
   cudaEvent_t done = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, persistent kernel start / end
   long long* trace[3] = {nullptr, nullptr, nullptr};  // per-ticket stamps: factor, forward, backward
+  unsigned long long* info = nullptr;  // first bad pivot column (&ctl[0].info, or a batch slot)
+  bool view = false;                   // tiles and values belong to a stiles_batch
   bool pending = false;
 };
 
@@ -230,6 +232,12 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
 
 void free_factor(stiles_factor* f) {
   if (!f) return;
+  if (f->view) {  // the batch owns the factor arrays; only the solve workspace is the view's
+    f->values = f->tiles = f->scratch = f->invdiag = f->ldiag = nullptr;
+    f->tiles32 = f->scratch32 = f->invdiag32 = nullptr;
+    f->tiles16 = nullptr;
+    f->flags = nullptr;
+  }
   cudaFree(f->values);
   cudaFree(f->tiles);
   cudaFree(f->scratch);
@@ -289,45 +297,64 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
                 std::string("factor allocation: ") + cudaGetErrorString(e));
   }
+  f->info = &f->ctl[0].info;
   *out = f;
   return STILES_OK;
+}
+
+dev::MatCtx mat_ctx(const stiles_plan* p, stiles_factor* f) {
+  dev::MatCtx c;
+  c.tiles = f->tiles;
+  c.scratch = f->scratch;
+  c.invdiag = f->invdiag;
+  c.tasks = p->dev->fac.tasks;
+  c.pairs = p->dev->fac.pairs;
+  c.parts = p->dev->fac.parts;
+  c.flags = f->flags;
+  c.sflags = f->flags + p->nsub;
+  c.info = f->info;
+  c.trace = f->trace[0];
+  return c;
+}
+
+dev::LPMatCtx lp_mat_ctx(const stiles_plan* p, stiles_factor* f) {
+  dev::LPMatCtx c;
+  c.tiles32 = f->tiles32;
+  c.tiles16 = f->tiles16;
+  c.scratch = f->scratch32;
+  c.invdiag32 = f->invdiag32;
+  c.ldiag = f->ldiag;
+  c.tasks = p->dev->fac.tasks;
+  c.pairs = p->dev->fac.pairs;
+  c.parts = p->dev->fac.parts;
+  c.flags = f->flags;
+  c.sflags = f->flags + p->nsub;
+  c.info = f->info;
+  c.trace = f->trace[0];
+  return c;
 }
 
 template <int B>
 cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
   dev::FactorArgs a;
-  a.tiles = f->tiles;
-  a.scratch = f->scratch;
-  a.invdiag = f->invdiag;
-  a.tasks = p->dev->fac.tasks;
+  a.single = mat_ctx(p, f);
+  a.mats = nullptr;
+  a.tickets = nullptr;
   a.ntasks = p->dev->fac.ntasks;
-  a.pairs = p->dev->fac.pairs;
-  a.parts = p->dev->fac.parts;
-  a.flags = f->flags;
-  a.sflags = f->flags + p->nsub;
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
-  a.trace = f->trace[0];
   dev::factor_f64_kernel<B><<<p->dev->grid_factor, 128, dev::FactorCfg<B>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
   dev::LPArgs a;
-  a.tiles32 = f->tiles32;
-  a.tiles16 = f->tiles16;
-  a.scratch = f->scratch32;
-  a.invdiag32 = f->invdiag32;
-  a.ldiag = f->ldiag;
-  a.tasks = p->dev->fac.tasks;
+  a.single = lp_mat_ctx(p, f);
+  a.mats = nullptr;
+  a.tickets = nullptr;
   a.ntasks = p->dev->fac.ntasks;
-  a.pairs = p->dev->fac.pairs;
-  a.parts = p->dev->fac.parts;
-  a.flags = f->flags;
-  a.sflags = f->flags + p->nsub;
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
-  a.trace = f->trace[0];
   a.fp16 = p->opts.precision == STILES_PREC_F16 ? 1 : 0;
   dev::factor_lp_kernel<<<p->dev->grid_factor, 128, dev::LP_SMEM, s>>>(a);
   return cudaGetLastError();
@@ -832,6 +859,433 @@ stiles_status stiles_probe_fp64_peak(double* tflops) {
   cudaFree(d);
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, cudaGetErrorString(e));
   *tflops = 2.0 * 8 * double(iters) * threads * blocks / (double(ms) * 1e-3) / 1e12;
+  return STILES_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched factorization (many matrices, one persistent launch).  The batch owns
+// concatenated device arrays for every matrix (values, tiles, flags, ...), a
+// merged ticket list that interleaves the matrices' task lists in proportion
+// to their lengths (each matrix keeps its own topological order, so the launch
+// stays deadlock-free), and a CUDA graph of the per-call device work (zeroing,
+// scatter, the persistent kernel).  Per-matrix factor views borrow the batch's
+// arrays for logdet and solves.
+// ---------------------------------------------------------------------------
+struct stiles_batch {
+  std::vector<const stiles_plan*> plans;
+  std::vector<stiles_factor*> views;
+  bool lp = false;
+  int B = 0;
+  int device = -1;
+  int fp16 = 0;
+  int64_t nnz_total = 0, pad_total = 0, tile_elems = 0, scratch_elems = 0, diag_elems = 0, flag_total = 0;
+  std::vector<int64_t> val_off;
+  double* values = nullptr;
+  int64_t* map = nullptr;
+  int64_t* pad = nullptr;
+  double* tiles = nullptr;
+  double* scratch = nullptr;
+  double* invdiag = nullptr;
+  float* tiles32 = nullptr;
+  uint16_t* tiles16 = nullptr;
+  float* scratch32 = nullptr;
+  float* invdiag32 = nullptr;
+  double* ldiag = nullptr;
+  int* flags = nullptr;
+  unsigned long long* infos = nullptr;
+  stiles::dev::Ctl* ctl = nullptr;
+  void* dmats = nullptr;
+  int2* dtickets = nullptr;
+  int ntickets = 0;
+  int grid = 0;
+  long long spin_limit = 0;
+  double* logdet_out = nullptr;
+  void* dlog = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+struct BatchLogCtx {
+  const double* tiles;      // FP64 factor tiles (FP64 path)
+  const int32_t* diag_sub;  // diagonal sub-tile of each sub-column
+  const double* ldiag;      // FP64 diagonal entries (mixed-precision path)
+  int64_t n;
+  int B;
+  int pad0;
+};
+
+// One block per matrix, each summing 2 log L_ii over its rows in a fixed order.
+__global__ void batch_logdet_kernel(const BatchLogCtx* ctx, double* out) {
+  __shared__ double red[256];
+  const BatchLogCtx c = ctx[blockIdx.x];
+  double s = 0.0;
+  for (int64_t g = threadIdx.x; g < c.n; g += blockDim.x) {
+    const double l = c.ldiag ? c.ldiag[g]
+                             : c.tiles[int64_t(c.diag_sub[g / c.B]) * c.B * c.B + (g % c.B) * c.B + (g % c.B)];
+    s += 2.0 * log(l);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+void free_batch(stiles_batch* b) {
+  if (!b) return;
+  for (stiles_factor* v : b->views) free_factor(v);
+  cudaFree(b->values);
+  cudaFree(b->map);
+  cudaFree(b->pad);
+  cudaFree(b->tiles);
+  cudaFree(b->scratch);
+  cudaFree(b->invdiag);
+  cudaFree(b->tiles32);
+  cudaFree(b->tiles16);
+  cudaFree(b->scratch32);
+  cudaFree(b->invdiag32);
+  cudaFree(b->ldiag);
+  cudaFree(b->flags);
+  cudaFree(b->infos);
+  cudaFree(b->ctl);
+  cudaFree(b->dmats);
+  cudaFree(b->dtickets);
+  cudaFree(b->logdet_out);
+  cudaFree(b->dlog);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Enqueue the per-call device work after the values are in place.
+stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
+  const size_t tbytes = b->lp ? sizeof(float) : sizeof(double);
+  if (b->lp) {
+    CUDA_TRY(cudaMemsetAsync(b->tiles32, 0, size_t(b->tile_elems) * tbytes, st));
+    dev::scatter_f32_kernel<<<grid_for(b->nnz_total, 256), 256, 0, st>>>(b->tiles32, b->values, b->map, b->nnz_total);
+  } else {
+    CUDA_TRY(cudaMemsetAsync(b->tiles, 0, size_t(b->tile_elems) * tbytes, st));
+    dev::scatter_kernel<<<grid_for(b->nnz_total, 256), 256, 0, st>>>(b->tiles, b->values, b->map, b->nnz_total);
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (b->pad_total) {
+    if (b->lp)
+      dev::set_ones_kernel<float><<<grid_for(b->pad_total, 128), 128, 0, st>>>(b->tiles32, b->pad, b->pad_total);
+    else
+      dev::set_ones_kernel<double><<<grid_for(b->pad_total, 128), 128, 0, st>>>(b->tiles, b->pad, b->pad_total);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaMemsetAsync(b->flags, 0, size_t(b->flag_total) * sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(b->infos, 0xFF, b->plans.size() * sizeof(unsigned long long), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->ctl, 1);
+  CUDA_TRY(cudaGetLastError());
+  if (b->lp) {
+    dev::LPArgs a{};
+    a.mats = static_cast<const dev::LPMatCtx*>(b->dmats);
+    a.tickets = b->dtickets;
+    a.ntasks = b->ntickets;
+    a.ctl = b->ctl;
+    a.spin_limit = b->spin_limit;
+    a.fp16 = b->fp16;
+    dev::factor_lp_kernel<<<b->grid, 128, dev::LP_SMEM, st>>>(a);
+  } else {
+    dev::FactorArgs a{};
+    a.mats = static_cast<const dev::MatCtx*>(b->dmats);
+    a.tickets = b->dtickets;
+    a.ntasks = b->ntickets;
+    a.ctl = b->ctl;
+    a.spin_limit = b->spin_limit;
+    switch (b->B) {
+      case 16: dev::factor_f64_kernel<16><<<b->grid, 128, dev::FactorCfg<16>::SMEM, st>>>(a); break;
+      case 32: dev::factor_f64_kernel<32><<<b->grid, 128, dev::FactorCfg<32>::SMEM, st>>>(a); break;
+      default: dev::factor_f64_kernel<64><<<b->grid, 128, dev::FactorCfg<64>::SMEM, st>>>(a); break;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  return STILES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count, stiles_batch** out) {
+  if (!plans || count < 1 || !out) return fail(STILES_ERR_INVALID, "bad argument");
+  *out = nullptr;
+  stiles_batch* b = new (std::nothrow) stiles_batch();
+  if (!b) return fail(STILES_ERR_NOMEM, "host allocation");
+  auto bail = [&](stiles_status s) {
+    free_batch(b);
+    return s;
+  };
+  b->plans.assign(plans, plans + count);
+  b->lp = plans[0]->opts.precision != STILES_PREC_F64;
+  b->B = plans[0]->B;
+  b->fp16 = plans[0]->opts.precision == STILES_PREC_F16 ? 1 : 0;
+  b->spin_limit = plans[0]->opts.spin_limit;
+  CUDA_TRY(cudaGetDevice(&b->device));
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = plans[i];
+    if (!p || p->opts.precision != plans[0]->opts.precision || p->B != b->B)
+      return bail(fail(STILES_ERR_INVALID, "batched plans must share precision and block size"));
+    stiles_status s = ensure_dev_plan(p);
+    if (s != STILES_OK) return bail(s);
+    b->spin_limit = std::max<long long>(b->spin_limit, p->opts.spin_limit);
+  }
+  // offsets of every matrix inside the concatenated arrays
+  const int64_t TB = int64_t(b->B) * b->B;
+  std::vector<int64_t> t_off(count), s_off(count), d_off(count), f_off(count);
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = plans[i];
+    b->val_off.push_back(b->nnz_total);
+    t_off[i] = b->tile_elems;
+    s_off[i] = b->scratch_elems;
+    d_off[i] = b->diag_elems;
+    f_off[i] = b->flag_total;
+    b->nnz_total += p->nnz;
+    b->pad_total += int64_t(p->pad.size());
+    b->tile_elems += p->nsub * TB;
+    b->scratch_elems += std::max<int64_t>(p->graph.nscratch, 1) * TB;
+    b->diag_elems += p->nsb * b->B;
+    b->flag_total += p->nsub + std::max<int64_t>(p->graph.nscratch, 1);
+  }
+  std::vector<int64_t> hmap(b->nnz_total), hpad;
+  hpad.reserve(b->pad_total);
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = plans[i];
+    for (int64_t e = 0; e < p->nnz; ++e) hmap[b->val_off[i] + e] = p->scatter[e] + t_off[i];
+    for (int64_t q : p->pad) hpad.push_back(q + t_off[i]);
+  }
+  cudaError_t e = cudaMalloc(&b->values, size_t(b->nnz_total) * sizeof(double));
+  if (e == cudaSuccess) e = upload(&b->map, hmap);
+  if (e == cudaSuccess) e = upload(&b->pad, hpad);
+  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->tiles, size_t(b->tile_elems) * sizeof(double));
+  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->scratch, size_t(b->scratch_elems) * sizeof(double));
+  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->invdiag, size_t(b->diag_elems) * sizeof(double));
+  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->tiles32, size_t(b->tile_elems) * sizeof(float));
+  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->tiles16, size_t(b->tile_elems) * sizeof(uint16_t));
+  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->scratch32, size_t(b->scratch_elems) * sizeof(float));
+  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->invdiag32, size_t(b->diag_elems) * sizeof(float));
+  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->ldiag, size_t(b->diag_elems) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->flags, size_t(b->flag_total) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->infos, size_t(count) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctl, sizeof(dev::Ctl));
+  if (e == cudaSuccess) e = cudaMalloc(&b->logdet_out, size_t(count) * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                     std::string("batch allocation: ") + cudaGetErrorString(e)));
+  }
+  hmap.clear();
+  hmap.shrink_to_fit();
+  // factor views and per-matrix contexts
+  std::vector<dev::MatCtx> mats;
+  std::vector<dev::LPMatCtx> lmats;
+  std::vector<BatchLogCtx> logs(count);
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = plans[i];
+    stiles_factor* v = new (std::nothrow) stiles_factor();
+    if (!v) return bail(fail(STILES_ERR_NOMEM, "host allocation"));
+    b->views.push_back(v);
+    v->plan = p;
+    v->device = b->device;
+    v->view = true;
+    v->lp = b->lp;
+    v->values = b->values + b->val_off[i];
+    v->flags = b->flags + f_off[i];
+    v->info = b->infos + i;
+    if (b->lp) {
+      v->tiles32 = b->tiles32 + t_off[i];
+      v->tiles16 = b->tiles16 + t_off[i];
+      v->scratch32 = b->scratch32 + s_off[i];
+      v->invdiag32 = b->invdiag32 + d_off[i];
+      v->ldiag = b->ldiag + d_off[i];
+    } else {
+      v->tiles = b->tiles + t_off[i];
+      v->scratch = b->scratch + s_off[i];
+      v->invdiag = b->invdiag + d_off[i];
+    }
+    CUDA_TRY(cudaMalloc(&v->ctl, 3 * sizeof(dev::Ctl)));
+    CUDA_TRY(cudaMalloc(&v->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&v->norms, 2 * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming));
+    for (int k = 0; k < 3; ++k) CUDA_TRY(cudaEventCreate(&v->ev[k]));
+    if (b->lp) lmats.push_back(lp_mat_ctx(p, v));
+    else mats.push_back(mat_ctx(p, v));
+    logs[i] = BatchLogCtx{v->tiles, p->dev->diag_sub, v->ldiag, p->n, b->B, 0};
+  }
+  if (b->lp) e = upload(reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
+  else e = upload(reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
+  if (e == cudaSuccess) e = upload(reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
+  if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
+  // merged tickets: matrix i's task j at key (j + 0.5) / n_i, ties by matrix
+  std::vector<std::pair<double, int2>> keyed;
+  for (int i = 0; i < count; ++i) {
+    const int64_t nt = int64_t(plans[i]->graph.tasks.size());
+    for (int64_t j = 0; j < nt; ++j) keyed.push_back({(double(j) + 0.5) / double(nt), make_int2(i, int(j))});
+  }
+  std::stable_sort(keyed.begin(), keyed.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+    return x.first < y.first;
+  });
+  std::vector<int2> tick(keyed.size());
+  for (size_t q = 0; q < keyed.size(); ++q) tick[q] = keyed[q].second;
+  if (tick.size() >= size_t(1) << 31) return bail(fail(STILES_ERR_UNSUPPORTED, "too many tasks in one batch"));
+  b->ntickets = int(tick.size());
+  e = upload(&b->dtickets, tick);
+  if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
+  // persistent grid: as many resident CTAs as fit
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  int per_sm = std::max(1, plans[0]->dev->grid_factor / std::max(1, sms));
+  if (b->lp) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::factor_lp_kernel, 128, dev::LP_SMEM);
+    per_sm = std::min(per_sm, 4);
+  } else {
+    switch (b->B) {
+      case 16: factor_occupancy<16>(&per_sm); break;
+      case 32: factor_occupancy<32>(&per_sm); break;
+      default: factor_occupancy<64>(&per_sm); break;
+    }
+  }
+  if (plans[0]->opts.ctas_per_sm > 0) per_sm = std::min(per_sm, int(plans[0]->opts.ctas_per_sm));
+  b->grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(std::max(per_sm, 1)) * sms, b->ntickets)));
+  // private stream + graph of the per-call work
+  CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    stiles_status s = batch_enqueue(b, b->stream);
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (s != STILES_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bail(s);
+    }
+    if (ce != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
+    ce = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)));
+  }
+  *out = b;
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* values, void* stream,
+                                     stiles_status* statuses, int64_t* infos) {
+  if (!b || !values) return fail(STILES_ERR_INVALID, "null argument");
+  const int count = int(b->plans.size());
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaEventRecord(b->ev_in, st));
+  CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  for (int i = 0; i < count; ++i) {
+    if (!values[i]) return fail(STILES_ERR_INVALID, "null values pointer");
+    CUDA_TRY(cudaMemcpyAsync(b->values + b->val_off[i], values[i], size_t(b->plans[i]->nnz) * sizeof(double),
+                             cudaMemcpyDefault, b->stream));
+  }
+  CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+  count_launch(b->pad_total ? 4 : 3);
+  CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
+  CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
+  CUDA_TRY(cudaEventSynchronize(b->ev_out));
+  for (stiles_factor* v : b->views) v->stream = st;
+  dev::Ctl c;
+  CUDA_TRY(cudaMemcpy(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> hinfo(count);
+  CUDA_TRY(cudaMemcpy(hinfo.data(), b->infos, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  stiles_status worst = STILES_OK;
+  for (int i = 0; i < count; ++i) {
+    stiles_status s = STILES_OK;
+    if (c.status != 0) s = STILES_ERR_TIMEOUT;
+    else if (hinfo[i] != ~0ull) s = STILES_ERR_NOT_SPD;
+    if (statuses) statuses[i] = s;
+    if (infos) infos[i] = hinfo[i] == ~0ull ? 0 : int64_t(hinfo[i]);
+    if (s != STILES_OK && worst == STILES_OK) worst = s;
+  }
+  if (worst == STILES_ERR_TIMEOUT) return fail(worst, "device wait timed out in the batched launch");
+  if (worst == STILES_ERR_NOT_SPD) return fail(worst, "a matrix of the batch is not positive definite");
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_factor(const stiles_batch* b, int32_t index, stiles_factor** out) {
+  if (!b || !out || index < 0 || index >= int32_t(b->views.size())) return fail(STILES_ERR_INVALID, "bad argument");
+  *out = b->views[index];
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_logdet(stiles_batch* b, double* out, void* stream) {
+  if (!b || !out) return fail(STILES_ERR_INVALID, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int count = int(b->plans.size());
+  batch_logdet_kernel<<<count, 256, 0, st>>>(static_cast<const BatchLogCtx*>(b->dlog), b->logdet_out);
+  CUDA_TRY(cudaGetLastError());
+  count_launch();
+  CUDA_TRY(cudaMemcpyAsync(out, b->logdet_out, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return STILES_OK;
+}
+
+void stiles_batch_destroy(stiles_batch* b) { free_batch(b); }
+
+}  // extern "C"
+
+extern "C" {
+
+stiles_status stiles_autotune(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                              const stiles_opts* opts, const int32_t* tiles, int32_t ntiles, const double* values,
+                              void* stream, int32_t* best_tile, double* ms) {
+  if (!tiles || ntiles < 1 || !values || !best_tile) return fail(STILES_ERR_INVALID, "bad argument");
+  stiles_opts o;
+  if (opts) o = *opts;
+  else stiles::default_opts(&o);
+  std::vector<stiles_plan*> plans(ntiles, nullptr);
+  std::vector<int64_t> flops(ntiles, -1);
+  int64_t fmin = -1;
+  for (int i = 0; i < ntiles; ++i) {
+    o.tile = tiles[i];
+    if (stiles_analyze(n, colptr, rowidx, n_arrow, &o, &plans[i]) != STILES_OK || !plans[i]->executable) continue;
+    stiles_plan_info inf;
+    stiles_plan_get_info(plans[i], &inf);
+    flops[i] = inf.flops_total;
+    if (fmin < 0 || flops[i] < fmin) fmin = flops[i];
+  }
+  double best = -1.0;
+  stiles_status result = STILES_ERR_INVALID;
+  for (int i = 0; i < ntiles; ++i) {
+    if (ms) ms[i] = -1.0;
+    // a tile whose padding multiplies the work beyond 4x cannot win on parallelism alone
+    if (!plans[i] || flops[i] < 0 || flops[i] > 4 * fmin) continue;
+    stiles_factor* f = nullptr;
+    stiles_status s = stiles_factorize(plans[i], values, stream, &f, nullptr);
+    double t = 1e300;
+    for (int rep = 0; rep < 2 && s == STILES_OK; ++rep) {
+      s = stiles_factorize(plans[i], values, stream, &f, nullptr);
+      double call = 0.0;
+      if (s == STILES_OK && stiles_factor_timing(f, &call, nullptr) == STILES_OK) t = std::min(t, call);
+    }
+    stiles_factor_destroy(f);
+    if (s != STILES_OK) {
+      result = s;
+      continue;
+    }
+    if (ms) ms[i] = t;
+    if (best < 0 || t < best) {
+      best = t;
+      *best_tile = tiles[i];
+      result = STILES_OK;
+    }
+  }
+  for (stiles_plan* p : plans) stiles_plan_destroy(p);
+  if (result != STILES_OK) return fail(result, "no candidate tile size could be factorized");
   return STILES_OK;
 }
 

@@ -41,19 +41,27 @@ struct FactorCfg {
 constexpr int kTargetShift = 30;
 constexpr int kIndexMask = (1 << 30) - 1;
 
-struct FactorArgs {
+// One matrix of a launch (a batched launch carries one per matrix).
+struct MatCtx {
   double* tiles;    // nsub * B * B, sub-tile s at s * B * B, column-major
   double* scratch;  // nscratch * B * B (tree partials, stored negated)
   double* invdiag;  // nsb * B: 1 / L_jj of each diagonal sub-tile
   const DevTask* tasks;
-  int ntasks;
   const int32_t* pairs;
   const int32_t* parts;
   int* flags;   // per sub-tile: 1 when final
   int* sflags;  // per scratch tile: 1 when final
-  Ctl* ctl;
+  unsigned long long* info;  // first bad pivot column of this matrix (atomicMin)
+  long long* trace;          // optional, 4 per task: start, dependencies ready, done, SM id
+};
+
+struct FactorArgs {
+  MatCtx single;        // the matrix of a one-matrix launch (mats == NULL)
+  const MatCtx* mats;   // batched launch: one context per matrix (device memory)
+  const int2* tickets;  // batched launch: (matrix, task) per ticket; NULL: one matrix, ticket = task
+  int ntasks;           // tickets in the launch
+  Ctl* ctl;             // ticket counter, timeout status, abort flag of the launch
   long long spin_limit;
-  long long* trace;  // optional, 4 per ticket: start, dependencies ready, done, SM id
 };
 
 // All threads have stored the tile; after the barrier, thread 0's release
@@ -197,8 +205,15 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     __syncthreads();
     const int t = sTicket;
     if (t < 0) break;
-    const DevTask tk = a.tasks[t];
-    long long* const trace = a.trace ? a.trace + 4 * size_t(t) : nullptr;
+    int mi = 0, ti = t;
+    if (a.tickets) {
+      const int2 v = a.tickets[t];
+      mi = v.x;
+      ti = v.y;
+    }
+    const MatCtx mc = a.mats ? a.mats[mi] : a.single;
+    const DevTask tk = mc.tasks[ti];
+    long long* const trace = mc.trace ? mc.trace + 4 * size_t(ti) : nullptr;
     unsigned long long t_ready = 0;
     if (trace && tid == 0) {
       t_ready = globaltimer();
@@ -213,12 +228,12 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc1[m] = 0.0;
     } else {
-      const double* src = a.tiles + size_t(tk.out) * TILE;
+      const double* src = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc1[m] = src[(q + RPT * m) * B + row];
     }
     if (chain) {
-      const double* src = a.tiles + size_t(tk.out2) * TILE;
+      const double* src = mc.tiles + size_t(tk.out2) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc2[m] = src[(q + RPT * m) * B + row];
     } else {
@@ -242,18 +257,18 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
           const double* g1;
           const double* g2 = nullptr;
           if (issued < nq) {
-            const int s = a.parts[tk.qb + issued] & kIndexMask;
-            f1 = a.sflags + s;
-            g1 = a.scratch + size_t(s) * TILE;
+            const int s = mc.parts[tk.qb + issued] & kIndexMask;
+            f1 = mc.sflags + s;
+            g1 = mc.scratch + size_t(s) * TILE;
           } else {
             const int pidx = tk.pb + issued - nq;
-            const int pa = a.pairs[2 * pidx] & kIndexMask;
-            const int pb = a.pairs[2 * pidx + 1];
-            f1 = a.flags + pa;
-            g1 = a.tiles + size_t(pa) * TILE;
+            const int pa = mc.pairs[2 * pidx] & kIndexMask;
+            const int pb = mc.pairs[2 * pidx + 1];
+            f1 = mc.flags + pa;
+            g1 = mc.tiles + size_t(pa) * TILE;
             if (pb != pa) {
-              f2 = a.flags + pb;
-              g2 = a.tiles + size_t(pb) * TILE;
+              f2 = mc.flags + pb;
+              g2 = mc.tiles + size_t(pb) * TILE;
             }
           }
           if (issued == it) {
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       phase ^= (1u << st);
       const double* sA = sStage + st * 2 * TILE;
       if (it < nq) {
-        if ((a.parts[tk.qb + it] >> kTargetShift) == 0) {
+        if ((mc.parts[tk.qb + it] >> kTargetShift) == 0) {
 #pragma unroll
           for (int m = 0; m < CPT; ++m) acc1[m] += sA[row + (q + RPT * m) * B];
         } else {
@@ -297,8 +312,8 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
         }
       } else {
         const int pidx = tk.pb + it - nq;
-        const int raw = a.pairs[2 * pidx];
-        const double* sB = ((raw & kIndexMask) == a.pairs[2 * pidx + 1]) ? sA : sA + TILE;
+        const int raw = mc.pairs[2 * pidx];
+        const double* sB = ((raw & kIndexMask) == mc.pairs[2 * pidx + 1]) ? sA : sA + TILE;
         if ((raw >> kTargetShift) == 0) {
 #pragma unroll 4
           for (int p = 0; p < B; ++p) {
@@ -332,36 +347,36 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
 
     if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) {
-      double* dst = a.scratch + size_t(tk.out) * TILE;
+      double* dst = mc.scratch + size_t(tk.out) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
-      publish(a.sflags + tk.out);
+      publish(mc.sflags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
 
     if (tk.type == TASK_DIAG) {
       const int bad = potrf_tile<B>(acc1, sC, sPiv, sInv, sRs, row, q, tid);
-      if (bad >= 0 && tid == 0) atomicMin(&a.ctl->info, (unsigned long long)tk.col * B + bad + 1);
-      double* dst = a.tiles + size_t(tk.out) * TILE;
+      if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col * B + bad + 1);
+      double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
-      if (tid < B) a.invdiag[size_t(tk.col) * B + tid] = sInv[tid];
-      publish(a.flags + tk.out);
+      if (tid < B) mc.invdiag[size_t(tk.col) * B + tid] = sInv[tid];
+      publish(mc.flags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
 
     // ---- OFF and CHAIN: TRSM of `out` with L_kk once it is final ----
     if (tid == 0) {
-      if (!wait_flag(a.flags + tk.diag, 1, limit, a.ctl)) {
+      if (!wait_flag(mc.flags + tk.diag, 1, limit, a.ctl)) {
         raise_timeout(a.ctl, t);
         sAbort = 1;
       } else {
         if (trace) t_ready = globaltimer();
         fence_proxy_async_global();
         mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
-        tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+        tma_load_1d(sL, mc.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
       }
     }
     __syncthreads();
@@ -376,18 +391,18 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
     double inv[CPT];
     {
-      const double* iv = a.invdiag + size_t(tk.col) * B;
+      const double* iv = mc.invdiag + size_t(tk.col) * B;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) inv[m] = __ldcg(iv + q + RPT * m);
     }
     trsm_rows<B>(acc1, inv, sL, q, row_lane0);
     {
-      double* dst = a.tiles + size_t(tk.out) * TILE;
+      double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc1[m];
     }
     if (!chain) {
-      publish(a.flags + tk.out);
+      publish(mc.flags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < CPT; ++m) sL[(q + RPT * m) * B + row] = acc1[m];
-    publish(a.flags + tk.out);  // includes the barrier that makes sL visible to the CTA
+    publish(mc.flags + tk.out);  // includes the barrier that makes sL visible to the CTA
 #pragma unroll 4
     for (int p = 0; p < B; ++p) {
       const double av = sL[row + p * B];
@@ -404,14 +419,14 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
     }
     const int bad = potrf_tile<B>(acc2, sC, sPiv, sInv, sRs, row, q, tid);
-    if (bad >= 0 && tid == 0) atomicMin(&a.ctl->info, (unsigned long long)tk.col2 * B + bad + 1);
+    if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
     {
-      double* dst = a.tiles + size_t(tk.out2) * TILE;
+      double* dst = mc.tiles + size_t(tk.out2) * TILE;
 #pragma unroll
       for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = acc2[m];
     }
-    if (tid < B) a.invdiag[size_t(tk.col2) * B + tid] = sInv[tid];
-    publish(a.flags + tk.out2);
+    if (tid < B) mc.invdiag[size_t(tk.col2) * B + tid] = sInv[tid];
+    publish(mc.flags + tk.out2);
     if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
   }
 }

@@ -38,21 +38,28 @@ constexpr uint32_t LP_TMEM_COLS = 128;              // two 64-column FP32 accumu
 constexpr size_t LP_SMEM = size_t(LP_NSTAGE) * LP_STAGE_BYTES + LP_TILE * 8 + LP_TILE * 4 + 3 * LP_B * 8 +
                            (LP_NSTAGE * 2 + 2) * 8 + 64;
 
-struct LPArgs {
+struct LPMatCtx {
   float* tiles32;        // nsub * 64 * 64, column-major
   uint16_t* tiles16;     // nsub * 64 * 64, core-matrix layout, BF16 or FP16
   float* scratch;        // tree partials (negated sums), FP32 column-major
   float* invdiag32;      // nsb * 64: 1 / L_jj
   double* ldiag;         // nsb * 64: L_jj in FP64 (log-determinant)
   const DevTask* tasks;
-  int ntasks;
   const int32_t* pairs;
   const int32_t* parts;
   int* flags;
   int* sflags;
+  unsigned long long* info;
+  long long* trace;
+};
+
+struct LPArgs {
+  LPMatCtx single;       // the matrix of a one-matrix launch (mats == NULL)
+  const LPMatCtx* mats;  // batched launch: one context per matrix (device memory)
+  const int2* tickets;   // batched launch: (matrix, task) per ticket; NULL: one matrix
+  int ntasks;
   Ctl* ctl;
   long long spin_limit;
-  long long* trace;
   int fp16;              // 0: BF16 operands, 1: FP16 operands
 };
 
@@ -109,17 +116,17 @@ __device__ __forceinline__ uint16_t to_lp(float x, int fp16) {
 
 // Store row `r` (64 FP32 values) of a finished tile: FP32 column-major and the
 // 16-bit core-matrix copy (8 x 16-byte vectors).
-__device__ __forceinline__ void lp_store_row(const LPArgs& a, int sub, int r, const float (&x)[LP_B]) {
-  float* t32 = a.tiles32 + size_t(sub) * LP_TILE;
+__device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int sub, int r, const float (&x)[LP_B]) {
+  float* t32 = mc.tiles32 + size_t(sub) * LP_TILE;
 #pragma unroll
   for (int c = 0; c < LP_B; ++c) t32[c * LP_B + r] = x[c];
-  unsigned char* t16 = reinterpret_cast<unsigned char*>(a.tiles16 + size_t(sub) * LP_TILE);
+  unsigned char* t16 = reinterpret_cast<unsigned char*>(mc.tiles16 + size_t(sub) * LP_TILE);
 #pragma unroll
   for (int kb = 0; kb < LP_B / 8; ++kb) {
     uint32_t w[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h)
-      w[h] = uint32_t(to_lp(x[kb * 8 + 2 * h], a.fp16)) | (uint32_t(to_lp(x[kb * 8 + 2 * h + 1], a.fp16)) << 16);
+      w[h] = uint32_t(to_lp(x[kb * 8 + 2 * h], fp16)) | (uint32_t(to_lp(x[kb * 8 + 2 * h + 1], fp16)) << 16);
     *reinterpret_cast<uint4*>(t16 + lp_core_offset(r, kb * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
@@ -187,8 +194,15 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     __syncthreads();
     const int t = sTicket;
     if (t < 0) break;
-    const DevTask tk = a.tasks[t];
-    long long* const trace = a.trace ? a.trace + 4 * size_t(t) : nullptr;
+    int mi = 0, ti = t;
+    if (a.tickets) {
+      const int2 v = a.tickets[t];
+      mi = v.x;
+      ti = v.y;
+    }
+    const LPMatCtx mc = a.mats ? a.mats[mi] : a.single;
+    const DevTask tk = mc.tasks[ti];
+    long long* const trace = mc.trace ? mc.trace + 4 * size_t(ti) : nullptr;
     if (trace && tid == 0) {
       trace[0] = (long long)globaltimer();
       trace[3] = smid();
@@ -202,14 +216,14 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     if (tid == 0) {
       int issued = 0;
       auto issue = [&](int j, bool block) -> int {  // 1 issued, 0 not ready, -1 abort
-        const int raw = a.pairs[2 * (tk.pb + j)];
-        const int pa = raw & kIndexMask, pb = a.pairs[2 * (tk.pb + j) + 1];
+        const int raw = mc.pairs[2 * (tk.pb + j)];
+        const int pa = raw & kIndexMask, pb = mc.pairs[2 * (tk.pb + j) + 1];
         if (block) {
-          if (!(wait_flag(a.flags + pa, 1, limit, a.ctl) && (pb == pa || wait_flag(a.flags + pb, 1, limit, a.ctl)))) {
+          if (!(wait_flag(mc.flags + pa, 1, limit, a.ctl) && (pb == pa || wait_flag(mc.flags + pb, 1, limit, a.ctl)))) {
             raise_timeout(a.ctl, t);
             return -1;
           }
-        } else if (!(ld_acquire(a.flags + pa) == 1 && (pb == pa || ld_acquire(a.flags + pb) == 1))) {
+        } else if (!(ld_acquire(mc.flags + pa) == 1 && (pb == pa || ld_acquire(mc.flags + pb) == 1))) {
           return 0;
         }
         const int st = j % LP_NSTAGE;
@@ -221,8 +235,8 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
         unsigned char* sa = sStage + st * LP_STAGE_BYTES;
         fence_proxy_async_global();
         mbar_arrive_expect_tx(&full[st], (pb == pa ? 1u : 2u) * LP_OP_BYTES);
-        tma_load_1d(sa, a.tiles16 + size_t(pa) * LP_TILE, LP_OP_BYTES, &full[st]);
-        if (pb != pa) tma_load_1d(sa + 2 * LP_OP_BYTES, a.tiles16 + size_t(pb) * LP_TILE, LP_OP_BYTES, &full[st]);
+        tma_load_1d(sa, mc.tiles16 + size_t(pa) * LP_TILE, LP_OP_BYTES, &full[st]);
+        if (pb != pa) tma_load_1d(sa + 2 * LP_OP_BYTES, mc.tiles16 + size_t(pb) * LP_TILE, LP_OP_BYTES, &full[st]);
         return 1;
       };
       for (int it = 0; it < np; ++it) {
@@ -241,8 +255,8 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
         if (!mbar_wait_bounded(&full[st], (ph_full >> st) & 1u)) { aborted = true; break; }
         ph_full ^= 1u << st;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int raw = a.pairs[2 * (tk.pb + it)];
-        const int pa = raw & kIndexMask, pb = a.pairs[2 * (tk.pb + it) + 1];
+        const int raw = mc.pairs[2 * (tk.pb + it)];
+        const int pa = raw & kIndexMask, pb = mc.pairs[2 * (tk.pb + it) + 1];
         const int target = raw >> kTargetShift;
         unsigned char* sa = sStage + st * LP_STAGE_BYTES;
         const uint32_t a_addr = smem_addr(sa), b_addr = smem_addr(pb == pa ? sa : sa + 2 * LP_OP_BYTES);
@@ -281,10 +295,10 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       // x = A (or 0 for a partial) - D + sum of partial tiles
       const bool from_tile = !(tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE);
 #pragma unroll
-      for (int c = 0; c < LP_B; ++c) x1[c] = from_tile ? a.tiles32[size_t(tk.out) * LP_TILE + c * LP_B + r] : 0.f;
+      for (int c = 0; c < LP_B; ++c) x1[c] = from_tile ? mc.tiles32[size_t(tk.out) * LP_TILE + c * LP_B + r] : 0.f;
       if (chain) {
 #pragma unroll
-        for (int c = 0; c < LP_B; ++c) x2[c] = a.tiles32[size_t(tk.out2) * LP_TILE + c * LP_B + r];
+        for (int c = 0; c < LP_B; ++c) x2[c] = mc.tiles32[size_t(tk.out2) * LP_TILE + c * LP_B + r];
       }
       for (int acc = 0; acc < 2; ++acc) {
         if (!((used_mask >> acc) & 1)) continue;
@@ -304,16 +318,16 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     }
     // partial tiles: acquire their flags (thread 0), then every row adds them
     for (int qi = 0; qi < nq; ++qi) {
-      const int raw = a.parts[tk.qb + qi];
+      const int raw = mc.parts[tk.qb + qi];
       const int s = raw & kIndexMask;
-      if (tid == 0 && !wait_flag(a.sflags + s, 1, limit, a.ctl)) {
+      if (tid == 0 && !wait_flag(mc.sflags + s, 1, limit, a.ctl)) {
         raise_timeout(a.ctl, t);
         sAbort = 1;
       }
       __syncthreads();
       if (sAbort) { aborted = true; break; }
       if (warp < 2) {
-        const float* src = a.scratch + size_t(s) * LP_TILE;
+        const float* src = mc.scratch + size_t(s) * LP_TILE;
         if ((raw >> kTargetShift) == 0) {
 #pragma unroll
           for (int c = 0; c < LP_B; ++c) x1[c] += __ldcg(src + c * LP_B + r);
@@ -328,12 +342,12 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
 
     if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) {
       if (warp < 2) {
-        float* dst = a.scratch + size_t(tk.out) * LP_TILE;
+        float* dst = mc.scratch + size_t(tk.out) * LP_TILE;
         // partials hold the negated sum: x1 = -D (+ children), as in the FP64 kernel
 #pragma unroll
         for (int c = 0; c < LP_B; ++c) dst[c * LP_B + r] = x1[c];
       }
-      publish(a.sflags + tk.out);
+      publish(mc.sflags + tk.out);
       if (trace && tid == 0) trace[2] = (long long)globaltimer();
       continue;
     }
@@ -341,14 +355,14 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     if (tk.type == TASK_OFF || chain) {
       // ---- FP32 TRSM: x L_kk^T = s, row by row ----
       if (tid == 0) {
-        if (!wait_flag(a.flags + tk.diag, 1, limit, a.ctl)) {
+        if (!wait_flag(mc.flags + tk.diag, 1, limit, a.ctl)) {
           raise_timeout(a.ctl, t);
           sAbort = 1;
         } else {
           if (trace) trace[1] = (long long)globaltimer();
           fence_proxy_async_global();
           mbar_arrive_expect_tx(lbar, LP_TILE * 4);
-          tma_load_1d(sL, a.tiles32 + size_t(tk.diag) * LP_TILE, LP_TILE * 4, lbar);
+          tma_load_1d(sL, mc.tiles32 + size_t(tk.diag) * LP_TILE, LP_TILE * 4, lbar);
         }
       }
       __syncthreads();
@@ -356,7 +370,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       if (!mbar_wait_bounded(lbar, ph_l & 1u)) { aborted = true; break; }
       ph_l ^= 1u;
       if (warp < 2) {
-        const float* iv = a.invdiag32 + size_t(tk.col) * LP_B;
+        const float* iv = mc.invdiag32 + size_t(tk.col) * LP_B;
 #pragma unroll
         for (int j = 0; j < LP_B; ++j) {
           float s = x1[j];
@@ -364,10 +378,10 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
           for (int p = 0; p < j; ++p) s = fmaf(-x1[p], sL[j + p * LP_B], s);
           x1[j] = s * __ldcg(iv + j);
         }
-        lp_store_row(a, tk.out, r, x1);
+        lp_store_row(mc, a.fp16, tk.out, r, x1);
       }
       if (!chain) {
-        publish(a.flags + tk.out);
+        publish(mc.flags + tk.out);
         if (trace && tid == 0) trace[2] = (long long)globaltimer();
         continue;
       }
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
 #pragma unroll
         for (int c = 0; c < LP_B; ++c) sL[c * LP_B + r] = x1[c];
       }
-      publish(a.flags + tk.out);
+      publish(mc.flags + tk.out);
       if (warp < 2) {
 #pragma unroll 8
         for (int p = 0; p < LP_B; ++p) {
@@ -406,20 +420,20 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       for (int m = 0; m < FactorCfg<64>::CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + row];
       __syncthreads();
       const int bad = potrf_tile<64>(acc, sD, sPiv, sInv, sRs, row, q, tid);
-      if (bad >= 0 && tid == 0) atomicMin(&a.ctl->info, (unsigned long long)col * LP_B + bad + 1);
+      if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)col * LP_B + bad + 1);
       // L back to shared memory (column-major), then row-wise stores
 #pragma unroll
       for (int m = 0; m < FactorCfg<64>::CPT; ++m) sD[(q + RPT * m) * LP_B + row] = acc[m];
     }
     __syncthreads();
     if (warp < 2) {
-      float* t32 = a.tiles32 + size_t(out) * LP_TILE;
+      float* t32 = mc.tiles32 + size_t(out) * LP_TILE;
 #pragma unroll
       for (int c = 0; c < LP_B; ++c) t32[c * LP_B + r] = float(sD[c * LP_B + r]);
-      a.ldiag[size_t(col) * LP_B + r] = sD[r * LP_B + r];
-      a.invdiag32[size_t(col) * LP_B + r] = float(1.0 / sD[r * LP_B + r]);
+      mc.ldiag[size_t(col) * LP_B + r] = sD[r * LP_B + r];
+      mc.invdiag32[size_t(col) * LP_B + r] = float(1.0 / sD[r * LP_B + r]);
     }
-    publish(a.flags + out);
+    publish(mc.flags + out);
     if (trace && tid == 0) trace[2] = (long long)globaltimer();
   }
 

@@ -17,7 +17,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
 
 import numpy as np
 
-__all__ = ["Plan", "Factor", "StilesError", "lib", "probe_fp64_peak", "kernel_launches", "ORDER_NONE", "ORDER_RCM", "ORDER_AUTO", "ORDER_ND",
+__all__ = ["Plan", "Factor", "Batch", "autotune", "StilesError", "lib", "probe_fp64_peak", "kernel_launches", "ORDER_NONE", "ORDER_RCM", "ORDER_AUTO", "ORDER_ND",
            "PREC_F64", "PREC_BF16", "PREC_F16", "LIB_PATH"]
 
 ORDER_NONE, ORDER_RCM, ORDER_AUTO, ORDER_ND = 0, 1, 2, 3
@@ -79,12 +79,21 @@ def lib():
         L.stiles_plan_tasks.argtypes = [P, c_int32, P, POINTER(c_int64)]
         L.stiles_factor_refine_iters.argtypes = [P]
         L.stiles_factor_refine_iters.restype = c_int32
+        L.stiles_batch_create.argtypes = [P, c_int32, POINTER(c_void_p)]
+        L.stiles_batch_factorize.argtypes = [P, P, P, P, P]
+        L.stiles_batch_factor.argtypes = [P, c_int32, POINTER(c_void_p)]
+        L.stiles_batch_logdet.argtypes = [P, P, P]
+        L.stiles_batch_destroy.argtypes = [P]
+        L.stiles_batch_destroy.restype = None
+        L.stiles_autotune.argtypes = [c_int64, P, P, c_int64, POINTER(Opts), P, c_int32, P, P, POINTER(c_int32), P]
         L.stiles_kernel_launches.argtypes = []
         L.stiles_kernel_launches.restype = c_int64
         for name in ("stiles_analyze", "stiles_plan_get_info", "stiles_plan_perm", "stiles_plan_tilemap",
                      "stiles_factorize", "stiles_factorize_async", "stiles_factor_wait", "stiles_logdet",
                      "stiles_solve", "stiles_factor_tiles", "stiles_probe_fp64_peak", "stiles_factor_timing",
-                     "stiles_factor_set_trace", "stiles_factor_get_trace", "stiles_plan_tasks"):
+                     "stiles_factor_set_trace", "stiles_factor_get_trace", "stiles_plan_tasks",
+                     "stiles_batch_create", "stiles_batch_factorize", "stiles_batch_factor", "stiles_batch_logdet",
+                     "stiles_autotune"):
             getattr(L, name).restype = c_int32
         _LIB = L
     return _LIB
@@ -292,6 +301,78 @@ class Factor:
             self.close()
         except Exception:
             pass
+
+
+class _View(Factor):
+    """A factor borrowed from a Batch (no destroy: the batch owns it)."""
+
+    def __init__(self, plan, handle, batch):
+        self.plan = plan
+        self._h = handle
+        self._batch = batch
+
+    def close(self):
+        self._h = c_void_p()
+
+
+class Batch:
+    """Many plans factorized in one persistent launch (stiles_batch_*)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = c_void_p()
+        _check(lib().stiles_batch_create(arr, len(self.plans), ctypes.byref(h)))
+        self._h = h
+
+    def factorize(self, values, stream=None, raise_on_error=True):
+        """values: list of host numpy / device torch arrays; returns (statuses, infos)."""
+        self._keep = list(values)
+        arr = (c_void_p * len(values))(*[_ptr(v) for v in values])
+        statuses = np.zeros(len(values), dtype=np.int32)
+        infos = np.zeros(len(values), dtype=np.int64)
+        st = lib().stiles_batch_factorize(self._h, arr, _stream(stream), _ptr(statuses), _ptr(infos))
+        if raise_on_error:
+            _check(st)
+        return statuses, infos
+
+    def factor(self, i):
+        h = c_void_p()
+        _check(lib().stiles_batch_factor(self._h, i, ctypes.byref(h)))
+        return _View(self.plans[i], h, self)
+
+    def logdets(self, stream=None):
+        out = np.zeros(len(self.plans), dtype=np.float64)
+        _check(lib().stiles_batch_logdet(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().stiles_batch_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(m, tiles, values=None, stream=None, **kw):
+    """Fastest tile size among ``tiles`` for matrix ``m`` (stiles_autotune); returns (tile, ms list)."""
+    o = default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    colptr = np.ascontiguousarray(m["colptr"], dtype=np.int64)
+    rowidx = np.ascontiguousarray(m["rowidx"], dtype=np.int32)
+    cand = np.ascontiguousarray(tiles, dtype=np.int32)
+    ms = np.zeros(cand.size, dtype=np.float64)
+    best = c_int32(0)
+    vals = m["values"] if values is None else values
+    _check(lib().stiles_autotune(int(m["n"]), _ptr(colptr), _ptr(rowidx), int(m["n_arrow"]), ctypes.byref(o),
+                                 _ptr(cand), int(cand.size), _ptr(vals), _stream(stream), ctypes.byref(best),
+                                 _ptr(ms)))
+    return int(best.value), ms.tolist()
 
 
 def kernel_launches():

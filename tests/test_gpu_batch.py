@@ -1,0 +1,110 @@
+"""GPU checks of the batched factorization (one persistent launch over many
+matrices, Appendix A) and of the tile-size autotuner.
+
+* every matrix of a batch gets the oracle's log-determinant and a solve with a
+  1e-12 (FP64) / 1e-10 (refined BF16) residual;
+* each factor in the mix is bitwise identical to the same matrix factorized
+  alone (the task graph and the arithmetic per task do not depend on the
+  batch);
+* a non-SPD matrix is reported per matrix with the oracle's column, the others
+  still succeed;
+* replaying the batch with new values (a hyperparameter sweep) is correct.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analyze as oan
+from oracle import cholesky as och
+from paper_2501_02483_b300 import build, inputs
+from paper_2501_02483_b300 import stiles as st
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build_library()
+    st.lib()
+
+
+def _mats(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nb = int(rng.integers(300, 3000))
+        out.append(inputs.band_arrow(nb, int(rng.integers(0, 30)), int(rng.choice([8, 24, 60])), 0.3,
+                                     int(rng.integers(0, 1 << 30)), nrhs=2))
+    return out
+
+
+@pytest.mark.parametrize("prec,T,order", [(st.PREC_F64, 16, st.ORDER_NONE), (st.PREC_F64, 32, st.ORDER_ND),
+                                          (st.PREC_BF16, 64, st.ORDER_NONE)])
+def test_batch_matches_oracle_and_single(prec, T, order):
+    mats = _mats(9, 7 + T)
+    plans = [st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec) for m in mats]
+    batch = st.Batch(plans)
+    vals = [torch.from_numpy(m["values"]).cuda() for m in mats]
+    statuses, infos = batch.factorize(vals)
+    assert np.all(statuses == 0)
+    lds = batch.logdets()
+    tol_ld = 1e-12 if prec == st.PREC_F64 else 1e-7
+    tol_rr = 1e-12 if prec == st.PREC_F64 else 1e-10
+    for i, m in enumerate(mats):
+        p = oan.analyze(m, T, order)
+        Lo = och.factorize(m, p["perm"], T, p["tcolptr"], p["trowidx"])
+        ld_o = och.logdet(Lo, p["nt"])
+        v = batch.factor(i)
+        assert abs(lds[i] - ld_o) <= tol_ld * abs(ld_o)
+        assert abs(v.logdet() - lds[i]) <= 1e-13 * abs(lds[i])
+        x, rr = v.solve(m["rhs"], relres=True)
+        assert rr <= tol_rr
+        # alone vs in the mix: the same bits
+        f = st.Factor(plans[i])
+        f.factorize(vals[i])
+        assert np.array_equal(f.tiles(), v.tiles())
+    batch.close()
+
+
+def test_batch_reports_non_spd_per_matrix():
+    mats = _mats(5, 3)
+    bad = 2
+    vals = mats[bad]["values"].copy()
+    vals[mats[bad]["colptr"][100]] = -5.0  # a negative diagonal entry in column 100
+    mats[bad] = dict(mats[bad], values=vals)
+    plans = [st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_NONE) for m in mats]
+    batch = st.Batch(plans)
+    statuses, infos = batch.factorize([m["values"] for m in mats], raise_on_error=False)
+    with pytest.raises(och.NotSPD) as eo:
+        p = oan.analyze(mats[bad], 16, oan.ORDER_NONE)
+        och.factorize(mats[bad], p["perm"], 16, p["tcolptr"], p["trowidx"])
+    assert statuses[bad] == 2 and infos[bad] == eo.value.info
+    assert np.all(np.delete(statuses, bad) == 0)
+    batch.close()
+
+
+def test_batch_replay_with_new_values_theta_sweep():
+    mats = _mats(6, 11)
+    plans = [st.Plan.from_matrix(m, tile=16) for m in mats]
+    batch = st.Batch(plans)
+    batch.factorize([m["values"] for m in mats])
+    ld1 = batch.logdets()
+    thetas = np.linspace(0.5, 2.0, len(mats))
+    batch.factorize([m["values"] * t for m, t in zip(mats, thetas)])
+    ld2 = batch.logdets()
+    for m, t, a, b in zip(mats, thetas, ld1, ld2):
+        assert abs(b - (a + m["n"] * math.log(t))) <= 1e-12 * abs(b)
+    batch.close()
+
+
+def test_autotune_picks_a_candidate():
+    m = inputs.band_arrow(20000, 20, 100, 0.3, 1)
+    best, ms = st.autotune(m, [16, 32, 64, 512])
+    assert best in (16, 32, 64, 512)
+    assert ms[[16, 32, 64, 512].index(best)] == min(t for t in ms if t > 0)
+    assert ms[3] == -1.0 or ms[3] >= min(t for t in ms if t > 0)
