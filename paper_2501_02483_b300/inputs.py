@@ -38,6 +38,7 @@ __all__ = [
     "pure_arrowhead",
     "batch_sweep",
     "serving_stream",
+    "serving_workload",
     "scaled",
     "dense_from_csc",
 ]
@@ -349,3 +350,46 @@ def dense_from_csc(m):
     a[rowidx, cols] = values
     a[cols, rowidx] = values
     return a
+
+
+def serving_workload(count, rate=500.0, seed=0, n_lo=1_000, n_hi=200_000, hw_lo=32, hw_hi=512, w_hi=100,
+                     nrhs_hi=16, resolve_frac=0.3, pool=48, density=0.2):
+    """Request stream of the serving workload.
+
+    Arrivals are Poisson with the given rate.  A pool of ``pool`` distinct
+    patterns is drawn first (n log-uniform in [n_lo, n_hi], lower half-width
+    uniform in [hw_lo, hw_hi], arrow uniform in [0, w_hi], in-band density
+    ``density``); a new request takes one of them with all values scaled by a
+    fresh theta ~ U(0.5, 2) (same structure, new values, as in a
+    hyperparameter sweep); a re-solve request (probability ``resolve_frac``)
+    names an earlier new request.  Every request carries nrhs ~ U{1..nrhs_hi}
+    N(0,1) right-hand sides.  Returns (requests, arrivals) with requests as
+    dicts {"id", "kind", "key", "matrix", "rhs", "target"}.
+    """
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for k in range(pool):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        h = int(rng.integers(hw_lo, hw_hi + 1))
+        w = int(rng.integers(0, w_hi + 1))
+        shapes.append(band_arrow(max(n - w, 1), w, min(h, max(n - w - 1, 1)), density, int(rng.integers(0, 2**31 - 1)),
+                                 nrhs=0, name=f"serve{k}"))
+    t = 0.0
+    reqs, arrivals, news = [], [], []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        nrhs = int(rng.integers(1, nrhs_hi + 1))
+        if news and rng.random() < resolve_frac:
+            tgt = news[int(rng.integers(0, len(news)))]
+            n = reqs[tgt]["matrix"]["n"]
+            reqs.append({"id": i, "kind": "resolve", "key": None, "matrix": None,
+                         "rhs": np.asfortranarray(rng.normal(0.0, 1.0, (n, nrhs))), "target": tgt})
+        else:
+            k = int(rng.integers(0, pool))
+            theta = float(rng.uniform(0.5, 2.0))
+            base = shapes[k]
+            reqs.append({"id": i, "kind": "new", "key": k, "matrix": scaled(base, theta),
+                         "rhs": np.asfortranarray(rng.normal(0.0, 1.0, (base["n"], nrhs))), "target": None})
+            news.append(i)
+        arrivals.append(t)
+    return reqs, arrivals
