@@ -230,6 +230,31 @@ stiles_status stiles_batch_factorize(stiles_batch* batch, const double* const* v
                                      stiles_status* statuses, int64_t* infos);
 stiles_status stiles_batch_factor(const stiles_batch* batch, int32_t index, stiles_factor** out);
 stiles_status stiles_batch_logdet(stiles_batch* batch, double* out, void* stream);
+
+/* Batched solves A_i x_i = b_i (Section III.D's forward and backward sweeps, every matrix of the
+ * batch in one forward and one backward persistent launch; the tickets interleave the matrices'
+ * sweep task lists like stiles_batch_create does for the factorization).
+ *   rhs[i], x[i] : matrix i's right-hand sides and solutions, n_i x nrhs[i] column-major with
+ *                  leading dimension n_i, host or device (each pointer on its own; caller-owned);
+ *                  may be NULL where nrhs[i] == 0.
+ *   nrhs[i]      : 0 .. 16 right-hand sides of matrix i (0 = matrix i takes no part).
+ *   relres       : NULL, or double[count] receiving max over matrix i's columns of
+ *                  ||b - A x||_2 / ||b||_2 in FP64 (computed only when requested or refining).
+ *   iters        : NULL, or int32[count] receiving the refinement steps matrix i took.
+ * Mixed-precision batches refine every matrix in FP64 (x <- x + solve(b - A x)) until its own
+ * residual meets its plan's refine_tol or max_refine steps; the refinement sweeps still cover the
+ * whole batch but only unfinished matrices take the correction.  The batch must have been
+ * factorized.  The first call allocates the batch's solve workspace (room for 16 right-hand sides
+ * per matrix).  The call waits for its work.  Errors: STILES_ERR_INVALID (null pointers, nrhs out
+ * of range), STILES_ERR_TIMEOUT, STILES_ERR_NOT_CONVERGED (a matrix missed refine_tol; its x is
+ * still the best iterate), STILES_ERR_NOMEM, STILES_ERR_CUDA, STILES_ERR_UNSUPPORTED (more than
+ * 65,535 matrices). */
+stiles_status stiles_batch_solve(stiles_batch* batch, const double* const* rhs, double* const* x,
+                                 const int32_t* nrhs, void* stream, double* relres, int32_t* iters);
+/* Device time of the persistent factorization kernel of the last stiles_batch_factorize, in ms
+ * (CUDA events recorded around the kernel inside the batch's graph).  Errors: STILES_ERR_INVALID,
+ * STILES_ERR_CUDA (no factorization yet). */
+stiles_status stiles_batch_timing(const stiles_batch* batch, double* ms_kernel);
 void stiles_batch_destroy(stiles_batch* batch);
 
 /* Tile-size autotuner (Section IV.B and Appendix B: the tile size trades the extra flops of

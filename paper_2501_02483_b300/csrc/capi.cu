@@ -360,39 +360,52 @@ cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_
   return cudaGetLastError();
 }
 
+template <typename TF>
+dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backward, int nr, const TF* tiles,
+                            const TF* invdiag, double* Y, double* scratch, int* flags) {
+  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1);
+  dev::SolveCtx<TF> c;
+  c.tiles = tiles;
+  c.invdiag = invdiag;
+  c.Y = Y;
+  c.nr = nr;
+  c.pad0 = 0;
+  if (!backward) {
+    c.scratch = scratch;
+    c.tasks = p->dev->fwd.stasks;
+    c.pairs = p->dev->fwd.pairs;
+    c.parts = p->dev->fwd.parts;
+    c.flags = flags;
+    c.sflags = flags + p->nsb;
+    c.trace = f ? f->trace[1] : nullptr;
+  } else {
+    c.scratch = scratch + size_t(nf) * p->B * dev::SOLVE_MAXR;
+    c.tasks = p->dev->bwd.stasks;
+    c.pairs = p->dev->bwd.pairs;
+    c.parts = p->dev->bwd.parts;
+    c.flags = flags + p->nsb + nf;
+    c.sflags = flags + 2 * p->nsb + nf;
+    c.trace = f ? f->trace[2] : nullptr;
+  }
+  return c;
+}
+
 template <int B, typename TF>
 cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr, const TF* tiles,
                          const TF* invdiag) {
   dev::SolveArgs<TF> a;
-  a.tiles = tiles;
-  a.invdiag = invdiag;
-  a.Y = f->Y;
+  a.mats = nullptr;
+  a.tickets = nullptr;
   a.spin_limit = p->opts.spin_limit;
-  a.nr = nr;
-  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1);
-  // forward
-  a.scratch = f->sscratch;
-  a.tasks = p->dev->fwd.stasks;
+  a.single = solve_ctx<TF>(p, f, false, nr, tiles, invdiag, f->Y, f->sscratch, f->sflags);
   a.ntasks = p->dev->fwd.ntasks;
-  a.pairs = p->dev->fwd.pairs;
-  a.parts = p->dev->fwd.parts;
-  a.flags = f->sflags;
-  a.sflags = f->sflags + p->nsb;
   a.ctl = f->ctl + 1;
-  a.trace = f->trace[1];
   dev::solve_f64_kernel<B, false, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // backward
-  a.scratch = f->sscratch + size_t(nf) * B * dev::SOLVE_MAXR;
-  a.tasks = p->dev->bwd.stasks;
+  a.single = solve_ctx<TF>(p, f, true, nr, tiles, invdiag, f->Y, f->sscratch, f->sflags);
   a.ntasks = p->dev->bwd.ntasks;
-  a.pairs = p->dev->bwd.pairs;
-  a.parts = p->dev->bwd.parts;
-  a.flags = f->sflags + p->nsb + nf;
-  a.sflags = f->sflags + 2 * p->nsb + nf;
   a.ctl = f->ctl + 2;
-  a.trace = f->trace[2];
   dev::solve_f64_kernel<B, true, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
@@ -905,10 +918,122 @@ struct stiles_batch {
   void* dlog = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the persistent kernel (recorded inside the graph)
   cudaGraphExec_t gexec = nullptr;
+  // batched solves (allocated on first use)
+  bool solve_ready = false;
+  int solve_grid = 0;
+  int64_t vec_total = 0;          // sum of n * SOLVE_MAXR
+  std::vector<int64_t> vec_off;   // per matrix offset of its n x SOLVE_MAXR vectors
+  double* sY = nullptr;
+  double* sScr = nullptr;
+  int* sFlags = nullptr;
+  int64_t sflag_total = 0;
+  double* vb = nullptr;  // right-hand sides, solutions, residuals, corrections, A x
+  double* vx = nullptr;
+  double* vr = nullptr;
+  double* vd = nullptr;
+  double* vy = nullptr;
+  double* vnorms = nullptr;
+  stiles::dev::Ctl* sctl = nullptr;
+  void* dfwd = nullptr;
+  void* dbwd = nullptr;
+  void* ddesc = nullptr;
+  int2* tfwd = nullptr;
+  int2* tbwd = nullptr;
+  int nfwd = 0, nbwd = 0;
+  std::vector<int64_t> y_off, scr_off, flag_off;
 };
 
 namespace {
+
+// Per-matrix descriptor of the batched helper kernels around the solves.
+struct BSolveDesc {
+  const int64_t* perm;
+  int64_t n, nsb;
+  int B, nr;
+  double* Y;
+  double* b;
+  double* x;
+  double* r;
+  double* d;
+  double* y;
+  const int64_t* colptr;
+  const int32_t* rowidx;
+  const double* values;
+  double* norms;  // 2 per right-hand side: ||b - A x||^2, ||b||^2
+};
+
+// which = 0: b -> Y / Y -> x;  which = 1: r -> Y / Y -> d
+__global__ void bpermute_in_kernel(const BSolveDesc* desc, int which) {
+  const BSolveDesc c = desc[blockIdx.y];
+  const double* src = which ? c.r : c.b;
+  const int64_t total = c.nsb * c.B * c.nr;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t k = e / (int64_t(c.B) * c.nr);
+    const int64_t rem = e % (int64_t(c.B) * c.nr);
+    const int64_t r = rem / c.B, i = rem % c.B;
+    const int64_t g = k * c.B + i;
+    c.Y[e] = (g < c.n) ? src[c.perm[g] + r * c.n] : 0.0;
+  }
+}
+
+__global__ void bpermute_out_kernel(const BSolveDesc* desc, int which) {
+  const BSolveDesc c = desc[blockIdx.y];
+  double* dst = which ? c.d : c.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < c.n * c.nr; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / c.n, g = e % c.n;
+    dst[c.perm[g] + r * c.n] = c.Y[((g / c.B) * c.nr + r) * c.B + (g % c.B)];
+  }
+}
+
+__global__ void bspmv_kernel(const BSolveDesc* desc) {
+  const BSolveDesc c = desc[blockIdx.y];
+  for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < c.n * c.nr; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = w / c.n, j = w % c.n;
+    const double* xr = c.x + r * c.n;
+    double* yr = c.y + r * c.n;
+    const double xj = xr[j];
+    double s = 0.0;
+    for (int64_t e = c.colptr[j]; e < c.colptr[j + 1]; ++e) {
+      const int64_t i = c.rowidx[e];
+      const double v = c.values[e];
+      s = fma(v, xr[i], s);
+      if (i != j) atomicAdd(yr + i, v * xj);
+    }
+    atomicAdd(yr + j, s);
+  }
+}
+
+// r = b - y and the squared norms per right-hand side (grid.z = right-hand side)
+__global__ void bresidual_kernel(const BSolveDesc* desc) {
+  __shared__ double rr[256], bb[256];
+  const BSolveDesc c = desc[blockIdx.y];
+  const int r = blockIdx.z;
+  if (r >= c.nr) return;
+  double sr = 0.0, sb = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < c.n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double bv = c.b[i + r * c.n];
+    const double dv = bv - c.y[i + r * c.n];
+    c.r[i + r * c.n] = dv;
+    sr = fma(dv, dv, sr);
+    sb = fma(bv, bv, sb);
+  }
+  rr[threadIdx.x] = sr;
+  bb[threadIdx.x] = sb;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) {
+      rr[threadIdx.x] += rr[threadIdx.x + w];
+      bb[threadIdx.x] += bb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(c.norms + 2 * r, rr[0]);
+    atomicAdd(c.norms + 2 * r + 1, bb[0]);
+  }
+}
 
 struct BatchLogCtx {
   const double* tiles;      // FP64 factor tiles (FP64 path)
@@ -959,9 +1084,26 @@ void free_batch(stiles_batch* b) {
   cudaFree(b->dtickets);
   cudaFree(b->logdet_out);
   cudaFree(b->dlog);
+  cudaFree(b->sY);
+  cudaFree(b->sScr);
+  cudaFree(b->sFlags);
+  cudaFree(b->vb);
+  cudaFree(b->vx);
+  cudaFree(b->vr);
+  cudaFree(b->vd);
+  cudaFree(b->vy);
+  cudaFree(b->vnorms);
+  cudaFree(b->sctl);
+  cudaFree(b->dfwd);
+  cudaFree(b->dbwd);
+  cudaFree(b->ddesc);
+  cudaFree(b->tfwd);
+  cudaFree(b->tbwd);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_k0) cudaEventDestroy(b->ev_k0);
+  if (b->ev_k1) cudaEventDestroy(b->ev_k1);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -988,6 +1130,7 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(b->infos, 0xFF, b->plans.size() * sizeof(unsigned long long), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->ctl, 1);
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecordWithFlags(b->ev_k0, st, cudaEventRecordExternal));  // a node of the captured graph
   if (b->lp) {
     dev::LPArgs a{};
     a.mats = static_cast<const dev::LPMatCtx*>(b->dmats);
@@ -1011,7 +1154,227 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
     }
   }
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecordWithFlags(b->ev_k1, st, cudaEventRecordExternal));
   return STILES_OK;
+}
+
+// Merged ticket order of per-matrix task lists: matrix i's task j sits at
+// (j + 0.5) / n_i (ties by matrix), so every matrix keeps its own order.
+std::vector<int2> merge_tickets(const std::vector<int64_t>& lens) {
+  std::vector<std::pair<double, int2>> keyed;
+  for (size_t i = 0; i < lens.size(); ++i)
+    for (int64_t j = 0; j < lens[i]; ++j)
+      keyed.push_back({(double(j) + 0.5) / double(lens[i]), make_int2(int(i), int(j))});
+  std::stable_sort(keyed.begin(), keyed.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+    return x.first < y.first;
+  });
+  std::vector<int2> tick(keyed.size());
+  for (size_t q = 0; q < keyed.size(); ++q) tick[q] = keyed[q].second;
+  return tick;
+}
+
+// Device workspace of batched solves, allocated on the first call: per
+// matrix room for SOLVE_MAXR right-hand sides in every vector.
+stiles_status ensure_batch_solve(stiles_batch* b) {
+  if (b->solve_ready) return STILES_OK;
+  const int count = int(b->plans.size());
+  if (count > 65535) return fail(STILES_ERR_UNSUPPORTED, "batched solves take at most 65535 matrices");
+  const int64_t R = dev::SOLVE_MAXR;
+  int64_t ytot = 0, stot = 0, ftot = 0, vtot = 0;
+  std::vector<int64_t> lf(count), lb(count);
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = b->plans[i];
+    const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
+    b->y_off.push_back(ytot);
+    b->scr_off.push_back(stot);
+    b->flag_off.push_back(ftot);
+    b->vec_off.push_back(vtot);
+    ytot += p->nsb * p->B * R;
+    stot += (nf + nb) * p->B * R;
+    ftot += 2 * p->nsb + nf + nb;
+    vtot += p->n * R;
+    lf[i] = int64_t(p->fwd.tasks.size());
+    lb[i] = int64_t(p->bwd.tasks.size());
+  }
+  b->vec_total = vtot;
+  b->sflag_total = ftot;
+  std::vector<int2> tf = merge_tickets(lf), tb = merge_tickets(lb);
+  if (tf.size() >= (size_t(1) << 31) || tb.size() >= (size_t(1) << 31))
+    return fail(STILES_ERR_UNSUPPORTED, "too many solve tasks in one batch");
+  b->nfwd = int(tf.size());
+  b->nbwd = int(tb.size());
+  const size_t ctx_bytes = b->lp ? sizeof(dev::SolveCtx<float>) : sizeof(dev::SolveCtx<double>);
+  cudaError_t e = cudaMalloc(&b->sY, size_t(ytot) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sScr, size_t(stot) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sFlags, size_t(ftot) * sizeof(int));
+  for (double** v : {&b->vb, &b->vx, &b->vr, &b->vd, &b->vy})
+    if (e == cudaSuccess) e = cudaMalloc(v, size_t(vtot) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->vnorms, size_t(count) * 2 * R * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sctl, 2 * sizeof(dev::Ctl));
+  if (e == cudaSuccess) e = cudaMalloc(&b->dfwd, size_t(count) * ctx_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dbwd, size_t(count) * ctx_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ddesc, size_t(count) * sizeof(BSolveDesc));
+  if (e == cudaSuccess) e = upload(&b->tfwd, tf);
+  if (e == cudaSuccess) e = upload(&b->tbwd, tb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                std::string("batched solve allocation: ") + cudaGetErrorString(e));
+  }
+  int sms = 0, per_sm = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  cudaError_t oe;
+  if (b->lp) oe = solve_occupancy<64, float>(&per_sm);
+  else switch (b->B) {
+    case 16: oe = solve_occupancy<16, double>(&per_sm); break;
+    case 32: oe = solve_occupancy<32, double>(&per_sm); break;
+    default: oe = solve_occupancy<64, double>(&per_sm); break;
+  }
+  if (oe != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(oe));
+  if (b->plans[0]->opts.ctas_per_sm > 0) per_sm = std::min(per_sm, int(b->plans[0]->opts.ctas_per_sm));
+  b->solve_grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(std::max(per_sm, 1)) * sms,
+                                                            std::max(b->nfwd, b->nbwd))));
+  b->solve_ready = true;
+  return STILES_OK;
+}
+
+// Upload the per-call contexts (they carry each matrix's right-hand-side count).
+template <typename TF>
+stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cudaStream_t st) {
+  const int count = int(b->plans.size());
+  std::vector<dev::SolveCtx<TF>> cf(count), cb(count);
+  std::vector<BSolveDesc> desc(count);
+  for (int i = 0; i < count; ++i) {
+    const stiles_plan* p = b->plans[i];
+    const stiles_factor* v = b->views[i];
+    const TF* tiles;
+    const TF* inv;
+    if constexpr (sizeof(TF) == 4) {
+      tiles = v->tiles32;
+      inv = v->invdiag32;
+    } else {
+      tiles = v->tiles;
+      inv = v->invdiag;
+    }
+    double* Y = b->sY + b->y_off[i];
+    cf[i] = solve_ctx<TF>(p, nullptr, false, nr[i], tiles, inv, Y, b->sScr + b->scr_off[i], b->sFlags + b->flag_off[i]);
+    cb[i] = solve_ctx<TF>(p, nullptr, true, nr[i], tiles, inv, Y, b->sScr + b->scr_off[i], b->sFlags + b->flag_off[i]);
+    BSolveDesc& d = desc[i];
+    d.perm = p->dev->perm;
+    d.n = p->n;
+    d.nsb = p->nsb;
+    d.B = p->B;
+    d.nr = nr[i];
+    d.Y = Y;
+    d.b = b->vb + b->vec_off[i];
+    d.x = b->vx + b->vec_off[i];
+    d.r = b->vr + b->vec_off[i];
+    d.d = b->vd + b->vec_off[i];
+    d.y = b->vy + b->vec_off[i];
+    d.colptr = p->dev->colptr;
+    d.rowidx = p->dev->rowidx;
+    d.values = v->values;
+    d.norms = b->vnorms + size_t(i) * 2 * dev::SOLVE_MAXR;
+  }
+  // synchronous copies: the host vectors go out of scope on return
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaMemcpy(b->dfwd, cf.data(), count * sizeof(cf[0]), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->dbwd, cb.data(), count * sizeof(cb[0]), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->ddesc, desc.data(), count * sizeof(desc[0]), cudaMemcpyHostToDevice));
+  return STILES_OK;
+}
+
+template <int B, typename TF>
+cudaError_t launch_batch_sweeps(stiles_batch* b, cudaStream_t st) {
+  dev::SolveArgs<TF> a{};
+  a.spin_limit = b->spin_limit;
+  a.mats = static_cast<const dev::SolveCtx<TF>*>(b->dfwd);
+  a.tickets = b->tfwd;
+  a.ntasks = b->nfwd;
+  a.ctl = b->sctl;
+  dev::solve_f64_kernel<B, false, TF><<<b->solve_grid, 128, dev::SolveCfg<B>::SMEM, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  a.mats = static_cast<const dev::SolveCtx<TF>*>(b->dbwd);
+  a.tickets = b->tbwd;
+  a.ntasks = b->nbwd;
+  a.ctl = b->sctl + 1;
+  dev::solve_f64_kernel<B, true, TF><<<b->solve_grid, 128, dev::SolveCfg<B>::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Grid of the per-matrix helper kernels: x covers the largest matrix, y the matrices.
+dim3 batch_grid(const stiles_batch* b, int64_t max_work) {
+  const int64_t count = int64_t(b->plans.size());
+  const int64_t cap = std::max<int64_t>(1, 148 * 32 / count);
+  return dim3(unsigned(std::max<int64_t>(1, std::min<int64_t>((max_work + 255) / 256, cap))), unsigned(count));
+}
+
+// One solve of every matrix: which = 0 solves b into x, which = 1 solves r into d.
+stiles_status batch_solve_pass(stiles_batch* b, cudaStream_t st, int which, int64_t max_rows) {
+  const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
+  const dim3 g = batch_grid(b, max_rows * dev::SOLVE_MAXR);
+  bpermute_in_kernel<<<g, 256, 0, st>>>(desc, which);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(b->sFlags, 0, size_t(b->sflag_total) * sizeof(int), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->sctl, 2);
+  CUDA_TRY(cudaGetLastError());
+  cudaError_t e;
+  if (b->lp) e = launch_batch_sweeps<64, float>(b, st);
+  else switch (b->B) {
+    case 16: e = launch_batch_sweeps<16, double>(b, st); break;
+    case 32: e = launch_batch_sweeps<32, double>(b, st); break;
+    default: e = launch_batch_sweeps<64, double>(b, st); break;
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("batched solve launch: ") + cudaGetErrorString(e));
+  bpermute_out_kernel<<<g, 256, 0, st>>>(desc, which);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(5);
+  dev::Ctl c[2];
+  CUDA_TRY(cudaMemcpyAsync(c, b->sctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < 2; ++k)
+    if (c[k].status != 0) {
+      char buf[96];
+      std::snprintf(buf, sizeof buf, "device wait timed out in the batched %s sweep (ticket %lld)",
+                    k ? "backward" : "forward", c[k].where);
+      return fail(STILES_ERR_TIMEOUT, buf);
+    }
+  return STILES_OK;
+}
+
+// r = b - A x for every matrix and ||r|| / ||b|| per matrix (largest over its columns).
+stiles_status batch_residual(stiles_batch* b, cudaStream_t st, int64_t max_rows, const std::vector<int>& nr,
+                             std::vector<double>* rel) {
+  const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
+  const int count = int(b->plans.size());
+  CUDA_TRY(cudaMemsetAsync(b->vy, 0, size_t(b->vec_total) * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(b->vnorms, 0, size_t(count) * 2 * dev::SOLVE_MAXR * sizeof(double), st));
+  bspmv_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(desc);
+  CUDA_TRY(cudaGetLastError());
+  dim3 g = batch_grid(b, max_rows);
+  g.z = dev::SOLVE_MAXR;
+  bresidual_kernel<<<g, 256, 0, st>>>(desc);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(2);
+  std::vector<double> h(size_t(count) * 2 * dev::SOLVE_MAXR);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), b->vnorms, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  rel->assign(count, 0.0);
+  for (int i = 0; i < count; ++i)
+    for (int r = 0; r < nr[i]; ++r) {
+      const double* q = h.data() + size_t(i) * 2 * dev::SOLVE_MAXR + 2 * r;
+      const double w = q[1] > 0 ? std::sqrt(q[0] / q[1]) : std::sqrt(q[0]);
+      if (!(w <= (*rel)[i])) (*rel)[i] = w;  // NaN propagates
+    }
+  return STILES_OK;
+}
+
+__global__ void baxpy_active_kernel(const BSolveDesc* desc, const int* active) {
+  if (!active[blockIdx.y]) return;
+  const BSolveDesc c = desc[blockIdx.y];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < c.n * c.nr; e += int64_t(gridDim.x) * blockDim.x)
+    c.x[e] += c.d[e];
 }
 
 }  // namespace
@@ -1127,17 +1490,9 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   else e = upload(reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
   if (e == cudaSuccess) e = upload(reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
-  // merged tickets: matrix i's task j at key (j + 0.5) / n_i, ties by matrix
-  std::vector<std::pair<double, int2>> keyed;
-  for (int i = 0; i < count; ++i) {
-    const int64_t nt = int64_t(plans[i]->graph.tasks.size());
-    for (int64_t j = 0; j < nt; ++j) keyed.push_back({(double(j) + 0.5) / double(nt), make_int2(i, int(j))});
-  }
-  std::stable_sort(keyed.begin(), keyed.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
-    return x.first < y.first;
-  });
-  std::vector<int2> tick(keyed.size());
-  for (size_t q = 0; q < keyed.size(); ++q) tick[q] = keyed[q].second;
+  std::vector<int64_t> lens(count);
+  for (int i = 0; i < count; ++i) lens[i] = int64_t(plans[i]->graph.tasks.size());
+  std::vector<int2> tick = merge_tickets(lens);
   if (tick.size() >= size_t(1) << 31) return bail(fail(STILES_ERR_UNSUPPORTED, "too many tasks in one batch"));
   b->ntickets = int(tick.size());
   e = upload(&b->dtickets, tick);
@@ -1162,6 +1517,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreate(&b->ev_k0));
+  CUDA_TRY(cudaEventCreate(&b->ev_k1));
   {
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1231,6 +1588,92 @@ stiles_status stiles_batch_logdet(stiles_batch* b, double* out, void* stream) {
   count_launch();
   CUDA_TRY(cudaMemcpyAsync(out, b->logdet_out, count * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, double* const* x, const int32_t* nrhs,
+                                 void* stream, double* relres, int32_t* iters) {
+  if (!b || !rhs || !x || !nrhs) return fail(STILES_ERR_INVALID, "null argument");
+  const int count = int(b->plans.size());
+  std::vector<int> nr(count);
+  int64_t max_rows = 0;
+  for (int i = 0; i < count; ++i) {
+    if (nrhs[i] < 0 || nrhs[i] > dev::SOLVE_MAXR) return fail(STILES_ERR_INVALID, "nrhs must be in [0, 16]");
+    if (nrhs[i] > 0 && (!rhs[i] || !x[i])) return fail(STILES_ERR_INVALID, "null right-hand side or solution");
+    nr[i] = nrhs[i];
+    max_rows = std::max<int64_t>(max_rows, b->plans[i]->nsb * b->plans[i]->B);
+  }
+  stiles_status s = ensure_batch_solve(b);
+  if (s != STILES_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->lp) s = upload_solve_ctx<float>(b, nr, st);
+  else s = upload_solve_ctx<double>(b, nr, st);
+  if (s != STILES_OK) return s;
+  for (int i = 0; i < count; ++i)
+    if (nr[i])
+      CUDA_TRY(cudaMemcpyAsync(b->vb + b->vec_off[i], rhs[i], size_t(b->plans[i]->n) * nr[i] * sizeof(double),
+                               cudaMemcpyDefault, st));
+  s = batch_solve_pass(b, st, 0, max_rows);
+  if (s != STILES_OK) return s;
+  std::vector<double> rel;
+  std::vector<int> it(count, 0);
+  bool converged = true;
+  if (b->lp) {
+    // iterative refinement in FP64 per matrix until its residual meets refine_tol
+    std::vector<int> active(count);
+    int* dactive = nullptr;
+    CUDA_TRY(cudaMalloc(&dactive, size_t(count) * sizeof(int)));
+    for (;;) {
+      s = batch_residual(b, st, max_rows, nr, &rel);
+      if (s != STILES_OK) break;
+      int any = 0;
+      for (int i = 0; i < count; ++i) {
+        const stiles_plan* p = b->plans[i];
+        active[i] = (rel[i] > p->opts.refine_tol && it[i] < p->opts.max_refine) ? 1 : 0;
+        any |= active[i];
+      }
+      if (!any) break;
+      if (cudaMemcpy(dactive, active.data(), size_t(count) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+        s = fail(STILES_ERR_CUDA, "batched refinement upload");
+        break;
+      }
+      s = batch_solve_pass(b, st, 1, max_rows);
+      if (s != STILES_OK) break;
+      baxpy_active_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(
+          static_cast<const BSolveDesc*>(b->ddesc), dactive);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) {
+        s = fail(STILES_ERR_CUDA, "batched refinement update");
+        break;
+      }
+      for (int i = 0; i < count; ++i) it[i] += active[i];
+    }
+    cudaFree(dactive);
+    if (s != STILES_OK) return s;
+    for (int i = 0; i < count; ++i)
+      if (nr[i] && !(rel[i] <= b->plans[i]->opts.refine_tol)) converged = false;
+  } else if (relres) {
+    s = batch_residual(b, st, max_rows, nr, &rel);
+    if (s != STILES_OK) return s;
+  }
+  for (int i = 0; i < count; ++i)
+    if (nr[i])
+      CUDA_TRY(cudaMemcpyAsync(x[i], b->vx + b->vec_off[i], size_t(b->plans[i]->n) * nr[i] * sizeof(double),
+                               cudaMemcpyDefault, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) {
+    if (relres) relres[i] = rel.empty() ? 0.0 : rel[i];
+    if (iters) iters[i] = it[i];
+  }
+  if (!converged) return fail(STILES_ERR_NOT_CONVERGED, "iterative refinement did not reach refine_tol in the batch");
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_timing(const stiles_batch* b, double* ms_kernel) {
+  if (!b || !ms_kernel) return fail(STILES_ERR_INVALID, "null argument");
+  float k = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&k, b->ev_k0, b->ev_k1));
+  *ms_kernel = k;
   return STILES_OK;
 }
 

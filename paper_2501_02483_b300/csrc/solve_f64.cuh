@@ -33,22 +33,31 @@ struct SolveCfg {
   static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
 
+// One matrix of a solve launch (a batched launch carries one per matrix).
 template <typename TF>
-struct SolveArgs {
+struct SolveCtx {
   const TF* tiles;        // factor sub-tiles (FP64, or FP32 for a mixed-precision factor)
   const TF* invdiag;      // nsb * B
   double* Y;              // nsb blocks of B x nr
   double* scratch;        // nscratch blocks
   const SolveTask* tasks;
-  int ntasks;
   const int32_t* pairs;   // (L sub-tile, block)
   const int32_t* parts;
   int* flags;             // per block
   int* sflags;            // per scratch block
+  long long* trace;       // optional, 4 per task: start, dependencies ready, done, SM id
+  int nr;                 // right-hand sides (<= SOLVE_MAXR)
+  int pad0;
+};
+
+template <typename TF>
+struct SolveArgs {
+  SolveCtx<TF> single;          // one-matrix launch (mats == NULL)
+  const SolveCtx<TF>* mats;     // batched launch: one context per matrix
+  const int2* tickets;          // batched launch: (matrix, task) per ticket
+  int ntasks;
   Ctl* ctl;
   long long spin_limit;
-  int nr;                 // right-hand sides in this launch (<= SOLVE_MAXR)
-  long long* trace;       // optional, 4 per ticket: start, dependencies ready, done, SM id
 };
 
 template <int B, bool BACKWARD, typename TF>
@@ -66,8 +75,6 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
   const int tid = threadIdx.x;
   const int li = tid % W;  // lane inside the column group
   const int grp = tid / W;
-  const int nr = a.nr;
-  const int blk = B * nr;  // doubles per block
   const long long limit = a.spin_limit;
 
   if (tid == 0) {
@@ -90,8 +97,17 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     __syncthreads();
     const int t = sTicket;
     if (t < 0) break;
-    const SolveTask tk = a.tasks[t];
-    long long* const trace = a.trace ? a.trace + 4 * size_t(t) : nullptr;
+    int mi = 0, ti = t;
+    if (a.tickets) {
+      const int2 v = a.tickets[t];
+      mi = v.x;
+      ti = v.y;
+    }
+    const SolveCtx<TF> mc = a.mats ? a.mats[mi] : a.single;
+    const SolveTask tk = mc.tasks[ti];
+    const int nr = mc.nr;
+    const int blk = B * nr;  // doubles per block
+    long long* const trace = mc.trace ? mc.trace + 4 * size_t(ti) : nullptr;
     unsigned long long t_ready = 0;
     if (trace && tid == 0) {
       t_ready = globaltimer();
@@ -101,7 +117,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
 
     double acc[RP][U];
     if (tk.type == SOLVE_FINAL) {
-      const double* src = a.Y + size_t(tk.out) * blk;
+      const double* src = mc.Y + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     // the diagonal sub-tile does not depend on this sweep: fetch it first
     if (tk.type == SOLVE_FINAL && tid == 0) {
       mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(TF)));
-      tma_load_1d(sL, a.tiles + size_t(tk.diag) * TILE, TILE * sizeof(TF), &bars[NSTAGE]);
+      tma_load_1d(sL, mc.tiles + size_t(tk.diag) * TILE, TILE * sizeof(TF), &bars[NSTAGE]);
     }
     const int npairs = tk.pe - tk.pb;
     const int nitems = npairs + (tk.qe - tk.qb);
@@ -131,15 +147,15 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
           const TF* gL = nullptr;
           const double* gY;
           if (issued < npairs) {
-            const int ls = a.pairs[2 * (tk.pb + issued)];
-            const int bk = a.pairs[2 * (tk.pb + issued) + 1];
-            f = a.flags + bk;
-            gL = a.tiles + size_t(ls) * TILE;
-            gY = a.Y + size_t(bk) * blk;
+            const int ls = mc.pairs[2 * (tk.pb + issued)];
+            const int bk = mc.pairs[2 * (tk.pb + issued) + 1];
+            f = mc.flags + bk;
+            gL = mc.tiles + size_t(ls) * TILE;
+            gY = mc.Y + size_t(bk) * blk;
           } else {
-            const int s = a.parts[tk.qb + issued - npairs];
-            f = a.sflags + s;
-            gY = a.scratch + size_t(s) * blk;
+            const int s = mc.parts[tk.qb + issued - npairs];
+            f = mc.sflags + s;
+            gY = mc.scratch + size_t(s) * blk;
           }
           if (issued == it) {
             if (!wait_flag(f, 1, limit, a.ctl)) {
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     }
 
     if (tk.type != SOLVE_FINAL) {
-      double* dst = a.scratch + size_t(tk.out) * blk;
+      double* dst = mc.scratch + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;
@@ -241,13 +257,13 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
 #pragma unroll
           for (int s = 0; s < RP; ++s) dst[r * B + li + W * s] = acc[s][u];
       }
-      publish(a.sflags + tk.out);
+      publish(mc.sflags + tk.out);
       if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
       continue;
     }
 
     // ---- triangular solve with the diagonal sub-tile (prefetched above) ----
-    if (tid < B) sInv[tid] = double(__ldcg(a.invdiag + size_t(tk.out) * B + tid));
+    if (tid < B) sInv[tid] = double(__ldcg(mc.invdiag + size_t(tk.out) * B + tid));
     {
       long long spins = 0;
       while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
       }
     }
     {
-      double* dst = a.Y + size_t(tk.out) * blk;
+      double* dst = mc.Y + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;
@@ -313,7 +329,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
           for (int s = 0; s < RP; ++s) dst[r * B + li + W * s] = acc[s][u];
       }
     }
-    publish(a.flags + tk.out);
+    publish(mc.flags + tk.out);
     if (trace && tid == 0) { trace[1] = (long long)t_ready; trace[2] = (long long)globaltimer(); }
   }
 }

@@ -8,8 +8,9 @@ re-solve against a factor that is still resident.  The loop:
 * every time the GPU side is free it takes *all* analysed requests that fit
   the HBM budget and factorizes them in one batched persistent launch
   (stiles_batch_*), then computes their log-determinants in one launch and
-  their solves (FP64 refinement for BF16/FP16 factors); requests that arrive
-  meanwhile join the next launch, so their work overlaps the running one;
+  their solves in one batched forward/backward sweep (FP64 refinement for
+  BF16/FP16 factors); requests that arrive meanwhile join the next launch,
+  so their work overlaps the running one;
 * keeps finished factors resident in an LRU cache bounded by the HBM budget;
   re-solve requests for a resident factor skip the factorization, a re-solve
   whose factor was evicted is refactorized (and counted as a miss).
@@ -124,13 +125,23 @@ class Server:
         batch = st.Batch(plans)
         statuses, _ = batch.factorize([r.matrix["values"] for r in reqs], stream=stream, raise_on_error=False)
         lds = batch.logdets(stream=stream)
+        # all first solves of the launch in one batched forward + backward sweep
+        # (requests with more than 16 right-hand sides are solved on their own)
+        rhs = [r.rhs if statuses[i] == 0 and r.rhs.shape[1] <= 16 else None for i, r in enumerate(reqs)]
+        xs, rel, _, bst = batch.solve(rhs, stream=stream, raise_on_error=False)
         members = {}
         for i, r in enumerate(reqs):
             r.batch_size = len(reqs)
             r.status = int(statuses[i])
             if r.status == 0:
                 r.logdet = float(lds[i])
-                self._solve(r, batch.factor(i), stream)
+                if rhs[i] is None:
+                    self._solve(r, batch.factor(i), stream)
+                elif bst in (0, 6):  # OK, or NOT_CONVERGED (judged per request below)
+                    r.x, r.relres = xs[i], float(rel[i])
+                    self.stats["solved_columns"] += r.rhs.shape[1] if r.relres <= self.opts["refine_tol"] else 0
+                else:
+                    r.status, r.relres = int(bst), float("inf")
             r.t_done = time.perf_counter()
             members[r.id] = i
         self.resident[reqs[0].id] = _Resident(batch, members, nbytes)

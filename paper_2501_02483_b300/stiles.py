@@ -83,6 +83,8 @@ def lib():
         L.stiles_batch_factorize.argtypes = [P, P, P, P, P]
         L.stiles_batch_factor.argtypes = [P, c_int32, POINTER(c_void_p)]
         L.stiles_batch_logdet.argtypes = [P, P, P]
+        L.stiles_batch_solve.argtypes = [P, P, P, P, P, P, P]
+        L.stiles_batch_timing.argtypes = [P, POINTER(c_double)]
         L.stiles_batch_destroy.argtypes = [P]
         L.stiles_batch_destroy.restype = None
         L.stiles_autotune.argtypes = [c_int64, P, P, c_int64, POINTER(Opts), P, c_int32, P, P, POINTER(c_int32), P]
@@ -341,10 +343,53 @@ class Batch:
         _check(lib().stiles_batch_factor(self._h, i, ctypes.byref(h)))
         return _View(self.plans[i], h, self)
 
+    def timing(self):
+        """ms of the persistent factorization kernel of the last factorize."""
+        ms = c_double(0.0)
+        _check(lib().stiles_batch_timing(self._h, ctypes.byref(ms)))
+        return ms.value
+
     def logdets(self, stream=None):
         out = np.zeros(len(self.plans), dtype=np.float64)
         _check(lib().stiles_batch_logdet(self._h, _ptr(out), _stream(stream)))
         return out
+
+    def solve(self, rhs, stream=None, relres=True, raise_on_error=True):
+        """rhs: list (one per matrix) of n_i x k_i arrays (k_i <= 16; host numpy or device
+        torch, column-major/Fortran order or 1-D), or None to skip a matrix.  Returns
+        (xs, relres, iters, status); xs[i] matches rhs[i]'s kind (None where skipped)."""
+        cnt = len(self.plans)
+        if len(rhs) != cnt:
+            raise ValueError("one right-hand side per matrix")
+        bs, xs, ks = [], [], np.zeros(cnt, dtype=np.int32)
+        for i, b in enumerate(rhs):
+            if b is None:
+                bs.append(None)
+                xs.append(None)
+                continue
+            n = self.plans[i].n
+            if isinstance(b, np.ndarray):
+                bn = np.asfortranarray(b.reshape(n, -1), dtype=np.float64)
+                xs.append(np.empty_like(bn, order="F"))
+            else:  # torch tensor (device or host)
+                bn = b.reshape(n, -1).t().contiguous().t()
+                xs.append(bn.clone())
+            ks[i] = bn.shape[1]
+            bs.append(bn)
+        barr = (c_void_p * cnt)(*[None if b is None else _ptr(b) for b in bs])
+        xarr = (c_void_p * cnt)(*[None if x is None else _ptr(x) for x in xs])
+        rel = np.zeros(cnt, dtype=np.float64)
+        its = np.zeros(cnt, dtype=np.int32)
+        st = lib().stiles_batch_solve(self._h, barr, xarr, _ptr(ks), _stream(stream),
+                                      _ptr(rel) if relres else None, _ptr(its))
+        if raise_on_error:
+            _check(st)
+        out = []
+        for i, x in enumerate(xs):
+            if x is not None and np.ndim(rhs[i]) == 1:
+                x = x.reshape(-1)
+            out.append(x)
+        return out, rel, its, int(st)
 
     def close(self):
         if self._h:

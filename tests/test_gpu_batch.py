@@ -108,3 +108,76 @@ def test_autotune_picks_a_candidate():
     assert best in (16, 32, 64, 512)
     assert ms[[16, 32, 64, 512].index(best)] == min(t for t in ms if t > 0)
     assert ms[3] == -1.0 or ms[3] >= min(t for t in ms if t > 0)
+
+
+@pytest.mark.parametrize("prec,T,order", [(st.PREC_F64, 16, st.ORDER_NONE), (st.PREC_F64, 32, st.ORDER_ND),
+                                          (st.PREC_BF16, 64, st.ORDER_NONE), (st.PREC_F16, 64, st.ORDER_ND)])
+def test_batch_solve_matches_single_and_oracle(prec, T, order):
+    """One forward + one backward launch over the whole batch: every matrix's x
+    meets the residual bound against its own A; FP64 solutions are bitwise the
+    single-matrix solve's (same task lists, same arithmetic); mixed-precision
+    matrices refine independently; mixed right-hand-side counts, a skipped
+    matrix, host and device right-hand sides."""
+    mats = _mats(11, 101 + T)
+    plans = [st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec) for m in mats]
+    batch = st.Batch(plans)
+    vals = [torch.from_numpy(m["values"]).cuda() for m in mats]
+    statuses, _ = batch.factorize(vals)
+    assert np.all(statuses == 0)
+    rng = np.random.default_rng(T)
+    rhs = []
+    for i, m in enumerate(mats):
+        k = [1, 3, 16, 7, 0][i % 5]
+        if k == 0:
+            rhs.append(None)
+            continue
+        b = np.asfortranarray(rng.standard_normal((m["n"], k)))
+        rhs.append(torch.from_numpy(b).cuda() if i % 2 else b)
+    xs, rel, its, status = batch.solve(rhs)
+    assert status == 0
+    tol = 1e-12 if prec == st.PREC_F64 else 1e-10
+    for i, m in enumerate(mats):
+        if rhs[i] is None:
+            assert xs[i] is None and rel[i] == 0.0
+            continue
+        b = rhs[i] if isinstance(rhs[i], np.ndarray) else rhs[i].cpu().numpy()
+        x = xs[i] if isinstance(xs[i], np.ndarray) else xs[i].cpu().numpy()
+        assert isinstance(xs[i], np.ndarray) == isinstance(rhs[i], np.ndarray)
+        A = inputs.dense_from_csc(m)
+        rr = np.linalg.norm(b - A @ x, axis=0) / np.linalg.norm(b, axis=0)
+        assert rr.max() <= tol * 10, (i, rr.max())
+        assert rel[i] <= tol
+        xs1 = batch.factor(i).solve(b)
+        if prec == st.PREC_F64:
+            assert its[i] == 0
+            assert np.array_equal(x, xs1)
+        else:
+            assert its[i] >= 1
+            assert np.max(np.abs(x - xs1)) <= 1e-8 * np.max(np.abs(x))
+    batch.close()
+
+
+def test_batch_solve_oracle_solution_small():
+    """The batched solve against the oracle's own triangular solves on C0-sized
+    matrices (independent of the single-matrix path)."""
+    mats = _mats(4, 55)
+    plans = [st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_RCM) for m in mats]
+    batch = st.Batch(plans)
+    batch.factorize([m["values"] for m in mats])
+    xs, rel, _, _ = batch.solve([m["rhs"] for m in mats])
+    for i, m in enumerate(mats):
+        p = oan.analyze(m, 16, oan.ORDER_RCM)
+        Lo = och.factorize(m, p["perm"], 16, p["tcolptr"], p["trowidx"])
+        xo = och.solve(Lo, p["perm"], 16, p["tcolptr"], p["trowidx"], m["rhs"])
+        assert np.max(np.abs(xs[i] - xo)) <= 1e-10 * np.max(np.abs(xo))
+    batch.close()
+
+
+def test_batch_solve_rejects_bad_counts():
+    mats = _mats(2, 9)
+    plans = [st.Plan.from_matrix(m, tile=16) for m in mats]
+    batch = st.Batch(plans)
+    batch.factorize([m["values"] for m in mats])
+    with pytest.raises(st.StilesError):
+        batch.solve([np.zeros((mats[0]["n"], 17)), None])
+    batch.close()
