@@ -116,8 +116,9 @@ __global__ void logdet_pass2(const double* __restrict__ partial, int np, double*
   }
 }
 
-// Y[block k][r][i] = b[perm[k*B+i] + (r0 + r) * ld]   (zero past n)
-__global__ void permute_in_kernel(double* __restrict__ Y, const double* __restrict__ b, const int64_t* __restrict__ perm,
+// Y[block k][r][i] = b[perm[k*B+i] + (r0 + r) * ld]   (zero past n; Y in the sweep's type)
+template <typename TY>
+__global__ void permute_in_kernel(TY* __restrict__ Y, const double* __restrict__ b, const int64_t* __restrict__ perm,
                                   int64_t n, int64_t ld, int r0, int nr, int B, int64_t nsb) {
   const int64_t total = nsb * B * nr;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -126,11 +127,12 @@ __global__ void permute_in_kernel(double* __restrict__ Y, const double* __restri
     const int64_t rem = e % (int64_t(B) * nr);
     const int r = int(rem / B), i = int(rem % B);
     const int64_t g = k * B + i;
-    Y[e] = (g < n) ? b[perm[g] + (r0 + r) * ld] : 0.0;
+    Y[e] = (g < n) ? TY(b[perm[g] + (r0 + r) * ld]) : TY(0);
   }
 }
 
-__global__ void permute_out_kernel(double* __restrict__ x, const double* __restrict__ Y, const int64_t* __restrict__ perm,
+template <typename TY>
+__global__ void permute_out_kernel(double* __restrict__ x, const TY* __restrict__ Y, const int64_t* __restrict__ perm,
                                    int64_t n, int64_t ld, int r0, int nr, int B) {
   const int64_t total = n * nr;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -138,7 +140,7 @@ __global__ void permute_out_kernel(double* __restrict__ x, const double* __restr
     const int r = int(e / n);
     const int64_t g = e % n;
     const int64_t k = g / B, i = g % B;
-    x[perm[g] + (r0 + r) * ld] = Y[(k * nr + r) * B + i];
+    x[perm[g] + (r0 + r) * ld] = double(Y[(k * nr + r) * B + i]);
   }
 }
 

@@ -16,7 +16,7 @@
 #include "factor_f64.cuh"
 #include "factor_lp.cuh"
 #include "plan.h"
-#include "solve_f64.cuh"
+#include "solve.cuh"
 
 namespace {
 
@@ -163,14 +163,14 @@ cudaError_t factor_occupancy(int* blocks) {
 
 template <int B, typename TF>
 cudaError_t solve_occupancy(int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, false, TF>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::SolveCfg<B>::SMEM));
+  cudaError_t e = cudaFuncSetAttribute(dev::solve_kernel<B, false, TF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::SolveCfg<B, TF>::SMEM));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(dev::solve_f64_kernel<B, true, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(dev::SolveCfg<B>::SMEM));
+  e = cudaFuncSetAttribute(dev::solve_kernel<B, true, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(dev::SolveCfg<B, TF>::SMEM));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::solve_f64_kernel<B, false, TF>, 128,
-                                                       dev::SolveCfg<B>::SMEM);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::solve_kernel<B, false, TF>, 128,
+                                                       dev::SolveCfg<B, TF>::SMEM);
 }
 
 stiles_status ensure_dev_plan(const stiles_plan* cp) {
@@ -362,7 +362,7 @@ cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_
 
 template <typename TF>
 dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backward, int nr, const TF* tiles,
-                            const TF* invdiag, double* Y, double* scratch, int* flags) {
+                            const TF* invdiag, TF* Y, TF* scratch, int* flags) {
   const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1);
   dev::SolveCtx<TF> c;
   c.tiles = tiles;
@@ -397,16 +397,18 @@ cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s,
   a.mats = nullptr;
   a.tickets = nullptr;
   a.spin_limit = p->opts.spin_limit;
-  a.single = solve_ctx<TF>(p, f, false, nr, tiles, invdiag, f->Y, f->sscratch, f->sflags);
+  TF* Y = reinterpret_cast<TF*>(f->Y);  // the double-sized workspaces also hold FP32 sweeps
+  TF* scr = reinterpret_cast<TF*>(f->sscratch);
+  a.single = solve_ctx<TF>(p, f, false, nr, tiles, invdiag, Y, scr, f->sflags);
   a.ntasks = p->dev->fwd.ntasks;
   a.ctl = f->ctl + 1;
-  dev::solve_f64_kernel<B, false, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  dev::solve_kernel<B, false, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B, TF>::SMEM, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  a.single = solve_ctx<TF>(p, f, true, nr, tiles, invdiag, f->Y, f->sscratch, f->sflags);
+  a.single = solve_ctx<TF>(p, f, true, nr, tiles, invdiag, Y, scr, f->sflags);
   a.ntasks = p->dev->bwd.ntasks;
   a.ctl = f->ctl + 2;
-  dev::solve_f64_kernel<B, true, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B>::SMEM, s>>>(a);
+  dev::solve_kernel<B, true, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B, TF>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -619,8 +621,12 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
                           double* out, int64_t old_, int r0, int nr) {
   const int64_t n = p->n, B = p->B;
   const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
-  dev::permute_in_kernel<<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(f->Y, rhs, p->dev->perm, n, rld, r0, nr,
-                                                                        int(B), p->nsb);
+  if (f->lp)
+    dev::permute_in_kernel<float><<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(
+        reinterpret_cast<float*>(f->Y), rhs, p->dev->perm, n, rld, r0, nr, int(B), p->nsb);
+  else
+    dev::permute_in_kernel<double><<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(f->Y, rhs, p->dev->perm, n, rld,
+                                                                                r0, nr, int(B), p->nsb);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(f->sflags, 0, size_t(2 * p->nsb + nf + nb) * sizeof(int), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl + 1, 2);
@@ -633,7 +639,12 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
     default: e = launch_solve<64, double>(p, f, st, nr, f->tiles, f->invdiag); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
-  dev::permute_out_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(out, f->Y, p->dev->perm, n, old_, r0, nr, int(B));
+  if (f->lp)
+    dev::permute_out_kernel<float><<<grid_for(n * nr, 256), 256, 0, st>>>(out, reinterpret_cast<const float*>(f->Y),
+                                                                          p->dev->perm, n, old_, r0, nr, int(B));
+  else
+    dev::permute_out_kernel<double><<<grid_for(n * nr, 256), 256, 0, st>>>(out, f->Y, p->dev->perm, n, old_, r0, nr,
+                                                                           int(B));
   CUDA_TRY(cudaGetLastError());
   count_launch(5);
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -952,7 +963,7 @@ struct BSolveDesc {
   const int64_t* perm;
   int64_t n, nsb;
   int B, nr;
-  double* Y;
+  void* Y;  // sweep blocks, in the factor's storage type
   double* b;
   double* x;
   double* r;
@@ -965,25 +976,29 @@ struct BSolveDesc {
 };
 
 // which = 0: b -> Y / Y -> x;  which = 1: r -> Y / Y -> d
+template <typename TY>
 __global__ void bpermute_in_kernel(const BSolveDesc* desc, int which) {
   const BSolveDesc c = desc[blockIdx.y];
   const double* src = which ? c.r : c.b;
+  TY* Y = static_cast<TY*>(c.Y);
   const int64_t total = c.nsb * c.B * c.nr;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t k = e / (int64_t(c.B) * c.nr);
     const int64_t rem = e % (int64_t(c.B) * c.nr);
     const int64_t r = rem / c.B, i = rem % c.B;
     const int64_t g = k * c.B + i;
-    c.Y[e] = (g < c.n) ? src[c.perm[g] + r * c.n] : 0.0;
+    Y[e] = (g < c.n) ? TY(src[c.perm[g] + r * c.n]) : TY(0);
   }
 }
 
+template <typename TY>
 __global__ void bpermute_out_kernel(const BSolveDesc* desc, int which) {
   const BSolveDesc c = desc[blockIdx.y];
   double* dst = which ? c.d : c.x;
+  const TY* Y = static_cast<const TY*>(c.Y);
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < c.n * c.nr; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = e / c.n, g = e % c.n;
-    dst[c.perm[g] + r * c.n] = c.Y[((g / c.B) * c.nr + r) * c.B + (g % c.B)];
+    dst[c.perm[g] + r * c.n] = double(Y[((g / c.B) * c.nr + r) * c.B + (g % c.B)]);
   }
 }
 
@@ -1256,9 +1271,10 @@ stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cuda
       tiles = v->tiles;
       inv = v->invdiag;
     }
-    double* Y = b->sY + b->y_off[i];
-    cf[i] = solve_ctx<TF>(p, nullptr, false, nr[i], tiles, inv, Y, b->sScr + b->scr_off[i], b->sFlags + b->flag_off[i]);
-    cb[i] = solve_ctx<TF>(p, nullptr, true, nr[i], tiles, inv, Y, b->sScr + b->scr_off[i], b->sFlags + b->flag_off[i]);
+    TF* Y = reinterpret_cast<TF*>(b->sY) + b->y_off[i];  // double-sized buffers also hold FP32 sweeps
+    TF* scr = reinterpret_cast<TF*>(b->sScr) + b->scr_off[i];
+    cf[i] = solve_ctx<TF>(p, nullptr, false, nr[i], tiles, inv, Y, scr, b->sFlags + b->flag_off[i]);
+    cb[i] = solve_ctx<TF>(p, nullptr, true, nr[i], tiles, inv, Y, scr, b->sFlags + b->flag_off[i]);
     BSolveDesc& d = desc[i];
     d.perm = p->dev->perm;
     d.n = p->n;
@@ -1292,14 +1308,14 @@ cudaError_t launch_batch_sweeps(stiles_batch* b, cudaStream_t st) {
   a.tickets = b->tfwd;
   a.ntasks = b->nfwd;
   a.ctl = b->sctl;
-  dev::solve_f64_kernel<B, false, TF><<<b->solve_grid, 128, dev::SolveCfg<B>::SMEM, st>>>(a);
+  dev::solve_kernel<B, false, TF><<<b->solve_grid, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   a.mats = static_cast<const dev::SolveCtx<TF>*>(b->dbwd);
   a.tickets = b->tbwd;
   a.ntasks = b->nbwd;
   a.ctl = b->sctl + 1;
-  dev::solve_f64_kernel<B, true, TF><<<b->solve_grid, 128, dev::SolveCfg<B>::SMEM, st>>>(a);
+  dev::solve_kernel<B, true, TF><<<b->solve_grid, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1314,7 +1330,8 @@ dim3 batch_grid(const stiles_batch* b, int64_t max_work) {
 stiles_status batch_solve_pass(stiles_batch* b, cudaStream_t st, int which, int64_t max_rows) {
   const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
   const dim3 g = batch_grid(b, max_rows * dev::SOLVE_MAXR);
-  bpermute_in_kernel<<<g, 256, 0, st>>>(desc, which);
+  if (b->lp) bpermute_in_kernel<float><<<g, 256, 0, st>>>(desc, which);
+  else bpermute_in_kernel<double><<<g, 256, 0, st>>>(desc, which);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(b->sFlags, 0, size_t(b->sflag_total) * sizeof(int), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->sctl, 2);
@@ -1327,7 +1344,8 @@ stiles_status batch_solve_pass(stiles_batch* b, cudaStream_t st, int which, int6
     default: e = launch_batch_sweeps<64, double>(b, st); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("batched solve launch: ") + cudaGetErrorString(e));
-  bpermute_out_kernel<<<g, 256, 0, st>>>(desc, which);
+  if (b->lp) bpermute_out_kernel<float><<<g, 256, 0, st>>>(desc, which);
+  else bpermute_out_kernel<double><<<g, 256, 0, st>>>(desc, which);
   CUDA_TRY(cudaGetLastError());
   count_launch(5);
   dev::Ctl c[2];

@@ -1,4 +1,10 @@
-// Persistent FP64 forward (L y = P b) and backward (L^T x = y) tile sweeps.
+// Persistent forward (L y = P b) and backward (L^T x = y) tile sweeps.
+//
+// The sweeps compute in the factor's storage type TF: FP64 for an FP64 factor;
+// FP32 for a mixed-precision factor (FP32 tiles), whose solves only feed the
+// FP64 iterative refinement -- the factor's own error (BF16/FP16 updates)
+// dominates FP32 rounding by orders of magnitude, and FP32 arithmetic runs at
+// 64 times the FP64 rate on this part.
 //
 // Same scheduling scheme as the factorization: one task per B-row block of
 // the right-hand sides, in ticket order, waiting on per-block ready flags.
@@ -19,7 +25,7 @@ namespace dev {
 
 constexpr int SOLVE_MAXR = 16;  // right-hand sides per launch
 
-template <int B>
+template <int B, typename TF>
 struct SolveCfg {
   static constexpr int NT = 128;
   static constexpr int W = (B < 32) ? B : 32;
@@ -29,17 +35,20 @@ struct SolveCfg {
   static constexpr int TILE = B * B;
   static constexpr int BLK = B * SOLVE_MAXR;
   static constexpr int NSTAGE = 3;
-  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * (TILE + BLK) + TILE + size_t(B) * (B + 1) + B;
-  static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
+  static constexpr size_t SMEM_ELEMS = size_t(NSTAGE) * (TILE + BLK) + TILE + size_t(B) * (B + 1) + B;
+  static constexpr size_t SMEM = ((SMEM_ELEMS * sizeof(TF) + 15) / 16) * 16 + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 // One matrix of a solve launch (a batched launch carries one per matrix).
 template <typename TF>
 struct SolveCtx {
   const TF* tiles;        // factor sub-tiles (FP64, or FP32 for a mixed-precision factor)
   const TF* invdiag;      // nsb * B
-  double* Y;              // nsb blocks of B x nr
-  double* scratch;        // nscratch blocks
+  TF* Y;                  // nsb blocks of B x nr
+  TF* scratch;            // nscratch blocks
   const SolveTask* tasks;
   const int32_t* pairs;   // (L sub-tile, block)
   const int32_t* parts;
@@ -61,15 +70,15 @@ struct SolveArgs {
 };
 
 template <int B, bool BACKWARD, typename TF>
-__global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
-  using Cfg = SolveCfg<B>;
+__global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
+  using Cfg = SolveCfg<B, TF>;
   constexpr int W = Cfg::W, RP = Cfg::RP, G = Cfg::G, U = Cfg::U, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  double* sStage = reinterpret_cast<double*>(smem_raw);            // NSTAGE * (TILE + BLK)
-  TF* sL = reinterpret_cast<TF*>(sStage + NSTAGE * (TILE + Cfg::BLK));  // TILE (room for doubles)
-  double* sLt = sStage + NSTAGE * (TILE + Cfg::BLK) + TILE;            // B x (B + 1), transposed L_kk
-  double* sInv = sLt + B * (B + 1);                                 // B
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sInv + B);
+  TF* sStage = reinterpret_cast<TF*>(smem_raw);                    // NSTAGE * (TILE + BLK)
+  TF* sL = sStage + NSTAGE * (TILE + Cfg::BLK);                     // TILE
+  TF* sLt = sL + TILE;                                              // B x (B + 1), transposed L_kk
+  TF* sInv = sLt + B * (B + 1);                                     // B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ((Cfg::SMEM_ELEMS * sizeof(TF) + 15) / 16) * 16);
   __shared__ int sTicket, sAbort;
 
   const int tid = threadIdx.x;
@@ -106,7 +115,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     const SolveCtx<TF> mc = a.mats ? a.mats[mi] : a.single;
     const SolveTask tk = mc.tasks[ti];
     const int nr = mc.nr;
-    const int blk = B * nr;  // doubles per block
+    const int blk = B * nr;  // elements per block
     long long* const trace = mc.trace ? mc.trace + 4 * size_t(ti) : nullptr;
     unsigned long long t_ready = 0;
     if (trace && tid == 0) {
@@ -115,20 +124,20 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
       trace[3] = smid();
     }
 
-    double acc[RP][U];
+    TF acc[RP][U];
     if (tk.type == SOLVE_FINAL) {
-      const double* src = mc.Y + size_t(tk.out) * blk;
+      const TF* src = mc.Y + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;
 #pragma unroll
-        for (int s = 0; s < RP; ++s) acc[s][u] = (r < nr) ? src[r * B + li + W * s] : 0.0;
+        for (int s = 0; s < RP; ++s) acc[s][u] = (r < nr) ? src[r * B + li + W * s] : TF(0);
       }
     } else {
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int s = 0; s < RP; ++s) acc[s][u] = 0.0;
+        for (int s = 0; s < RP; ++s) acc[s][u] = TF(0);
     }
 
     // the diagonal sub-tile does not depend on this sweep: fetch it first
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
         while (issued < nitems && issued < it + NSTAGE) {
           const int* f;
           const TF* gL = nullptr;
-          const double* gY;
+          const TF* gY;
           if (issued < npairs) {
             const int ls = mc.pairs[2 * (tk.pb + issued)];
             const int bk = mc.pairs[2 * (tk.pb + issued) + 1];
@@ -168,10 +177,10 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
           }
           fence_proxy_async_global();
           const int st = issued % NSTAGE;
-          double* dst = sStage + st * (TILE + Cfg::BLK);
-          mbar_arrive_expect_tx(&bars[st], uint32_t((gL ? TILE * sizeof(TF) : 0) + blk * sizeof(double)));
+          TF* dst = sStage + st * (TILE + Cfg::BLK);
+          mbar_arrive_expect_tx(&bars[st], uint32_t((gL ? TILE * sizeof(TF) : 0) + blk * sizeof(TF)));
           if (gL) tma_load_1d(dst, gL, TILE * sizeof(TF), &bars[st]);
-          tma_load_1d(dst + TILE, gY, uint32_t(blk * sizeof(double)), &bars[st]);
+          tma_load_1d(dst + TILE, gY, uint32_t(blk * sizeof(TF)), &bars[st]);
           ++issued;
         }
         if (trace && it == nitems - 1) t_ready = globaltimer();
@@ -187,8 +196,8 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
       }
       if (aborted) { stop = it; break; }
       phase ^= (1u << st);
-      const TF* sT = reinterpret_cast<const TF*>(sStage + st * (TILE + Cfg::BLK));
-      const double* sY = sStage + st * (TILE + Cfg::BLK) + TILE;
+      const TF* sT = sStage + st * (TILE + Cfg::BLK);
+      const TF* sY = sT + TILE;
       if (it < npairs) {
         if (!BACKWARD) {
           // acc(i, r) -= sum_p L(i, p) y(p, r)
@@ -198,9 +207,9 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
             for (int u = 0; u < U; ++u) {
               const int r = grp + G * u;
               if (r < nr) {
-                const double yv = sY[r * B + p];
+                const TF yv = sY[r * B + p];
 #pragma unroll
-                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-double(sT[li + W * s + p * B]), yv, acc[s][u]);
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma_t(-sT[li + W * s + p * B], yv, acc[s][u]);
               }
             }
           }
@@ -213,9 +222,9 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
             for (int u = 0; u < U; ++u) {
               const int r = grp + G * u;
               if (r < nr) {
-                const double xv = sY[r * B + p];
+                const TF xv = sY[r * B + p];
 #pragma unroll
-                for (int s = 0; s < RP; ++s) acc[s][u] = fma(-double(sT[p + (li + W * s) * B]), xv, acc[s][u]);
+                for (int s = 0; s < RP; ++s) acc[s][u] = fma_t(-sT[p + (li + W * s) * B], xv, acc[s][u]);
               }
             }
           }
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     }
 
     if (tk.type != SOLVE_FINAL) {
-      double* dst = mc.scratch + size_t(tk.out) * blk;
+      TF* dst = mc.scratch + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     }
 
     // ---- triangular solve with the diagonal sub-tile (prefetched above) ----
-    if (tid < B) sInv[tid] = double(__ldcg(mc.invdiag + size_t(tk.out) * B + tid));
+    if (tid < B) sInv[tid] = __ldcg(mc.invdiag + size_t(tk.out) * B + tid);
     {
       long long spins = 0;
       while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
     if (BACKWARD) {
       for (int e = tid; e < TILE; e += Cfg::NT) {
         const int r = e % B, c = e / B;
-        sLt[c + r * (B + 1)] = double(sL[e]);  // sLt(c, r) = L(r, c)
+        sLt[c + r * (B + 1)] = sL[e];  // sLt(c, r) = L(r, c)
       }
     }
     __syncthreads();
@@ -285,17 +294,17 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
 #pragma unroll
       for (int j = 0; j < B; ++j) {
         const int sj = j / W, lj = j % W;
-        const double inv = sInv[j];
+        const TF inv = sInv[j];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (warp_grp0 + G * u >= nr) break;
-          double y = acc[sj][u] * inv;
+          TF y = acc[sj][u] * inv;
           y = __shfl_sync(0xffffffffu, y, (tid & 31) - li + lj);
           if (li == lj) acc[sj][u] = y;
 #pragma unroll
           for (int s = 0; s < RP; ++s) {
             const int i = li + W * s;
-            if (i > j) acc[s][u] = fma(-double(sL[i + j * B]), y, acc[s][u]);
+            if (i > j) acc[s][u] = fma_t(-sL[i + j * B], y, acc[s][u]);
           }
         }
       }
@@ -304,23 +313,23 @@ __global__ void __launch_bounds__(128) solve_f64_kernel(SolveArgs<TF> a) {
 #pragma unroll
       for (int j = B - 1; j >= 0; --j) {
         const int sj = j / W, lj = j % W;
-        const double inv = sInv[j];
+        const TF inv = sInv[j];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (warp_grp0 + G * u >= nr) break;
-          double x = acc[sj][u] * inv;
+          TF x = acc[sj][u] * inv;
           x = __shfl_sync(0xffffffffu, x, (tid & 31) - li + lj);
           if (li == lj) acc[sj][u] = x;
 #pragma unroll
           for (int s = 0; s < RP; ++s) {
             const int i = li + W * s;
-            if (i < j) acc[s][u] = fma(-sLt[i + j * (B + 1)], x, acc[s][u]);
+            if (i < j) acc[s][u] = fma_t(-sLt[i + j * (B + 1)], x, acc[s][u]);
           }
         }
       }
     }
     {
-      double* dst = mc.Y + size_t(tk.out) * blk;
+      TF* dst = mc.Y + size_t(tk.out) * blk;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int r = grp + G * u;

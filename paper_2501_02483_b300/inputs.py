@@ -353,7 +353,7 @@ def dense_from_csc(m):
 
 
 def serving_workload(count, rate=500.0, seed=0, n_lo=1_000, n_hi=200_000, hw_lo=32, hw_hi=512, w_hi=100,
-                     nrhs_hi=16, resolve_frac=0.3, pool=48, density=0.2):
+                     nrhs_hi=16, resolve_frac=0.3, pool=48, density=0.2, variants=0):
     """Request stream of the serving workload.
 
     Arrivals are Poisson with the given rate.  A pool of ``pool`` distinct
@@ -363,8 +363,11 @@ def serving_workload(count, rate=500.0, seed=0, n_lo=1_000, n_hi=200_000, hw_lo=
     fresh theta ~ U(0.5, 2) (same structure, new values, as in a
     hyperparameter sweep); a re-solve request (probability ``resolve_frac``)
     names an earlier new request.  Every request carries nrhs ~ U{1..nrhs_hi}
-    N(0,1) right-hand sides.  Returns (requests, arrivals) with requests as
-    dicts {"id", "kind", "key", "matrix", "rhs", "target"}.
+    N(0,1) right-hand sides.  With ``variants`` > 0 each pattern has that many
+    pre-drawn thetas and a new request picks one of them (bounds host memory on
+    long streams; the matrices still differ from request to request in pattern
+    or scale).  Returns (requests, arrivals) with requests as dicts {"id",
+    "kind", "key", "matrix", "rhs", "target"}.
     """
     rng = np.random.default_rng(seed)
     shapes = []
@@ -376,6 +379,7 @@ def serving_workload(count, rate=500.0, seed=0, n_lo=1_000, n_hi=200_000, hw_lo=
                                  nrhs=0, name=f"serve{k}"))
     t = 0.0
     reqs, arrivals, news = [], [], []
+    shared = {}
     for i in range(count):
         t += float(rng.exponential(1.0 / rate))
         nrhs = int(rng.integers(1, nrhs_hi + 1))
@@ -388,7 +392,14 @@ def serving_workload(count, rate=500.0, seed=0, n_lo=1_000, n_hi=200_000, hw_lo=
             k = int(rng.integers(0, pool))
             theta = float(rng.uniform(0.5, 2.0))
             base = shapes[k]
-            reqs.append({"id": i, "kind": "new", "key": k, "matrix": scaled(base, theta),
+            if variants > 0:
+                v = int(rng.integers(0, variants))
+                mat = shared.get((k, v))
+                if mat is None:
+                    mat = shared[(k, v)] = scaled(base, 0.5 + 1.5 * (v + 0.5) / variants)
+            else:
+                mat = scaled(base, theta)
+            reqs.append({"id": i, "kind": "new", "key": k, "matrix": mat,
                          "rhs": np.asfortranarray(rng.normal(0.0, 1.0, (base["n"], nrhs))), "target": None})
             news.append(i)
         arrivals.append(t)
