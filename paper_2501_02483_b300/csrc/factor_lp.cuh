@@ -34,7 +34,9 @@ constexpr uint32_t LP_OP_BYTES = LP_TILE * 2;       // one 16-bit operand tile
 constexpr uint32_t LP_STAGE_BYTES = 3 * LP_OP_BYTES; // A (tile + 64 zero rows) + B
 constexpr uint32_t LP_TMEM_COLS = 128;              // two 64-column FP32 accumulators
 
-// shared memory: stages | sD (FP64 64x64) | sL (FP32 64x64) | sInv/sPiv/sRs (FP64 x 64 each) | barriers
+// shared memory: stages | sD (FP64 64x64) | sL (FP32 64x64) | sInv/sPiv/sRs (FP64 x 64 each; sPiv and sRs
+// hold the POTRF's flag words) | barriers
+static_assert(PotrfFlags<64>::WORDS * sizeof(int) <= 2 * 64 * sizeof(double), "POTRF flags fit in sPiv/sRs");
 constexpr size_t LP_SMEM = size_t(LP_NSTAGE) * LP_STAGE_BYTES + LP_TILE * 8 + LP_TILE * 4 + 3 * LP_B * 8 +
                            (LP_NSTAGE * 2 + 2) * 8 + 64;
 
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
   uint64_t* lbar = accbar + 1;                                // L_kk landed
   __shared__ uint32_t sTmem;
   __shared__ int sTicket, sAbort;
+  __shared__ uint16_t sIC[LP_B * (LP_B + 1) / 2];  // lower-triangle numbering of the POTRF
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     mbar_init(lbar, 1);
     mbar_fence_init();
   }
+  init_lower_index<LP_B>(sIC, tid, 128);
   // the 64 zero rows below each A operand tile (the MMA is M = 128)
   for (int s = 0; s < LP_NSTAGE; ++s) {
     uint4* z = reinterpret_cast<uint4*>(sStage + s * LP_STAGE_BYTES + LP_OP_BYTES);
@@ -412,26 +416,22 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       for (int c = 0; c < LP_B; ++c) sD[c * LP_B + r] = double(x1[c]);
     }
     __syncthreads();
-    double acc[FactorCfg<64>::CPT];
     {
-      constexpr int RPT = FactorCfg<64>::RPT;
-      const int row = tid / RPT, q = tid % RPT;
-#pragma unroll
-      for (int m = 0; m < FactorCfg<64>::CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + row];
-      __syncthreads();
-      const int bad = potrf_tile<64>(acc, sD, sPiv, sInv, sRs, row, q, tid);
+      // sPiv/sRs (2 x 64 doubles) hold the POTRF's flag words
+      const int bad = potrf_tile_ws<LP_B>(sD, sInv, sIC, reinterpret_cast<int*>(sPiv), tid, limit);
+      if (bad == -2) {
+        if (tid == 0) raise_timeout(a.ctl, t);
+        aborted = true;
+        break;
+      }
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)col * LP_B + bad + 1);
-      // L back to shared memory (column-major), then row-wise stores
-#pragma unroll
-      for (int m = 0; m < FactorCfg<64>::CPT; ++m) sD[(q + RPT * m) * LP_B + row] = acc[m];
     }
-    __syncthreads();
     if (warp < 2) {
       float* t32 = mc.tiles32 + size_t(out) * LP_TILE;
 #pragma unroll
       for (int c = 0; c < LP_B; ++c) t32[c * LP_B + r] = float(sD[c * LP_B + r]);
       mc.ldiag[size_t(col) * LP_B + r] = sD[r * LP_B + r];
-      mc.invdiag32[size_t(col) * LP_B + r] = float(1.0 / sD[r * LP_B + r]);
+      mc.invdiag32[size_t(col) * LP_B + r] = float(sInv[r]);
     }
     publish(mc.flags + out);
     if (trace && tid == 0) trace[2] = (long long)globaltimer();
