@@ -79,10 +79,15 @@ def parse():
     ap.add_argument("--workload", choices=["large", "sweep", "serve"], default="large")
     ap.add_argument("--batch", type=int, default=256, help="sweep: matrices per batch")
     ap.add_argument("--lp-tile", type=int, default=64, help="sweep/serve: tile of the mixed-precision arm")
+    ap.add_argument("--lp-precision", choices=["bf16", "f16"], default="f16",
+                    help="sweep/serve: 16-bit type of the mixed-precision updates")
     ap.add_argument("--f64-tile", type=int, default=16, help="sweep/serve: tile of the FP64 arm")
     ap.add_argument("--requests", type=int, default=1500, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=500.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=64, help="serve: matrices per batched launch")
+    ap.add_argument("--gpu-workers", type=int, default=3, help="serve: GPU jobs in flight (one stream each)")
+    ap.add_argument("--serve-ordering", choices=["none", "rcm", "auto", "nd"], default="nd",
+                    help="serve: ordering of every plan (nd halves the chains of the large matrices)")
     return ap.parse_args()
 
 
@@ -432,7 +437,7 @@ def run_sweep(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     mats = inputs.batch_sweep(args.batch, seed=rank)
-    prec = st.PREC_BF16
+    prec = st.PREC_BF16 if args.lp_precision == "bf16" else st.PREC_F16
     lp = _sweep_arm(args, st, torch, mats, prec, args.lp_tile, dev, stream, dist)
     f64 = _sweep_arm(args, st, torch, mats, st.PREC_F64, args.f64_tile, dev, stream, dist)
     ld_err = float(np.max(np.abs(lp["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
@@ -451,7 +456,7 @@ def run_sweep(args):
     line = {
         "metric": METRIC, "value": world * lp["tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": lp["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic",
         "config": {"workload": f"batched sweep: {args.batch} matrices, n log-uniform [5000, 50000], hw {{64,128,256}}, "
                                "arrow 0..50, theta ~ U(0.5, 2), 1 RHS each; refined to 1e-10",
                    "step": "batched factorize (one persistent launch) + all logdets + batched solve with FP64 "
@@ -495,15 +500,32 @@ def sweep_cpu_baseline(args, count=4):
                       f"({dt:.1f} s, one thread)", "seconds": dt, "flops": fl}
 
 
+def _pin_requests(torch, reqs):
+    """Client-side buffers in page-locked host memory (as a server receiving
+    requests would hold them): values arrays shared between requests stay
+    shared; right-hand sides keep their column-major layout."""
+    pinned = {}
+    for r in reqs:
+        if r["matrix"] is not None:
+            v = r["matrix"]["values"]
+            if id(v) not in pinned:
+                pinned[id(v)] = (v, torch.from_numpy(v).pin_memory().numpy())
+            r["matrix"] = dict(r["matrix"], values=pinned[id(v)][1])
+        r["rhs"] = torch.from_numpy(np.ascontiguousarray(r["rhs"].T)).pin_memory().numpy().T
+
+
 def _serve_arm(args, st, sv, torch, work, prec, T, stream):
     reqs, arrivals = work
     # warm-up on a throw-away server: a few requests of another stream load the kernels
-    warm = sv.Server(precision=prec, tile=T, max_batch=args.max_batch, hbm_budget=150e9)
+    order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[args.serve_ordering]
+    warm = sv.Server(precision=prec, tile=T, ordering=order, max_batch=args.max_batch, hbm_budget=150e9,
+                     gpu_workers=args.gpu_workers)
     wr, wa = inputs.serving_workload(12, rate=args.rate, seed=99, n_hi=20_000, pool=4)
     warm.run([sv.Request(r["id"], r["kind"], r["key"], r["matrix"], r["rhs"], r["target"]) for r in wr], wa,
              stream=stream, realtime=False)
     warm.close()
-    srv = sv.Server(precision=prec, tile=T, max_batch=args.max_batch, hbm_budget=150e9)
+    srv = sv.Server(precision=prec, tile=T, ordering=order, max_batch=args.max_batch, hbm_budget=150e9,
+                    gpu_workers=args.gpu_workers)
     objs = [sv.Request(r["id"], r["kind"], r["key"], r["matrix"], r["rhs"], r["target"]) for r in reqs]
     n0 = st.kernel_launches()
     with ClockSampler(stream.device.index) as clk:
@@ -517,6 +539,7 @@ def _serve_arm(args, st, sv, torch, work, prec, T, stream):
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "mean_batch": float(np.mean([r.batch_size for r in done if r.batch_size])),
            "requests_at_1e-10": len(ok), "requests": len(done), "stats": dict(srv.stats),
+           "seconds_by_phase": {k: round(v, 3) for k, v in srv.times.items()},
            "gpu_launches": launches, "clocks": clk.result}
     srv.close()
     return out
@@ -530,16 +553,19 @@ def run_serve(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     work = inputs.serving_workload(args.requests, rate=args.rate, seed=rank, variants=2)
-    lp = _serve_arm(args, st, sv, torch, work, st.PREC_BF16, args.lp_tile, stream)
+    _pin_requests(torch, work[0])
+    lp_prec = st.PREC_BF16 if args.lp_precision == "bf16" else st.PREC_F16
+    lp = _serve_arm(args, st, sv, torch, work, lp_prec, args.lp_tile, stream)
     f64 = _serve_arm(args, st, sv, torch, work, st.PREC_F64, args.f64_tile, stream)
     value = _max_over_ranks(torch, dist, dev, -lp["solves_per_s"])
     line = {
         "metric": METRIC, "value": -value * world, "unit": "solves/s", "n_gpus": world, "steps": 1,
         "warmup": 1, "ms_per_step": 1e3 * lp["wall_s"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic",
         "config": {"workload": f"serving: Poisson {args.rate:g} req/s, {args.requests} requests, n log-uniform "
                                "[1000, 200000], hw 32..512, arrow 0..100, nrhs 1..16, 30% re-solves, "
-                               "HBM budget 150 GB; 48 patterns x 2 value scales (theta in {0.875, 1.625})",
+                               "HBM budget 150 GB; 48 patterns x 2 value scales (theta in {0.875, 1.625}); client "
+                               "buffers in pinned host memory; ordering " + args.serve_ordering,
                    "step": "the whole request stream through the continuous-batching loop (arrivals in real time)",
                    "mixed_precision": lp, "fp64": f64,
                    "solves_per_s_bf16_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},

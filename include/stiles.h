@@ -223,7 +223,9 @@ stiles_status stiles_logdet_tiles_noalloc(const double* tiles, const int64_t* tc
  *   matrix: statuses[i] (OK, NOT_SPD, TIMEOUT) and infos[i] (first bad permuted column, 1-based,
  *   else 0); either array may be NULL.  Returns the first failure or OK.
  * stiles_batch_factor: a borrowed factor handle of matrix `index` for stiles_logdet, stiles_solve
- *   and stiles_factor_tiles; it lives until the batch is destroyed (do not destroy it).
+ *   and stiles_factor_tiles; it lives until the batch is destroyed (do not destroy it).  It is
+ *   factorized only through its batch: stiles_factorize(_async), stiles_factor_wait and
+ *   stiles_factor_timing on it return STILES_ERR_INVALID.
  * stiles_batch_logdet: all log-determinants in one launch, out[count] on the host. */
 stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count, stiles_batch** out);
 stiles_status stiles_batch_factorize(stiles_batch* batch, const double* const* values, void* stream,
@@ -237,7 +239,8 @@ stiles_status stiles_batch_logdet(stiles_batch* batch, double* out, void* stream
  *   rhs[i], x[i] : matrix i's right-hand sides and solutions, n_i x nrhs[i] column-major with
  *                  leading dimension n_i, host or device (each pointer on its own; caller-owned);
  *                  may be NULL where nrhs[i] == 0.
- *   nrhs[i]      : 0 .. 16 right-hand sides of matrix i (0 = matrix i takes no part).
+ *   nrhs[i]      : 0 .. 16 right-hand sides of matrix i (0 = matrix i takes no part: its tasks are
+ *                  left out of the sweeps, so a call costs what its participating matrices cost).
  *   relres       : NULL, or double[count] receiving max over matrix i's columns of
  *                  ||b - A x||_2 / ||b||_2 in FP64 (computed only when requested or refining).
  *   iters        : NULL, or int32[count] receiving the refinement steps matrix i took.
@@ -245,7 +248,7 @@ stiles_status stiles_batch_logdet(stiles_batch* batch, double* out, void* stream
  * residual meets its plan's refine_tol or max_refine steps; the refinement sweeps still cover the
  * whole batch but only unfinished matrices take the correction.  The batch must have been
  * factorized.  The first call allocates the batch's solve workspace (room for 16 right-hand sides
- * per matrix).  The call waits for its work.  Errors: STILES_ERR_INVALID (null pointers, nrhs out
+ * per matrix).  The call waits for its work; one thread at a time may use a batch.  Errors: STILES_ERR_INVALID (null pointers, nrhs out
  * of range), STILES_ERR_TIMEOUT, STILES_ERR_NOT_CONVERGED (a matrix missed refine_tol; its x is
  * still the best iterate), STILES_ERR_NOMEM, STILES_ERR_CUDA, STILES_ERR_UNSUPPORTED (more than
  * 65,535 matrices). */

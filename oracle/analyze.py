@@ -27,7 +27,7 @@ def analyze(m, T, order=ORDER_AUTO):
         cands = [(ORDER_RCM, ordering.partial_rcm(n, colptr, rowidx, na))]
     elif order == ORDER_ND:
         # chosen for parallelism, not fill (Section III.A: "when enough cores are available")
-        cands = [(ORDER_ND, ordering.adaptable_nd(n, colptr, rowidx, na))]
+        cands = [(ORDER_ND, ordering.adaptable_nd(n, colptr, rowidx, na, align=T))]
     else:
         cands = [(ORDER_NONE, ident), (ORDER_RCM, ordering.partial_rcm(n, colptr, rowidx, na))]
     best = None

@@ -127,13 +127,16 @@ def partial_rcm(n, colptr, rowidx, n_arrow):
     return np.concatenate([body, np.arange(nb, n, dtype=np.int64)])
 
 
-def adaptable_nd(n, colptr, rowidx, n_arrow):
+def adaptable_nd(n, colptr, rowidx, n_arrow, align=1):
     """One level of the adaptable nested dissection of Section III.A.
 
     The paper's recipe: take a separator as wide as the bandwidth and move it
     towards the end of the matrix, ahead of the arrow.  Reading used here:
 
-    * the body [0, nb) is split at mid = nb // 2;
+    * the body [0, nb) is split at mid = (nb // 2) rounded down to a multiple
+      of ``align`` (the tile size: a tile holding rows of both parts would join
+      the two elimination chains again at the tile level); mid = 0 leaves the
+      order unchanged;
     * the separator S = [mid, s_end) holds every row that some body column
       left of mid reaches: s_end = 1 + max{i : (i, j) stored, j < mid <= i < nb}
       (S is empty when nothing crosses mid);
@@ -144,9 +147,9 @@ def adaptable_nd(n, colptr, rowidx, n_arrow):
     and the part's interior, and the two parts are independent chains.
     """
     nb = n - n_arrow
-    if nb < 2:
+    mid = (nb // 2) // align * align
+    if nb < 2 or mid == 0:
         return identity_perm(n)
-    mid = nb // 2
     cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr))
     rows = rowidx.astype(np.int64)
     cross = (cols < mid) & (rows >= mid) & (rows < nb)

@@ -150,20 +150,24 @@ std::vector<int64_t> partial_rcm(int64_t n, const int64_t* colptr, const int32_t
 
 // ---------------------------------------------------------------------------
 // Adaptable nested dissection, one level (Section III.A): split the body at
-// mid = nb / 2, take as separator every row in [mid, nb) that a column left of
-// mid reaches, and order [0, mid), then the rest of the body reversed, then the
-// separator, then the arrow.  Both parts meet the separator with their last
-// rows, so they are independent elimination chains.
+// mid = nb / 2 rounded down to a multiple of the tile size, take as separator
+// every row in [mid, nb) that a column left of mid reaches, and order [0, mid),
+// then the rest of the body reversed, then the separator, then the arrow.
+// Both parts meet the separator with their last rows, so they are independent
+// elimination chains (also at the tile level, the split being tile-aligned).
 // ---------------------------------------------------------------------------
-std::vector<int64_t> adaptable_nd(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow) {
+std::vector<int64_t> adaptable_nd(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
+                                  int64_t align) {
   const int64_t nb = n - n_arrow;
   std::vector<int64_t> perm;
   perm.reserve(n);
-  if (nb < 2) {
+  // split at nb / 2 rounded down to a tile boundary: a tile holding rows of
+  // both parts would join the two elimination chains again at the tile level
+  const int64_t mid = (nb / 2) / align * align;
+  if (nb < 2 || mid == 0) {
     for (int64_t i = 0; i < n; ++i) perm.push_back(i);
     return perm;
   }
-  const int64_t mid = nb / 2;
   int64_t s_end = mid;
   for (int64_t j = 0; j < mid; ++j)
     for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
@@ -183,27 +187,34 @@ std::vector<int64_t> adaptable_nd(int64_t n, const int64_t* colptr, const int32_
 // tree: the structure of tile column k (minus its first row p) is merged into
 // column p, which yields the same map as adding every pair of S_k.
 // ---------------------------------------------------------------------------
+// Tile row/column of every original index under the permutation: tile of
+// position iperm[i] (avoids a division per entry in the O(nnz) passes).
+std::vector<int32_t> tile_of_index(int64_t n, const std::vector<int64_t>& iperm, int64_t T) {
+  std::vector<int32_t> t(n);
+  for (int64_t i = 0; i < n; ++i) t[i] = int32_t(iperm[i] / T);
+  return t;
+}
+
 std::vector<std::vector<int32_t>> tile_columns(int64_t n, const int64_t* colptr, const int32_t* rowidx,
                                                const std::vector<int64_t>& iperm, int64_t T, int64_t nt) {
+  const std::vector<int32_t> tile = tile_of_index(n, iperm, T);
   // bucket the entries of P A P^T (flipped to the lower triangle) by tile column
   std::vector<int64_t> cnt(nt + 1, 0);
   for (int64_t j = 0; j < n; ++j) {
-    int64_t q = iperm[j];
+    const int32_t tq = tile[j];
     for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
-      int64_t p = iperm[rowidx[e]];
-      int64_t r = std::max(p, q), c = std::min(p, q);
-      if (r / T != c / T) ++cnt[c / T + 1];
+      const int32_t tp = tile[rowidx[e]];
+      if (tp != tq) ++cnt[std::min(tp, tq) + 1];
     }
   }
   for (int64_t J = 0; J < nt; ++J) cnt[J + 1] += cnt[J];
   std::vector<int32_t> rows(cnt[nt]);
   std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
   for (int64_t j = 0; j < n; ++j) {
-    int64_t q = iperm[j];
+    const int32_t tq = tile[j];
     for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
-      int64_t p = iperm[rowidx[e]];
-      int64_t r = std::max(p, q), c = std::min(p, q);
-      if (r / T != c / T) rows[fill[c / T]++] = int32_t(r / T);
+      const int32_t tp = tile[rowidx[e]];
+      if (tp != tq) rows[fill[std::min(tp, tq)]++] = std::max(tp, tq);
     }
   }
   std::vector<std::vector<int32_t>> cols(nt);
@@ -562,6 +573,25 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   p->T = int32_t(T);
   p->colptr.assign(colptr, colptr + n + 1);
   p->rowidx.assign(rowidx, rowidx + nnz);
+  // CSR index of the strict lower part (the residual y = A x gathers row i's
+  // entries j < i from it and column i's entries from the CSC)
+  p->rptr.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e)
+      if (rowidx[e] != j) ++p->rptr[rowidx[e] + 1];
+  for (int64_t i = 0; i < n; ++i) p->rptr[i + 1] += p->rptr[i];
+  p->rcol.resize(p->rptr[n]);
+  p->rval.resize(p->rptr[n]);
+  {
+    std::vector<int64_t> fill(p->rptr.begin(), p->rptr.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+        const int64_t i = rowidx[e];
+        if (i == j) continue;
+        p->rcol[fill[i]] = int32_t(j);
+        p->rval[fill[i]++] = e;
+      }
+  }
   const int64_t nt = (n + T - 1) / T;
   p->nt = nt;
 
@@ -576,7 +606,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   }
   if (o.ordering == STILES_ORDER_ND) {
     // chosen for parallelism (two independent chains), not by the fill rule
-    p->perm = adaptable_nd(n, colptr, rowidx, n_arrow);
+    p->perm = adaptable_nd(n, colptr, rowidx, n_arrow, T);
     best_cols = tile_columns(n, colptr, rowidx, invert(p->perm), T, nt);
     p->ordering_used = STILES_ORDER_ND;
   }
@@ -686,17 +716,35 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   p->diag_sub.assign(nsb, -1);
   for (int64_t k = 0; k < nsb; ++k) p->diag_sub[k] = scol[k].front().sub;
 
-  // scatter map of every input entry into the tile buffer
+  // scatter map of every input entry into the tile buffer; B is a power of two
+  // and per-index tables give each permuted index's tile and offset, so the
+  // O(nnz) pass does no division, and consecutive entries usually hit the tile
+  // looked up last
   p->scatter.resize(nnz);
-  for (int64_t j = 0; j < n; ++j) {
-    const int64_t q = p->iperm[j];
-    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
-      const int64_t pr = p->iperm[rowidx[e]];
-      const int64_t r = std::max(pr, q), c = std::min(pr, q);
-      const int64_t t = tile_index(r / T, c / T);
-      if (t < 0) { *err = "internal: entry outside the tile map"; return STILES_ERR_INVALID; }
-      const int64_t s = t * R * R + ((c % T) / B) * R + ((r % T) / B);
-      p->scatter[e] = s * B * B + (c % B) * B + (r % B);
+  {
+    const int lb = (B == 16) ? 4 : (B == 32 ? 5 : 6);
+    std::vector<int32_t> tile(n), off(n);
+    for (int64_t i = 0; i < n; ++i) {
+      tile[i] = int32_t(p->iperm[i] / T);
+      off[i] = int32_t(p->iperm[i] % T);
+    }
+    int64_t lastI = -1, lastJ = -1, lastT = -1;
+    for (int64_t j = 0; j < n; ++j) {
+      for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+        const int64_t i = rowidx[e];
+        // lower-triangle orientation of the permuted entry: (row r, column c) with r >= c
+        const bool flip = p->iperm[i] < p->iperm[j];
+        const int64_t tr = flip ? tile[j] : tile[i], tc = flip ? tile[i] : tile[j];
+        const int64_t orr = flip ? off[j] : off[i], oc = flip ? off[i] : off[j];
+        if (tr != lastI || tc != lastJ) {
+          lastI = tr;
+          lastJ = tc;
+          lastT = tile_index(tr, tc);
+          if (lastT < 0) { *err = "internal: entry outside the tile map"; return STILES_ERR_INVALID; }
+        }
+        const int64_t sub = lastT * R * R + (oc >> lb) * R + (orr >> lb);
+        p->scatter[e] = (sub << (2 * lb)) + ((oc & (B - 1)) << lb) + (orr & (B - 1));
+      }
     }
   }
   p->pad.clear();

@@ -144,29 +144,90 @@ __global__ void permute_out_kernel(double* __restrict__ x, const TY* __restrict_
   }
 }
 
-// y = A x for the symmetric A stored as its lower CSC (diagonal included):
-// column j contributes a_jj x_j and sum_{i>j} a_ij x_i to y_j (gather) and
-// a_ij x_j to y_i (scatter, atomic).  r = b - y, then per column the sums of
-// squares of r and b.
-__global__ void spmv_lower_kernel(double* __restrict__ y, const double* __restrict__ x, const int64_t* __restrict__ colptr,
-                                  const int32_t* __restrict__ rowidx, const double* __restrict__ val, int64_t n,
-                                  int64_t ldx, int nr) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < n * nr; w += stride) {
-    const int r = int(w / n);
-    const int64_t j = w % n;
-    const double* xr = x + r * ldx;
-    double* yr = y + r * n;
-    const double xj = xr[j];
-    double s = 0.0;
-    for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
-      const int64_t i = rowidx[e];
-      const double v = val[e];
-      s = fma(v, xr[i], s);
-      if (i != j) atomicAdd(yr + i, v * xj);
-    }
-    atomicAdd(yr + j, s);
+// y(k, r) = sum_i a_ki x(i, r) for the symmetric A held as its lower CSC
+// (diagonal included) plus the CSR index of its strict lower part (rptr, rcol,
+// and rval = the CSC position of each entry): column k of the CSC gives the
+// terms i >= k, row k of the CSR the terms j < k, so the product is a pure
+// gather (no atomics, a fixed summation order).  One warp per index k, the
+// lanes striding over the entries (coalesced), each loaded entry serving all
+// NR right-hand sides.  The NR per-lane sums are combined by a butterfly
+// reduce-scatter: at each of the first log2(NR) shuffle levels a lane keeps
+// half of its sums and adds the partner's copy of that half, so NR = 16 costs
+// 16 FP64 adds per warp instead of 5 * 16 for separate reductions (an FP64 add
+// takes as much pipe time as an FMA); lane l ends with column (l >> (5 - log2 NR)).
+template <int NR>
+__device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* __restrict__ colptr,
+                                           const int32_t* __restrict__ rowidx, const int64_t* __restrict__ rptr,
+                                           const int32_t* __restrict__ rcol, const int64_t* __restrict__ rval,
+                                           const double* __restrict__ val, const double* __restrict__ x, int64_t ldx,
+                                           double* __restrict__ y, int64_t ldy, int nr) {
+  static_assert(NR == 1 || NR == 2 || NR == 4 || NR == 8 || NR == 16, "NR is a power of two <= 16");
+  double v[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) v[r] = 0.0;
+  const int64_t c1 = colptr[k + 1];
+  for (int64_t e = colptr[k] + lane; e < c1; e += 32) {
+    const double a = __ldg(val + e);
+    const int64_t i = __ldg(rowidx + e);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) v[r] = fma(a, __ldg(x + i + r * ldx), v[r]);
   }
+  const int64_t r1 = rptr[k + 1];
+  for (int64_t e = rptr[k] + lane; e < r1; e += 32) {
+    const double a = __ldg(val + __ldg(rval + e));
+    const int64_t j = __ldg(rcol + e);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) v[r] = fma(a, __ldg(x + j + r * ldx), v[r]);
+  }
+  // butterfly reduce-scatter over the 32 lanes
+  int cnt = NR;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt / 2;
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int h = 0; h < NR / 2; ++h) {
+        if (h < half) {
+          const double send = upper ? v[h] : v[h + half];
+          const double keep = upper ? v[h + half] : v[h];
+          v[h] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      cnt = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    }
+  }
+  constexpr int SHIFT = (NR == 1) ? 5 : (NR == 2) ? 4 : (NR == 4) ? 3 : (NR == 8) ? 2 : 1;
+  const int r = lane >> SHIFT;
+  if ((lane & ((1 << SHIFT) - 1)) == 0 && r < nr) y[k + r * ldy] = v[0];
+}
+
+// nr <= 16 right-hand sides in groups of 1, 2, 4, 8 or 16 (an FP64 instruction
+// predicated off still takes its pipe slot, so the group fits nr)
+__device__ __forceinline__ void symv_index_any(int64_t k, int lane, const int64_t* colptr, const int32_t* rowidx,
+                                               const int64_t* rptr, const int32_t* rcol, const int64_t* rval,
+                                               const double* val, const double* x, int64_t ldx, double* y,
+                                               int64_t ldy, int nr) {
+  if (nr <= 1) symv_index<1>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+  else if (nr <= 2) symv_index<2>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+  else if (nr <= 4) symv_index<4>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+  else if (nr <= 8) symv_index<8>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+  else symv_index<16>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+}
+
+// y = A x (n x nr, leading dimensions ldx / n), one warp per index
+__global__ void symv_kernel(double* __restrict__ y, const double* __restrict__ x, const int64_t* __restrict__ colptr,
+                            const int32_t* __restrict__ rowidx, const int64_t* __restrict__ rptr,
+                            const int32_t* __restrict__ rcol, const int64_t* __restrict__ rval,
+                            const double* __restrict__ val, int64_t n, int64_t ldx, int nr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps)
+    symv_index_any(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, n, nr);
 }
 
 __global__ void residual_norms_kernel(const double* __restrict__ y, const double* __restrict__ b, int64_t n, int64_t ldb,

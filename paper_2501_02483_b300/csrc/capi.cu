@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -82,6 +83,9 @@ struct DevPlan {
   int32_t* diag_sub = nullptr;
   int64_t* colptr = nullptr;
   int32_t* rowidx = nullptr;
+  int64_t* rptr = nullptr;   // CSR index of the strict lower part (residual SpMV)
+  int32_t* rcol = nullptr;
+  int64_t* rval = nullptr;
   DevGraph fac, fwd, bwd;
   int grid_factor = 0, grid_solve = 0;
 };
@@ -146,6 +150,9 @@ void free_dev_plan(stiles_plan* p) {
   cudaFree(d->diag_sub);
   cudaFree(d->colptr);
   cudaFree(d->rowidx);
+  cudaFree(d->rptr);
+  cudaFree(d->rcol);
+  cudaFree(d->rval);
   free_graph(d->fac);
   free_graph(d->fwd);
   free_graph(d->bwd);
@@ -173,7 +180,15 @@ cudaError_t solve_occupancy(int* blocks) {
                                                        dev::SolveCfg<B, TF>::SMEM);
 }
 
+std::mutex g_plan_mutex;  // plans are shared between threads (plan caches); uploads happen once
+
+#ifndef STILES_SOLVE_CTAS_PER_MATRIX
+#define STILES_SOLVE_CTAS_PER_MATRIX 128
+#endif
+constexpr int kSolveCtasPerMatrix = STILES_SOLVE_CTAS_PER_MATRIX;  // persistent CTAs per matrix of a solve launch
+
 stiles_status ensure_dev_plan(const stiles_plan* cp) {
+  std::lock_guard<std::mutex> lock(g_plan_mutex);
   stiles_plan* p = const_cast<stiles_plan*>(cp);
   int device = 0;
   CUDA_TRY(cudaGetDevice(&device));
@@ -189,7 +204,8 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
   auto chk = [&](cudaError_t e) { return e == cudaSuccess; };
   bool ok = chk(upload(&d->scatter, p->scatter)) && chk(upload(&d->pad, p->pad)) && chk(upload(&d->perm, p->perm)) &&
             chk(upload(&d->diag_sub, p->diag_sub)) && chk(upload(&d->colptr, p->colptr)) &&
-            chk(upload(&d->rowidx, p->rowidx)) && chk(upload(&d->fac.tasks, p->graph.tasks)) &&
+            chk(upload(&d->rowidx, p->rowidx)) && chk(upload(&d->rptr, p->rptr)) && chk(upload(&d->rcol, p->rcol)) &&
+            chk(upload(&d->rval, p->rval)) && chk(upload(&d->fac.tasks, p->graph.tasks)) &&
             chk(upload(&d->fac.pairs, p->graph.pairs)) && chk(upload(&d->fac.parts, p->graph.parts)) &&
             chk(upload(&d->fwd.stasks, p->fwd.tasks)) && chk(upload(&d->fwd.pairs, p->fwd.pairs)) &&
             chk(upload(&d->fwd.parts, p->fwd.parts)) && chk(upload(&d->bwd.stasks, p->bwd.tasks)) &&
@@ -226,7 +242,11 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
     sb = std::min(sb, int(p->opts.ctas_per_sm));
   }
   d->grid_factor = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(fb) * sms, d->fac.ntasks)));
-  d->grid_solve = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sb) * sms, std::max(d->fwd.ntasks, d->bwd.ntasks))));
+  // a sweep is a few dependency chains (two per nested-dissection level plus the
+  // arrow tree): a small grid keeps them fed and leaves the other SMs to
+  // concurrent launches (a waiting persistent CTA holds its SM slot)
+  d->grid_solve = int(std::max<int64_t>(
+      1, std::min<int64_t>({int64_t(sb) * sms, int64_t(kSolveCtasPerMatrix), std::max(d->fwd.ntasks, d->bwd.ntasks)})));
   return STILES_OK;
 }
 
@@ -237,6 +257,8 @@ void free_factor(stiles_factor* f) {
     f->tiles32 = f->scratch32 = f->invdiag32 = nullptr;
     f->tiles16 = nullptr;
     f->flags = nullptr;
+    f->ctl = nullptr;
+    f->logdet_part = f->norms = nullptr;
   }
   cudaFree(f->values);
   cudaFree(f->tiles);
@@ -528,6 +550,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   if (s != STILES_OK) return s;
   stiles_factor* f = *inout;
   if (f && f->plan != p) return fail(STILES_ERR_INVALID, "factor belongs to another plan");
+  if (f && f->view) return fail(STILES_ERR_INVALID, "a factor of a batch is factorized through its batch");
   if (!f) {
     s = alloc_factor(p, &f);
     if (s != STILES_OK) return s;
@@ -578,6 +601,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
 
 stiles_status stiles_factor_wait(stiles_factor* f, int64_t* info) {
   if (!f) return fail(STILES_ERR_INVALID, "null factor");
+  if (f->view) return fail(STILES_ERR_INVALID, "a factor of a batch is waited on through its batch");
   if (info) *info = 0;
   CUDA_TRY(cudaEventSynchronize(f->done));
   f->pending = false;
@@ -658,10 +682,10 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
 stiles_status residual_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t st, const double* x, int64_t ldx,
                              const double* b, int64_t ldb, int r0, int nr, double* rout, double* worst) {
   const int64_t n = p->n;
-  CUDA_TRY(cudaMemsetAsync(f->ywork, 0, size_t(n) * nr * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(f->norms, 0, 2 * dev::SOLVE_MAXR * sizeof(double), st));
-  dev::spmv_lower_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(f->ywork, x + r0 * ldx, p->dev->colptr,
-                                                               p->dev->rowidx, f->values, n, ldx, nr);
+  dev::symv_kernel<<<grid_for(n * 32, 256), 256, 0, st>>>(f->ywork, x + r0 * ldx, p->dev->colptr, p->dev->rowidx,
+                                                         p->dev->rptr, p->dev->rcol, p->dev->rval, f->values, n,
+                                                         ldx, nr);
   CUDA_TRY(cudaGetLastError());
   dev::residual_norms_kernel<<<dim3(64, nr), 256, 0, st>>>(f->ywork, b + r0 * ldb, n, ldb, nr, f->norms);
   CUDA_TRY(cudaGetLastError());
@@ -808,6 +832,7 @@ stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* st
 
 stiles_status stiles_factor_timing(const stiles_factor* f, double* ms_call, double* ms_kernel) {
   if (!f) return fail(STILES_ERR_INVALID, "null factor");
+  if (!f->ev[0]) return fail(STILES_ERR_INVALID, "a factor of a batch has no own timing (stiles_batch_timing)");
   float a = 0.f, b = 0.f;
   CUDA_TRY(cudaEventSynchronize(f->ev[2]));
   CUDA_TRY(cudaEventElapsedTime(&a, f->ev[0], f->ev[2]));
@@ -907,8 +932,8 @@ struct stiles_batch {
   int64_t nnz_total = 0, pad_total = 0, tile_elems = 0, scratch_elems = 0, diag_elems = 0, flag_total = 0;
   std::vector<int64_t> val_off;
   double* values = nullptr;
-  int64_t* map = nullptr;
-  int64_t* pad = nullptr;
+  void* dscatter = nullptr;  // per-matrix BScatter descriptors (each plan's own device scatter map)
+  int64_t max_scatter = 0;   // largest nnz + padding count of one matrix
   double* tiles = nullptr;
   double* scratch = nullptr;
   double* invdiag = nullptr;
@@ -927,6 +952,9 @@ struct stiles_batch {
   long long spin_limit = 0;
   double* logdet_out = nullptr;
   void* dlog = nullptr;
+  stiles::dev::Ctl* vctl = nullptr;  // the views' small arrays, 3 Ctl / logdet partials / norms each
+  double* vlog = nullptr;
+  double* vnorm = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the persistent kernel (recorded inside the graph)
@@ -953,10 +981,32 @@ struct stiles_batch {
   int2* tfwd = nullptr;
   int2* tbwd = nullptr;
   int nfwd = 0, nbwd = 0;
+  int2* tcall_fwd = nullptr;  // tickets of a call that solves only some matrices
+  int2* tcall_bwd = nullptr;
   std::vector<int64_t> y_off, scr_off, flag_off;
 };
 
 namespace {
+
+// Per-matrix descriptor of the batched scatter: the plan's own device scatter
+// map and padding list, offset into the batch's concatenated values and tiles.
+struct BScatter {
+  const int64_t* map;
+  const int64_t* pad;
+  int64_t nnz, npad, val_off, tile_off;
+};
+
+// tiles[tile_off + map[e]] = values[val_off + e] and the padding diagonal ones,
+// matrix blockIdx.y (targets are distinct: the tiles are zeroed beforehand).
+template <typename T>
+__global__ void bscatter_kernel(T* __restrict__ tiles, const double* __restrict__ values, const BScatter* desc) {
+  const BScatter c = desc[blockIdx.y];
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < c.nnz; e += stride)
+    tiles[c.tile_off + __ldg(c.map + e)] = T(__ldg(values + c.val_off + e));
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < c.npad; e += stride)
+    tiles[c.tile_off + __ldg(c.pad + e)] = T(1);
+}
 
 // Per-matrix descriptor of the batched helper kernels around the solves.
 struct BSolveDesc {
@@ -971,6 +1021,9 @@ struct BSolveDesc {
   double* y;
   const int64_t* colptr;
   const int32_t* rowidx;
+  const int64_t* rptr;
+  const int32_t* rcol;
+  const int64_t* rval;
   const double* values;
   double* norms;  // 2 per right-hand side: ||b - A x||^2, ||b||^2
 };
@@ -1002,22 +1055,14 @@ __global__ void bpermute_out_kernel(const BSolveDesc* desc, int which) {
   }
 }
 
+// y = A x for matrix blockIdx.y, one warp per index (no atomics)
 __global__ void bspmv_kernel(const BSolveDesc* desc) {
   const BSolveDesc c = desc[blockIdx.y];
-  for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < c.n * c.nr; w += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = w / c.n, j = w % c.n;
-    const double* xr = c.x + r * c.n;
-    double* yr = c.y + r * c.n;
-    const double xj = xr[j];
-    double s = 0.0;
-    for (int64_t e = c.colptr[j]; e < c.colptr[j + 1]; ++e) {
-      const int64_t i = c.rowidx[e];
-      const double v = c.values[e];
-      s = fma(v, xr[i], s);
-      if (i != j) atomicAdd(yr + i, v * xj);
-    }
-    atomicAdd(yr + j, s);
-  }
+  if (c.nr == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c.n; k += warps)
+    dev::symv_index_any(k, lane, c.colptr, c.rowidx, c.rptr, c.rcol, c.rval, c.values, c.x, c.n, c.y, c.n, c.nr);
 }
 
 // r = b - y and the squared norms per right-hand side (grid.z = right-hand side)
@@ -1078,42 +1123,82 @@ __global__ void batch_logdet_kernel(const BatchLogCtx* ctx, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
+// Batch arrays come from the device's stream-ordered memory pool, allocated
+// and freed on the batch's private stream: creating and destroying batches in a
+// serving loop then neither maps fresh device pages each time nor waits for the
+// whole device (as a cudaFree may while other streams run).  The pool keeps
+// freed memory for reuse (release threshold raised once per device).
+void keep_pool_memory(int device) {
+  static std::mutex m;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lock(m);
+  if (std::find(done.begin(), done.end(), device) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t threshold = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  cudaGetLastError();
+  done.push_back(device);
+}
+
+template <class T>
+cudaError_t batch_alloc(stiles_batch* b, T** p, size_t count) {
+  return cudaMallocAsync(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T), b->stream);
+}
+
+template <class T>
+cudaError_t batch_upload(stiles_batch* b, T** p, const std::vector<T>& v) {
+  cudaError_t e = batch_alloc(b, p, v.size());
+  if (e == cudaSuccess && !v.empty())
+    e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream);
+  return e;
+}
+
 void free_batch(stiles_batch* b) {
   if (!b) return;
   for (stiles_factor* v : b->views) free_factor(v);
-  cudaFree(b->values);
-  cudaFree(b->map);
-  cudaFree(b->pad);
-  cudaFree(b->tiles);
-  cudaFree(b->scratch);
-  cudaFree(b->invdiag);
-  cudaFree(b->tiles32);
-  cudaFree(b->tiles16);
-  cudaFree(b->scratch32);
-  cudaFree(b->invdiag32);
-  cudaFree(b->ldiag);
-  cudaFree(b->flags);
-  cudaFree(b->infos);
-  cudaFree(b->ctl);
-  cudaFree(b->dmats);
-  cudaFree(b->dtickets);
-  cudaFree(b->logdet_out);
-  cudaFree(b->dlog);
-  cudaFree(b->sY);
-  cudaFree(b->sScr);
-  cudaFree(b->sFlags);
-  cudaFree(b->vb);
-  cudaFree(b->vx);
-  cudaFree(b->vr);
-  cudaFree(b->vd);
-  cudaFree(b->vy);
-  cudaFree(b->vnorms);
-  cudaFree(b->sctl);
-  cudaFree(b->dfwd);
-  cudaFree(b->dbwd);
-  cudaFree(b->ddesc);
-  cudaFree(b->tfwd);
-  cudaFree(b->tbwd);
+  // batch arrays come from the stream-ordered pool (batch_alloc)
+  auto release = [&](void* q) {
+    if (q) cudaFreeAsync(q, b->stream);
+  };
+  release(b->values);
+  release(b->dscatter);
+  release(b->tiles);
+  release(b->scratch);
+  release(b->invdiag);
+  release(b->tiles32);
+  release(b->tiles16);
+  release(b->scratch32);
+  release(b->invdiag32);
+  release(b->ldiag);
+  release(b->flags);
+  release(b->infos);
+  release(b->ctl);
+  release(b->dmats);
+  release(b->dtickets);
+  release(b->logdet_out);
+  release(b->dlog);
+  release(b->vctl);
+  release(b->vlog);
+  release(b->vnorm);
+  release(b->sY);
+  release(b->sScr);
+  release(b->sFlags);
+  release(b->vb);
+  release(b->vx);
+  release(b->vr);
+  release(b->vd);
+  release(b->vy);
+  release(b->vnorms);
+  release(b->sctl);
+  release(b->dfwd);
+  release(b->dbwd);
+  release(b->ddesc);
+  release(b->tfwd);
+  release(b->tbwd);
+  release(b->tcall_fwd);
+  release(b->tcall_bwd);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -1126,21 +1211,19 @@ void free_batch(stiles_batch* b) {
 // Enqueue the per-call device work after the values are in place.
 stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   const size_t tbytes = b->lp ? sizeof(float) : sizeof(double);
+  const int count = int(b->plans.size());
+  const dim3 sg(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_scatter + 255) / 256,
+                                                                  std::max<int64_t>(1, 148 * 32 / count)))),
+                unsigned(count));
+  const BScatter* sd = static_cast<const BScatter*>(b->dscatter);
   if (b->lp) {
     CUDA_TRY(cudaMemsetAsync(b->tiles32, 0, size_t(b->tile_elems) * tbytes, st));
-    dev::scatter_f32_kernel<<<grid_for(b->nnz_total, 256), 256, 0, st>>>(b->tiles32, b->values, b->map, b->nnz_total);
+    bscatter_kernel<float><<<sg, 256, 0, st>>>(b->tiles32, b->values, sd);
   } else {
     CUDA_TRY(cudaMemsetAsync(b->tiles, 0, size_t(b->tile_elems) * tbytes, st));
-    dev::scatter_kernel<<<grid_for(b->nnz_total, 256), 256, 0, st>>>(b->tiles, b->values, b->map, b->nnz_total);
+    bscatter_kernel<double><<<sg, 256, 0, st>>>(b->tiles, b->values, sd);
   }
   CUDA_TRY(cudaGetLastError());
-  if (b->pad_total) {
-    if (b->lp)
-      dev::set_ones_kernel<float><<<grid_for(b->pad_total, 128), 128, 0, st>>>(b->tiles32, b->pad, b->pad_total);
-    else
-      dev::set_ones_kernel<double><<<grid_for(b->pad_total, 128), 128, 0, st>>>(b->tiles, b->pad, b->pad_total);
-    CUDA_TRY(cudaGetLastError());
-  }
   CUDA_TRY(cudaMemsetAsync(b->flags, 0, size_t(b->flag_total) * sizeof(int), st));
   CUDA_TRY(cudaMemsetAsync(b->infos, 0xFF, b->plans.size() * sizeof(unsigned long long), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->ctl, 1);
@@ -1219,18 +1302,21 @@ stiles_status ensure_batch_solve(stiles_batch* b) {
   b->nfwd = int(tf.size());
   b->nbwd = int(tb.size());
   const size_t ctx_bytes = b->lp ? sizeof(dev::SolveCtx<float>) : sizeof(dev::SolveCtx<double>);
-  cudaError_t e = cudaMalloc(&b->sY, size_t(ytot) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->sScr, size_t(stot) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->sFlags, size_t(ftot) * sizeof(int));
+  cudaError_t e = batch_alloc(b, &b->sY, size_t(ytot));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->sScr, size_t(stot));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->sFlags, size_t(ftot));
   for (double** v : {&b->vb, &b->vx, &b->vr, &b->vd, &b->vy})
-    if (e == cudaSuccess) e = cudaMalloc(v, size_t(vtot) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->vnorms, size_t(count) * 2 * R * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->sctl, 2 * sizeof(dev::Ctl));
-  if (e == cudaSuccess) e = cudaMalloc(&b->dfwd, size_t(count) * ctx_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->dbwd, size_t(count) * ctx_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->ddesc, size_t(count) * sizeof(BSolveDesc));
-  if (e == cudaSuccess) e = upload(&b->tfwd, tf);
-  if (e == cudaSuccess) e = upload(&b->tbwd, tb);
+    if (e == cudaSuccess) e = batch_alloc(b, v, size_t(vtot));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->vnorms, size_t(count) * 2 * R);
+  if (e == cudaSuccess) e = batch_alloc(b, &b->sctl, 2);
+  if (e == cudaSuccess) e = batch_alloc(b, reinterpret_cast<unsigned char**>(&b->dfwd), size_t(count) * ctx_bytes);
+  if (e == cudaSuccess) e = batch_alloc(b, reinterpret_cast<unsigned char**>(&b->dbwd), size_t(count) * ctx_bytes);
+  if (e == cudaSuccess) e = batch_alloc(b, reinterpret_cast<BSolveDesc**>(&b->ddesc), size_t(count));
+  if (e == cudaSuccess) e = batch_upload(b, &b->tfwd, tf);
+  if (e == cudaSuccess) e = batch_upload(b, &b->tbwd, tb);
+  if (e == cudaSuccess) e = batch_alloc(b, &b->tcall_fwd, tf.size());
+  if (e == cudaSuccess) e = batch_alloc(b, &b->tcall_bwd, tb.size());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the arrays are used from the caller's streams
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
@@ -1289,6 +1375,9 @@ stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cuda
     d.y = b->vy + b->vec_off[i];
     d.colptr = p->dev->colptr;
     d.rowidx = p->dev->rowidx;
+    d.rptr = p->dev->rptr;
+    d.rcol = p->dev->rcol;
+    d.rval = p->dev->rval;
     d.values = v->values;
     d.norms = b->vnorms + size_t(i) * 2 * dev::SOLVE_MAXR;
   }
@@ -1300,22 +1389,32 @@ stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cuda
   return STILES_OK;
 }
 
+// Tickets of one batched solve call: every matrix, or only those with right-hand sides.
+struct SweepTickets {
+  const int2* fwd;
+  const int2* bwd;
+  int nfwd, nbwd;
+  int nmat;  // matrices taking part
+};
+
 template <int B, typename TF>
-cudaError_t launch_batch_sweeps(stiles_batch* b, cudaStream_t st) {
+cudaError_t launch_batch_sweeps(stiles_batch* b, const SweepTickets& tk, cudaStream_t st) {
   dev::SolveArgs<TF> a{};
   a.spin_limit = b->spin_limit;
   a.mats = static_cast<const dev::SolveCtx<TF>*>(b->dfwd);
-  a.tickets = b->tfwd;
-  a.ntasks = b->nfwd;
+  a.tickets = tk.fwd;
+  a.ntasks = tk.nfwd;
   a.ctl = b->sctl;
-  dev::solve_kernel<B, false, TF><<<b->solve_grid, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
+  const int gf = std::max(1, std::min({b->solve_grid, tk.nfwd, kSolveCtasPerMatrix * tk.nmat}));
+  const int gb = std::max(1, std::min({b->solve_grid, tk.nbwd, kSolveCtasPerMatrix * tk.nmat}));
+  dev::solve_kernel<B, false, TF><<<gf, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   a.mats = static_cast<const dev::SolveCtx<TF>*>(b->dbwd);
-  a.tickets = b->tbwd;
-  a.ntasks = b->nbwd;
+  a.tickets = tk.bwd;
+  a.ntasks = tk.nbwd;
   a.ctl = b->sctl + 1;
-  dev::solve_kernel<B, true, TF><<<b->solve_grid, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
+  dev::solve_kernel<B, true, TF><<<gb, 128, dev::SolveCfg<B, TF>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1327,7 +1426,8 @@ dim3 batch_grid(const stiles_batch* b, int64_t max_work) {
 }
 
 // One solve of every matrix: which = 0 solves b into x, which = 1 solves r into d.
-stiles_status batch_solve_pass(stiles_batch* b, cudaStream_t st, int which, int64_t max_rows) {
+stiles_status batch_solve_pass(stiles_batch* b, const SweepTickets& tk, cudaStream_t st, int which,
+                               int64_t max_rows) {
   const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
   const dim3 g = batch_grid(b, max_rows * dev::SOLVE_MAXR);
   if (b->lp) bpermute_in_kernel<float><<<g, 256, 0, st>>>(desc, which);
@@ -1337,11 +1437,11 @@ stiles_status batch_solve_pass(stiles_batch* b, cudaStream_t st, int which, int6
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->sctl, 2);
   CUDA_TRY(cudaGetLastError());
   cudaError_t e;
-  if (b->lp) e = launch_batch_sweeps<64, float>(b, st);
+  if (b->lp) e = launch_batch_sweeps<64, float>(b, tk, st);
   else switch (b->B) {
-    case 16: e = launch_batch_sweeps<16, double>(b, st); break;
-    case 32: e = launch_batch_sweeps<32, double>(b, st); break;
-    default: e = launch_batch_sweeps<64, double>(b, st); break;
+    case 16: e = launch_batch_sweeps<16, double>(b, tk, st); break;
+    case 32: e = launch_batch_sweeps<32, double>(b, tk, st); break;
+    default: e = launch_batch_sweeps<64, double>(b, tk, st); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("batched solve launch: ") + cudaGetErrorString(e));
   if (b->lp) bpermute_out_kernel<float><<<g, 256, 0, st>>>(desc, which);
@@ -1366,9 +1466,8 @@ stiles_status batch_residual(stiles_batch* b, cudaStream_t st, int64_t max_rows,
                              std::vector<double>* rel) {
   const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
   const int count = int(b->plans.size());
-  CUDA_TRY(cudaMemsetAsync(b->vy, 0, size_t(b->vec_total) * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(b->vnorms, 0, size_t(count) * 2 * dev::SOLVE_MAXR * sizeof(double), st));
-  bspmv_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(desc);
+  bspmv_kernel<<<batch_grid(b, max_rows * 32), 256, 0, st>>>(desc);
   CUDA_TRY(cudaGetLastError());
   dim3 g = batch_grid(b, max_rows);
   g.z = dev::SOLVE_MAXR;
@@ -1402,6 +1501,7 @@ extern "C" {
 stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count, stiles_batch** out) {
   if (!plans || count < 1 || !out) return fail(STILES_ERR_INVALID, "bad argument");
   *out = nullptr;
+  if (count > 65535) return fail(STILES_ERR_UNSUPPORTED, "a batch holds at most 65,535 matrices");
   stiles_batch* b = new (std::nothrow) stiles_batch();
   if (!b) return fail(STILES_ERR_NOMEM, "host allocation");
   auto bail = [&](stiles_status s) {
@@ -1439,35 +1539,36 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     b->diag_elems += p->nsb * b->B;
     b->flag_total += p->nsub + std::max<int64_t>(p->graph.nscratch, 1);
   }
-  std::vector<int64_t> hmap(b->nnz_total), hpad;
-  hpad.reserve(b->pad_total);
+  std::vector<BScatter> scat(count);
   for (int i = 0; i < count; ++i) {
     const stiles_plan* p = plans[i];
-    for (int64_t e = 0; e < p->nnz; ++e) hmap[b->val_off[i] + e] = p->scatter[e] + t_off[i];
-    for (int64_t q : p->pad) hpad.push_back(q + t_off[i]);
+    scat[i] = BScatter{p->dev->scatter, p->dev->pad, p->nnz, int64_t(p->pad.size()), b->val_off[i], t_off[i]};
+    b->max_scatter = std::max<int64_t>(b->max_scatter, std::max<int64_t>(p->nnz, int64_t(p->pad.size())));
   }
-  cudaError_t e = cudaMalloc(&b->values, size_t(b->nnz_total) * sizeof(double));
-  if (e == cudaSuccess) e = upload(&b->map, hmap);
-  if (e == cudaSuccess) e = upload(&b->pad, hpad);
-  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->tiles, size_t(b->tile_elems) * sizeof(double));
-  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->scratch, size_t(b->scratch_elems) * sizeof(double));
-  if (e == cudaSuccess && !b->lp) e = cudaMalloc(&b->invdiag, size_t(b->diag_elems) * sizeof(double));
-  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->tiles32, size_t(b->tile_elems) * sizeof(float));
-  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->tiles16, size_t(b->tile_elems) * sizeof(uint16_t));
-  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->scratch32, size_t(b->scratch_elems) * sizeof(float));
-  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->invdiag32, size_t(b->diag_elems) * sizeof(float));
-  if (e == cudaSuccess && b->lp) e = cudaMalloc(&b->ldiag, size_t(b->diag_elems) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->flags, size_t(b->flag_total) * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->infos, size_t(count) * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&b->ctl, sizeof(dev::Ctl));
-  if (e == cudaSuccess) e = cudaMalloc(&b->logdet_out, size_t(count) * sizeof(double));
+  keep_pool_memory(b->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = batch_alloc(b, &b->values, size_t(b->nnz_total));
+  if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BScatter**>(&b->dscatter), scat);
+  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->tiles, size_t(b->tile_elems));
+  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->scratch, size_t(b->scratch_elems));
+  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->invdiag, size_t(b->diag_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles16, size_t(b->tile_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->invdiag32, size_t(b->diag_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->ldiag, size_t(b->diag_elems));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->flags, size_t(b->flag_total));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->infos, size_t(count));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->ctl, 1);
+  if (e == cudaSuccess) e = batch_alloc(b, &b->logdet_out, size_t(count));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->vctl, size_t(count) * 3);
+  if (e == cudaSuccess) e = batch_alloc(b, &b->vlog, size_t(count) * (dev::LOGDET_BLOCKS + 1));
+  if (e == cudaSuccess) e = batch_alloc(b, &b->vnorm, size_t(count) * 2 * dev::SOLVE_MAXR);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
                      std::string("batch allocation: ") + cudaGetErrorString(e)));
   }
-  hmap.clear();
-  hmap.shrink_to_fit();
   // factor views and per-matrix contexts
   std::vector<dev::MatCtx> mats;
   std::vector<dev::LPMatCtx> lmats;
@@ -1495,25 +1596,25 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       v->scratch = b->scratch + s_off[i];
       v->invdiag = b->invdiag + d_off[i];
     }
-    CUDA_TRY(cudaMalloc(&v->ctl, 3 * sizeof(dev::Ctl)));
-    CUDA_TRY(cudaMalloc(&v->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double)));
-    CUDA_TRY(cudaMalloc(&v->norms, 2 * dev::SOLVE_MAXR * sizeof(double)));
-    CUDA_TRY(cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming));
-    for (int k = 0; k < 3; ++k) CUDA_TRY(cudaEventCreate(&v->ev[k]));
+    // the view's small arrays are slices of batch-wide ones; a view never
+    // factorizes, so it has no events
+    v->ctl = b->vctl + 3 * size_t(i);
+    v->logdet_part = b->vlog + size_t(i) * (dev::LOGDET_BLOCKS + 1);
+    v->norms = b->vnorm + size_t(i) * 2 * dev::SOLVE_MAXR;
     if (b->lp) lmats.push_back(lp_mat_ctx(p, v));
     else mats.push_back(mat_ctx(p, v));
     logs[i] = BatchLogCtx{v->tiles, p->dev->diag_sub, v->ldiag, p->n, b->B, 0};
   }
-  if (b->lp) e = upload(reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
-  else e = upload(reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
-  if (e == cudaSuccess) e = upload(reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
+  if (b->lp) e = batch_upload(b, reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
+  else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
+  if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   std::vector<int64_t> lens(count);
   for (int i = 0; i < count; ++i) lens[i] = int64_t(plans[i]->graph.tasks.size());
   std::vector<int2> tick = merge_tickets(lens);
   if (tick.size() >= size_t(1) << 31) return bail(fail(STILES_ERR_UNSUPPORTED, "too many tasks in one batch"));
   b->ntickets = int(tick.size());
-  e = upload(&b->dtickets, tick);
+  e = batch_upload(b, &b->dtickets, tick);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   // persistent grid: as many resident CTAs as fit
   int sms = 0;
@@ -1532,7 +1633,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (plans[0]->opts.ctas_per_sm > 0) per_sm = std::min(per_sm, int(plans[0]->opts.ctas_per_sm));
   b->grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(std::max(per_sm, 1)) * sms, b->ntickets)));
   // private stream + graph of the per-call work
-  CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));  // pool arrays in place before other streams use them
   CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreate(&b->ev_k0));
@@ -1568,7 +1669,7 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(b->pad_total ? 4 : 3);
+  count_launch(3);  // scatter, init, persistent kernel
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));
@@ -1624,6 +1725,26 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
   stiles_status s = ensure_batch_solve(b);
   if (s != STILES_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // tickets: the batch's full lists, or merged lists of the matrices that take part
+  const int nact = int(count - std::count(nr.begin(), nr.end(), 0));
+  SweepTickets tk{b->tfwd, b->tbwd, b->nfwd, b->nbwd, nact};
+  if (std::count(nr.begin(), nr.end(), 0) > 0) {
+    std::vector<int64_t> lf(count, 0), lb(count, 0);
+    for (int i = 0; i < count; ++i)
+      if (nr[i]) {
+        lf[i] = int64_t(b->plans[i]->fwd.tasks.size());
+        lb[i] = int64_t(b->plans[i]->bwd.tasks.size());
+      }
+    std::vector<int2> tf = merge_tickets(lf), tb = merge_tickets(lb);
+    if (tf.empty()) {  // nothing to solve
+      if (relres) std::fill(relres, relres + count, 0.0);
+      if (iters) std::fill(iters, iters + count, 0);
+      return STILES_OK;
+    }
+    CUDA_TRY(cudaMemcpy(b->tcall_fwd, tf.data(), tf.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b->tcall_bwd, tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    tk = SweepTickets{b->tcall_fwd, b->tcall_bwd, int(tf.size()), int(tb.size()), nact};
+  }
   if (b->lp) s = upload_solve_ctx<float>(b, nr, st);
   else s = upload_solve_ctx<double>(b, nr, st);
   if (s != STILES_OK) return s;
@@ -1631,7 +1752,7 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
     if (nr[i])
       CUDA_TRY(cudaMemcpyAsync(b->vb + b->vec_off[i], rhs[i], size_t(b->plans[i]->n) * nr[i] * sizeof(double),
                                cudaMemcpyDefault, st));
-  s = batch_solve_pass(b, st, 0, max_rows);
+  s = batch_solve_pass(b, tk, st, 0, max_rows);
   if (s != STILES_OK) return s;
   std::vector<double> rel;
   std::vector<int> it(count, 0);
@@ -1655,7 +1776,7 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
         s = fail(STILES_ERR_CUDA, "batched refinement upload");
         break;
       }
-      s = batch_solve_pass(b, st, 1, max_rows);
+      s = batch_solve_pass(b, tk, st, 1, max_rows);
       if (s != STILES_OK) break;
       baxpy_active_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(
           static_cast<const BSolveDesc*>(b->ddesc), dactive);

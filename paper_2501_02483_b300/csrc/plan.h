@@ -77,6 +77,9 @@ struct stiles_plan {
   int32_t ordering_used = 0;
   std::vector<int64_t> colptr;   // copy of the input pattern (for the residual SpMV)
   std::vector<int32_t> rowidx;
+  std::vector<int64_t> rptr;     // CSR index of its strict lower part: row i holds columns j < i
+  std::vector<int32_t> rcol;
+  std::vector<int64_t> rval;     //   and the CSC position of each entry
   std::vector<int64_t> perm;     // perm[new] = old
   std::vector<int64_t> iperm;    // iperm[old] = new
   // T-level tile map (tile-CSC, diagonal first)

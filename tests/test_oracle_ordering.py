@@ -160,3 +160,32 @@ def test_adaptable_nd_no_crossing_entries():
     # two disconnected blocks: nothing crosses mid, separator empty
     n, colptr, rowidx = _graph_matrix(8, [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 7)])
     assert ordering.adaptable_nd(n, colptr, rowidx, 0).tolist() == [0, 1, 2, 3, 7, 6, 5, 4]
+
+
+def test_adaptable_nd_split_is_tile_aligned():
+    # path 0..9 with tiles of 4: mid = 5 rounds down to 4, separator {4}
+    n, colptr, rowidx = _graph_matrix(10, [(i, i + 1) for i in range(9)], n_arrow=2)
+    assert ordering.adaptable_nd(n, colptr, rowidx, 2, align=4).tolist() == [0, 1, 2, 3, 9, 8, 7, 6, 5, 4, 10, 11]
+    # a tile wider than half the body leaves the order unchanged
+    assert ordering.adaptable_nd(n, colptr, rowidx, 2, align=8).tolist() == list(range(12))
+
+
+def _tile_etree_leaves(m, perm, T):
+    from oracle import tiles
+    nt, present = tiles.tile_map(m["n"], m["colptr"], m["rowidx"], perm, T)
+    tcp, tri = tiles.tile_csc(nt, tiles.symbolic_closure(nt, present))
+    parent = [int(tri[tcp[k] + 1]) if tcp[k + 1] - tcp[k] > 1 else -1 for k in range(nt)]
+    has_child = set(p for p in parent if p >= 0)
+    return [k for k in range(nt) if k not in has_child]
+
+
+def test_adaptable_nd_gives_two_tile_chains_only_when_aligned():
+    # body of 1001 rows (mid = 500, not a multiple of 16): aligned at 16 the
+    # tile elimination tree has two leaves (two independent chains); the
+    # unaligned split puts rows of both parts into one tile and leaves one chain
+    m = inputs.band_arrow(1001, 5, 20, 1.0, 1)
+    T = 16
+    aligned = ordering.adaptable_nd(m["n"], m["colptr"], m["rowidx"], 5, align=T)
+    unaligned = ordering.adaptable_nd(m["n"], m["colptr"], m["rowidx"], 5, align=1)
+    assert len(_tile_etree_leaves(m, aligned, T)) == 2
+    assert len(_tile_etree_leaves(m, unaligned, T)) == 1
