@@ -58,8 +58,8 @@ METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set res
 # DRAM bytes per launch of the factorization kernel, from an ncu capture (see
 # profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
 # changed after the capture.
-TRAFFIC = {("factor_f64_v2", 16, 16): 1.285e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
-KERNEL_TAG = "factor_f64_v4"
+TRAFFIC = {("factor_f64_v5", 16, 16): 1.302e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
+KERNEL_TAG = "factor_f64_v5"
 
 
 def parse():
@@ -462,8 +462,8 @@ def run_sweep(args):
                    "step": "batched factorize (one persistent launch) + all logdets + batched solve with FP64 "
                            "refinement (analysis once per pattern, timed separately)",
                    "l2": "inputs larger than L2 (factor tiles of the batch > 1 GB); no flush",
-                   "mixed_precision": lp, "fp64": f64, "logdet_rel_diff_bf16_vs_fp64": ld_err,
-                   "solves_per_s_bf16_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
+                   "mixed_precision": lp, "fp64": f64, "logdet_rel_diff_lp_vs_fp64": ld_err,
+                   "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "factor_lp_kernel (batched)",
                      "kernel_ms": lp["kernel_ms"], "peak_source": peak_src},
@@ -568,7 +568,7 @@ def run_serve(args):
                                "buffers in pinned host memory; ordering " + args.serve_ordering,
                    "step": "the whole request stream through the continuous-batching loop (arrivals in real time)",
                    "mixed_precision": lp, "fp64": f64,
-                   "solves_per_s_bf16_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
+                   "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
         "e2e": {"value": -value * world, "unit": "solves/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None,
                 "note": "requests enter as host arrays; every value and right-hand side crosses H2D"},
