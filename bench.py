@@ -58,7 +58,7 @@ METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set res
 # DRAM bytes per launch of the factorization kernel, from an ncu capture (see
 # profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
 # changed after the capture.
-TRAFFIC = {("factor_f64_v5", 16, 16): 1.302e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
+TRAFFIC = {("factor_f64_v5", "large", 16, 16): 1.302e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
 KERNEL_TAG = "factor_f64_v5"
 
 
@@ -73,10 +73,13 @@ def parse():
     ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="nd")
     ap.add_argument("--sweep", default="32,64,128,256,512", help="tile sizes timed briefly; '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-largest", action="store_true", help="large: skip the largest-configuration FP64 line")
     ap.add_argument("--cpu-sample-rows", type=int, default=60_000)
     ap.add_argument("--rows", type=int, default=200_000,
                     help="body rows (profiling runs only; the benchmarked workload is 200,000)")
-    ap.add_argument("--workload", choices=["large", "sweep", "serve"], default="large")
+    ap.add_argument("--workload", choices=["large", "spatiotemporal", "sweep", "serve"], default="large")
+    ap.add_argument("--precision", choices=["f64", "bf16", "f16"], default="f64",
+                    help="large/spatiotemporal: update precision (bf16/f16 need tile 64; FP64 refinement)")
     ap.add_argument("--batch", type=int, default=256, help="sweep: matrices per batch")
     ap.add_argument("--lp-tile", type=int, default=64, help="sweep/serve: tile of the mixed-precision arm")
     ap.add_argument("--lp-precision", choices=["bf16", "f16"], default="f16",
@@ -92,16 +95,25 @@ def parse():
 
 
 def workload(args, seed=0):
+    if args.workload == "spatiotemporal":
+        return inputs.config_spatiotemporal(seed)
     return inputs.config_large(seed, n_body=args.rows)
 
 
 def workload_config(args, info=None):
-    cfg = {"workload": f"band{args.rows}_hw100-500_d0.2_arrow100_nrhs4 (large single matrix, FP64)",
-           "n": args.rows + 100, "n_arrow": 100, "nrhs": 4, "tile": args.tile, "ordering": args.ordering,
-           "l2": "inputs larger than L2 (values 0.26 GB, factor tiles > 0.7 GB vs 126 MB L2); no flush",
-           "step": "factorize + logdet + 4-RHS solve (analysis once per pattern, timed separately)",
+    if args.workload == "spatiotemporal":
+        cfg = {"workload": "spatio-temporal Q_t (x) Q_s: AR(1) n_t=100 rho=0.9, (kappa^2 I + L)^2 on a 45x45 grid "
+                           f"(kappa^2=1), time-major, + 20 fixed-effect arrow rows, nrhs 1 ({args.precision})",
+               "n": 202520, "n_arrow": 20, "nrhs": 1, "tile": args.tile, "ordering": args.ordering,
+               "l2": "inputs larger than L2 (factor tiles > 1 GB vs 126 MB L2); no flush"}
+    else:
+        cfg = {"workload": f"band{args.rows}_hw100-500_d0.2_arrow100_nrhs4 (large single matrix, {args.precision})",
+               "n": args.rows + 100, "n_arrow": 100, "nrhs": 4, "tile": args.tile, "ordering": args.ordering,
+               "l2": "inputs larger than L2 (values 0.26 GB, factor tiles > 0.7 GB vs 126 MB L2); no flush"}
+    cfg.update({
+           "step": "factorize + logdet + solve (analysis once per pattern, timed separately)",
            "flops": "tile-level task flops of Algorithm 1 at tile T (POTRF b(b+1)(2b+1)/6, SYRK kb(b+1), "
-                    "GEMM 2mnk, TRSM mb^2)"}
+                    "GEMM 2mnk, TRSM mb^2)"})
     if info:
         cfg.update({"block": info["block"], "nnzt": info["nnzt"], "ntasks": info["ntasks"],
                     "flops_factor": info["flops_total"]})
@@ -161,7 +173,13 @@ def cpu_baseline(args, T):
     from oracle import tiles as otiles
 
     rows = args.cpu_sample_rows
-    m = inputs.config_large(0, n_body=rows, n_arrow=100, nrhs=4)
+    if args.workload == "spatiotemporal":
+        # 4 time steps of the same Kronecker structure (8,120 rows), tile 64
+        m = inputs.kronecker_spatiotemporal(4, 0.9, 45, 1.0, 20, 0.1, 0, nrhs=1)
+        T = 64
+        rows = m["n"]
+    else:
+        m = inputs.config_large(0, n_body=rows, n_arrow=100, nrhs=4)
     p = oan.analyze(m, T, oan.ORDER_NONE)
     fl = otiles.task_flops(m["n"], T, p["tcolptr"], p["trowidx"])["total"]
     t0 = time.perf_counter()
@@ -169,10 +187,11 @@ def cpu_baseline(args, T):
     och.logdet(L, p["nt"])
     och.solve(L, p["perm"], T, p["tcolptr"], p["trowidx"], m["rhs"])
     dt = time.perf_counter() - t0
+    what = (f"the same generator with {rows} body rows + 100-row arrow" if args.workload != "spatiotemporal"
+            else f"the same Kronecker structure with 4 time steps ({rows} rows)")
     return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"the same generator with {rows} body rows + 100-row arrow, T={T}, one "
-                      f"factorize+logdet+4-RHS solve ({dt:.1f} s, one thread: Python/numpy, BLAS pinned to 1 "
-                      f"thread)", "seconds": dt, "flops": fl}
+            "sample": f"{what}, T={T}, one factorize+logdet+solve ({dt:.1f} s, one thread: Python/numpy, BLAS "
+                      f"pinned to 1 thread)", "seconds": dt, "flops": fl}
 
 
 def run_reference(args):
@@ -218,8 +237,9 @@ def run_ours(args):
     order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[args.ordering]
 
     m = workload(args, seed=rank)
+    prec = {"f64": st.PREC_F64, "bf16": st.PREC_BF16, "f16": st.PREC_F16}[args.precision]
     t0 = time.perf_counter()
-    plan = st.Plan.from_matrix(m, tile=args.tile, block=args.block, ordering=order)
+    plan = st.Plan.from_matrix(m, tile=args.tile, block=args.block, ordering=order, precision=prec)
     analyze_s = time.perf_counter() - t0
     info = plan.info()
     flops = info["flops_total"]
@@ -299,7 +319,9 @@ def run_ours(args):
     sweep = {}
     if rank == 0 and args.sweep:
         for T in [int(t) for t in args.sweep.split(",") if t]:
-            pl = st.Plan.from_matrix(m, tile=T, ordering=order)
+            if prec != st.PREC_F64 and T % 64:
+                continue
+            pl = st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec)
             ff = st.Factor(pl)
             ff.factorize(vals_d)
             ks = []
@@ -314,26 +336,34 @@ def run_ours(args):
 
     kms = statistics.mean(kernel_ms)
     achieved = flops / (kms * 1e-3) / 1e12
-    traffic = TRAFFIC.get((KERNEL_TAG, args.tile, info["block"]))
+    if prec == st.PREC_F64:
+        traffic = TRAFFIC.get((KERNEL_TAG, args.workload, args.tile, info["block"]))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": f"factor_f64_kernel<{info['block']}>", "kernel_ms": kms,
+                "peak_source": "FP64 DFMA probe of libstiles.so measured in this run (MEASURED_PEAKS.json "
+                               "has no FP64 entry)"}
+    else:
+        tpeak, src = _tensor_peak()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s", "frac": achieved / tpeak,
+                "traffic": None, "kernel": "factor_lp_kernel", "kernel_ms": kms, "peak_source": src}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": dict(workload_config(args, info), analyze_s=round(analyze_s, 3), logdet=ld,
-                       relres=relres, tile_sweep=sweep, percent_of_fp64_peak=round(100 * value / peak, 2)),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": f"factor_f64_kernel<{info['block']}>",
-                     "kernel_ms": kms,
-                     "peak_source": "FP64 DFMA probe of libstiles.so measured in this run (MEASURED_PEAKS.json "
-                                    "has no FP64 entry)"},
+                       relres=relres, tile_sweep=sweep, percent_of_fp64_peak=round(100 * value / peak, 2),
+                       refine_iters=f.refine_iters()),
+        "roofline": roof,
         "e2e": e2e, "gpu_launches": launches, "clocks": clk.result,
     }
+    f.close()
+    plan.close()
+    if rank == 0 and args.workload == "large" and not args.no_largest:
+        line["config"]["largest_config_fp64"] = _largest_config_fp64(st, torch, dev, stream, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args, args.tile).items() if k not in ("seconds", "flops")}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    f.close()
-    plan.close()
     if dist:
         dist.destroy_process_group()
 
@@ -341,6 +371,41 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched sweep and serving workloads
 # ---------------------------------------------------------------------------
+def _largest_config_fp64(st, torch, dev, stream, peak):
+    """FP64 factorization of the largest configuration (the spatio-temporal
+    matrix, n = 202,520, tile 16, nested dissection): kernel time of 2 timed
+    factorizations after one warm-up, as a fraction of the measured FP64 peak."""
+    m = inputs.config_spatiotemporal(0)
+    pl = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_ND)
+    ff = st.Factor(pl)
+    vd = torch.from_numpy(m["values"]).to(dev)
+    ff.factorize(vd, stream=stream)
+    ks = []
+    for _ in range(2):
+        ff.factorize(vd, stream=stream)
+        ks.append(ff.timing()[1])
+    fl = pl.info()["flops_total"]
+    ms = statistics.mean(ks)
+    out = {"workload": "spatio-temporal Q_t (x) Q_s + 20 arrow rows, n = 202,520, T = 16, ND",
+           "factor_kernel_ms": round(ms, 2), "flops": fl, "tflops": round(fl / ms / 1e9, 4),
+           "frac_of_fp64_peak": round(fl / ms / 1e9 / peak, 4)}
+    ff.close()
+    pl.close()
+    return out
+
+
+def _tensor_peak():
+    """The sustained bf16 tensor peak of MEASURED_PEAKS.json (f16 runs at the same rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = json.load(fh).get("bf16_tflops_sustained")
+        if v:
+            return float(v), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; f16 has the same nominal rate)"
+    except OSError:
+        pass
+    return 1400.0, "fallback sustained bf16 (of fallback)"
+
+
 def _setup_rank():
     import torch
 
@@ -443,15 +508,7 @@ def run_sweep(args):
     ld_err = float(np.max(np.abs(lp["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
     for a in (lp, f64):
         a.pop("logdets")
-    peak = None
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peak = json.load(fh).get("bf16_tflops_sustained")
-    except OSError:
-        pass
-    peak_src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-    if peak is None:
-        peak, peak_src = 1400.0, "fallback sustained bf16 (of fallback)"
+    peak, peak_src = _tensor_peak()
     achieved = lp["flops"] / (lp["kernel_ms"] * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": world * lp["tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
