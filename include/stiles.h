@@ -144,6 +144,9 @@ stiles_status stiles_logdet(const stiles_factor* factor, double* out);
  * For a BF16/FP16 factor the solve refines in FP64: x <- x + solve(b - A x) with the residual
  * from the original FP64 values, until ||b - A x||_2 / ||b||_2 <= opts.refine_tol for every
  * column or opts.max_refine steps (then STILES_ERR_NOT_CONVERGED, x holding the last iterate).
+ * A refinement step that does not halve the residual (the factor too inaccurate for refinement
+ * to converge) hands the rest of the max_refine budget to conjugate gradients on A x = b
+ * preconditioned by the same factor (FP64 residuals, dot products and updates).
  *   b, x  : n x nrhs, column-major with leading dimension ld >= n, host or device (both
  *           on the same side); x may equal b.
  *   final_relres : may be NULL; else receives max over columns of ||b - A x||_2 / ||b||_2,
@@ -156,6 +159,10 @@ stiles_status stiles_solve(const stiles_factor* factor, const double* b, double*
  * chunks): 0 for FP64 factors; for BF16/FP16 factors the number of x <- x + solve(b - A x)
  * corrections after the first solve.  -1 for a NULL factor. */
 int32_t stiles_factor_refine_iters(const stiles_factor* factor);
+
+/* Of those steps, how many were preconditioned conjugate-gradient iterations (0 unless the
+ * refinement stalled).  -1 for a NULL factor. */
+int32_t stiles_factor_cg_iters(const stiles_factor* factor);
 
 /* Copy the factor out as T x T column-major tiles in tile-CSC order (nnzt * T * T doubles),
  * host or device.  Rows/columns past n are padding (identity on the diagonal). */

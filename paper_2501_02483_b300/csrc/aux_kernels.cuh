@@ -257,6 +257,43 @@ __global__ void residual_norms_kernel(const double* __restrict__ y, const double
   }
 }
 
+// out[c] += sum_i a(i, c) b(i, c) for c < nr (grid.y = column; out zeroed beforehand)
+__global__ void dot_cols_kernel(const double* __restrict__ a, int64_t lda, const double* __restrict__ b, int64_t ldb,
+                                int64_t n, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.y;
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    s = fma(a[i + c * lda], b[i + c * ldb], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out + c, red[0]);
+}
+
+// Conjugate-gradient update of nr columns: x += alpha_c p, r -= alpha_c q
+__global__ void cg_update_kernel(double* __restrict__ x, int64_t ldx, double* __restrict__ r,
+                                 const double* __restrict__ p, const double* __restrict__ q,
+                                 const double* __restrict__ alpha, int64_t n, int nr) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * nr; e += stride) {
+    const int64_t c = e / n, i = e % n;
+    x[i + c * ldx] = fma(alpha[c], p[e], x[i + c * ldx]);
+    r[e] = fma(-alpha[c], q[e], r[e]);
+  }
+}
+
+// p = z + beta_c p (nr columns of length n)
+__global__ void cg_direction_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                    const double* __restrict__ beta, int64_t n, int nr) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * nr; e += stride)
+    p[e] = fma(beta[e / n], p[e], z[e]);
+}
+
 // Export T x T column-major tiles from the sub-tile layout (R = T / B).
 template <typename TF>
 __global__ void export_tiles_kernel(double* __restrict__ out, const TF* __restrict__ tiles, int64_t nnzt, int T, int B) {

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -105,8 +106,10 @@ struct stiles_factor {
   float* scratch32 = nullptr;
   float* invdiag32 = nullptr;
   double* ldiag = nullptr;
-  double* irwork = nullptr;   // refinement: correction and residual, 2 * n * SOLVE_MAXR
+  double* irwork = nullptr;   // refinement: correction, residual, CG direction and A p, 4 * n * SOLVE_MAXR
+  double* cgs = nullptr;      // CG scalars: dot products and step lengths, 2 * SOLVE_MAXR
   int last_refine_iters = 0;
+  int last_cg_iters = 0;      // of those, conjugate-gradient iterations (refinement stalled)
   int* flags = nullptr;       // nsub + nscratch
   stiles::dev::Ctl* ctl = nullptr;  // [0] factor, [1] forward, [2] backward
   double* logdet_part = nullptr;    // LOGDET_BLOCKS + 1
@@ -270,6 +273,7 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->invdiag32);
   cudaFree(f->ldiag);
   cudaFree(f->irwork);
+  cudaFree(f->cgs);
   cudaFree(f->flags);
   cudaFree(f->ctl);
   cudaFree(f->logdet_part);
@@ -707,6 +711,78 @@ stiles_status residual_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_
   return STILES_OK;
 }
 
+// Conjugate gradients on A x = b preconditioned by the mixed-precision factor
+// (z = (L L^T)^{-1} r through the factor's sweeps), started from the current x
+// of columns [r0, r0 + nr) and its residual r = b - A x (held in the second
+// quarter of irwork); per-column step lengths in FP64.  Used when iterative
+// refinement stalls.  Stops when the recomputed true residual meets refine_tol
+// or after `budget` iterations; *worst = the largest ||b - A x|| / ||b||.
+stiles_status pcg_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t st, double* dx, int64_t dld,
+                        const double* db, int64_t bld, int r0, int nr, int budget, int* used, double* worst) {
+  constexpr int R = dev::SOLVE_MAXR;
+  const int64_t n = p->n;
+  double* z = f->irwork;                   // preconditioned residual
+  double* r = f->irwork + size_t(n) * R;   // residual
+  double* pv = r + size_t(n) * R;          // search direction
+  double* q = pv + size_t(n) * R;          // A p
+  double* xc = dx + r0 * dld;
+  const double* bc = db + r0 * bld;
+  auto dots = [&](const double* a, int64_t lda, const double* c, int64_t ldc, double* h) -> stiles_status {
+    CUDA_TRY(cudaMemsetAsync(f->cgs, 0, nr * sizeof(double), st));
+    dev::dot_cols_kernel<<<dim3(64, nr), 256, 0, st>>>(a, lda, c, ldc, n, f->cgs);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    CUDA_TRY(cudaMemcpyAsync(h, f->cgs, nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return STILES_OK;
+  };
+  auto set_coef = [&](const double* h) -> stiles_status {
+    CUDA_TRY(cudaMemcpyAsync(f->cgs + R, h, nr * sizeof(double), cudaMemcpyHostToDevice, st));
+    return STILES_OK;
+  };
+  double bb[R], rz[R], tmp[R], coef[R];
+  stiles_status s = dots(bc, bld, bc, bld, bb);
+  if (s != STILES_OK) return s;
+  s = solve_chunk(p, f, st, r, n, z, n, 0, nr);
+  if (s != STILES_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(pv, z, size_t(n) * nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if ((s = dots(r, n, z, n, rz)) != STILES_OK) return s;
+  *worst = std::numeric_limits<double>::infinity();
+  for (int k = 0; k < budget; ++k) {
+    dev::symv_kernel<<<grid_for(n * 32, 256), 256, 0, st>>>(q, pv, p->dev->colptr, p->dev->rowidx, p->dev->rptr,
+                                                           p->dev->rcol, p->dev->rval, f->values, n, n, nr);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    if ((s = dots(pv, n, q, n, tmp)) != STILES_OK) return s;
+    for (int c = 0; c < nr; ++c) coef[c] = tmp[c] > 0 ? rz[c] / tmp[c] : 0.0;
+    if ((s = set_coef(coef)) != STILES_OK) return s;
+    dev::cg_update_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(xc, dld, r, pv, q, f->cgs + R, n, nr);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+    ++*used;
+    if ((s = dots(r, n, r, n, tmp)) != STILES_OK) return s;
+    double w = 0.0;
+    for (int c = 0; c < nr; ++c) w = std::max(w, bb[c] > 0 ? std::sqrt(tmp[c] / bb[c]) : std::sqrt(tmp[c]));
+    if (!(w > p->opts.refine_tol)) {
+      // the recursive residual says done: confirm with the true one (and continue from it if not)
+      if ((s = residual_chunk(p, f, st, dx, dld, db, bld, r0, nr, r, worst)) != STILES_OK) return s;
+      if (!(*worst > p->opts.refine_tol)) return STILES_OK;
+    }
+    *worst = w;
+    if ((s = solve_chunk(p, f, st, r, n, z, n, 0, nr)) != STILES_OK) return s;
+    if ((s = dots(r, n, z, n, tmp)) != STILES_OK) return s;
+    for (int c = 0; c < nr; ++c) {
+      coef[c] = rz[c] > 0 ? tmp[c] / rz[c] : 0.0;
+      rz[c] = tmp[c];
+    }
+    if ((s = set_coef(coef)) != STILES_OK) return s;
+    dev::cg_direction_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(pv, z, f->cgs + R, n, nr);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  return residual_chunk(p, f, st, dx, dld, db, bld, r0, nr, r, worst);
+}
+
 }  // namespace
 
 extern "C" {
@@ -736,10 +812,30 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
     CUDA_TRY(cudaMalloc(&f->ywork, size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
     f->solve_nr = dev::SOLVE_MAXR;
   }
-  if (f->lp && !f->irwork) CUDA_TRY(cudaMalloc(&f->irwork, 2 * size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
+  if (f->lp && !f->irwork) {
+    CUDA_TRY(cudaMalloc(&f->irwork, 4 * size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&f->cgs, 2 * dev::SOLVE_MAXR * sizeof(double)));
+  }
   const double* db = b;
   double* dx = x;
-  int64_t dld = ld;
+  int64_t bld = ld, xld = ld;  // leading dimensions of the device-side b and x
+  if (bdev && b == x && (f->lp || final_relres)) {
+    // in place on the device: keep b for the residuals
+    const int64_t need = n * nrhs;
+    if (f->stage_elems < need) {
+      cudaFree(f->bstage);
+      cudaFree(f->xstage);
+      f->bstage = f->xstage = nullptr;
+      f->stage_elems = 0;
+      CUDA_TRY(cudaMalloc(&f->bstage, size_t(need) * sizeof(double)));
+      CUDA_TRY(cudaMalloc(&f->xstage, size_t(need) * sizeof(double)));
+      f->stage_elems = need;
+    }
+    CUDA_TRY(cudaMemcpy2DAsync(f->bstage, n * sizeof(double), b, ld * sizeof(double), n * sizeof(double), nrhs,
+                               cudaMemcpyDeviceToDevice, st));
+    db = f->bstage;
+    bld = n;
+  }
   if (!bdev) {
     const int64_t need = n * nrhs;
     if (f->stage_elems < need) {
@@ -755,42 +851,64 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
                                cudaMemcpyHostToDevice, st));
     db = f->bstage;
     dx = f->xstage;
-    dld = n;
+    bld = xld = n;
   }
   double worst = 0.0;
   bool converged = true;
   f->last_refine_iters = 0;
+  f->last_cg_iters = 0;
   for (int64_t r0 = 0; r0 < nrhs; r0 += dev::SOLVE_MAXR) {
     const int nr = int(std::min<int64_t>(dev::SOLVE_MAXR, nrhs - r0));
     if (!f->lp) {
-      stiles_status s1 = solve_chunk(p, f, st, db, dld, dx, dld, int(r0), nr);
+      stiles_status s1 = solve_chunk(p, f, st, db, bld, dx, xld, int(r0), nr);
       if (s1 != STILES_OK) return s1;
       if (final_relres) {
         double w = 0.0;
-        s1 = residual_chunk(p, f, st, dx, dld, db, dld, int(r0), nr, nullptr, &w);
+        s1 = residual_chunk(p, f, st, dx, xld, db, bld, int(r0), nr, nullptr, &w);
         if (s1 != STILES_OK) return s1;
         worst = std::max(worst, w);
       }
       continue;
     }
     // Mixed-precision factor: iterative refinement with FP64 residuals,
-    // x <- x + solve(b - A x), until ||b - A x|| / ||b|| <= refine_tol.
+    // x <- x + solve(b - A x), until ||b - A x|| / ||b|| <= refine_tol.  A step
+    // that does not at least halve the residual (or a NaN) means the factor is
+    // too inaccurate for refinement to converge: the remaining budget goes to
+    // conjugate gradients preconditioned by the same factor.
     double* dwork = f->irwork;                  // correction, n x nr
     double* rwork = f->irwork + size_t(n) * dev::SOLVE_MAXR;  // residual, n x nr
-    stiles_status s1 = solve_chunk(p, f, st, db, dld, dx, dld, int(r0), nr);
+    stiles_status s1 = solve_chunk(p, f, st, db, bld, dx, xld, int(r0), nr);
     if (s1 != STILES_OK) return s1;
-    double w = 0.0;
+    double w = 0.0, wprev = std::numeric_limits<double>::infinity();
     int it = 0;
+    bool stalled = false;
     for (;;) {
-      s1 = residual_chunk(p, f, st, dx, dld, db, dld, int(r0), nr, rwork, &w);
+      s1 = residual_chunk(p, f, st, dx, xld, db, bld, int(r0), nr, rwork, &w);
       if (s1 != STILES_OK) return s1;
       if (!(w > p->opts.refine_tol) || it >= p->opts.max_refine) break;
+      if (!(w <= 0.5 * wprev)) {
+        stalled = true;
+        break;
+      }
+      wprev = w;
       s1 = solve_chunk(p, f, st, rwork, n, dwork, n, 0, nr);
       if (s1 != STILES_OK) return s1;
-      dev::axpy_cols_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(dx + r0 * dld, dwork, n, dld, nr);
+      dev::axpy_cols_kernel<<<grid_for(n * nr, 256), 256, 0, st>>>(dx + r0 * xld, dwork, n, xld, nr);
       CUDA_TRY(cudaGetLastError());
       count_launch();
       ++it;
+    }
+    if (stalled) {
+      if (w != w) {  // the iterate is lost: restart from x = 0 (r = b)
+        CUDA_TRY(cudaMemset2DAsync(dx + r0 * xld, xld * sizeof(double), 0, n * sizeof(double), nr, st));
+        s1 = residual_chunk(p, f, st, dx, xld, db, bld, int(r0), nr, rwork, &w);
+        if (s1 != STILES_OK) return s1;
+      }
+      int used = 0;
+      s1 = pcg_chunk(p, f, st, dx, xld, db, bld, int(r0), nr, std::max(0, p->opts.max_refine - it), &used, &w);
+      if (s1 != STILES_OK) return s1;
+      it += used;
+      f->last_cg_iters = std::max(f->last_cg_iters, used);
     }
     f->last_refine_iters = std::max(f->last_refine_iters, it);
     if (w > p->opts.refine_tol || w != w) converged = false;
@@ -807,6 +925,8 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
 }
 
 int32_t stiles_factor_refine_iters(const stiles_factor* f) { return f ? f->last_refine_iters : -1; }
+
+int32_t stiles_factor_cg_iters(const stiles_factor* f) { return f ? f->last_cg_iters : -1; }
 
 stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* stream) {
   if (!cf || !out) return fail(STILES_ERR_INVALID, "null argument");

@@ -41,6 +41,7 @@ __all__ = [
     "serving_workload",
     "scaled",
     "dense_from_csc",
+    "near_singular_arrowhead",
 ]
 
 
@@ -296,6 +297,27 @@ def scaled(m, theta):
     out["values"] = m["values"] * theta
     out["name"] = f"{m['name']}_x{theta:g}"
     return out
+
+
+def near_singular_arrowhead(n_body, n_arrow, eps_rel, seed=0):
+    """Diagonal body d ~ U(1, 2), dense arrow B ~ N(0, 1), and an arrow block
+    D = B^T diag(d)^{-1} B + eps_rel ||B^T diag(d)^{-1} B||_2 I, so the Schur
+    complement of the body is eps_rel times its norm times the identity: an SPD
+    matrix whose conditioning is set by eps_rel (a low-precision factor of it
+    is a poor approximation when eps_rel is near the 16-bit rounding level)."""
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(1.0, 2.0, n_body)
+    B = rng.standard_normal((n_body, n_arrow))
+    S = B.T @ (B / d[:, None])
+    D = S + eps_rel * np.linalg.norm(S, 2) * np.eye(n_arrow)
+    bi, bj = np.nonzero(np.ones((n_body, n_arrow)))
+    di, dj = np.tril_indices(n_arrow)
+    rows = np.concatenate([np.arange(n_body), n_body + bj, n_body + di])
+    cols = np.concatenate([np.arange(n_body), bi, n_body + dj])
+    vals = np.concatenate([d, B[bi, bj], D[di, dj]])
+    colptr, rowidx, values = coo_to_csc_lower(n_body + n_arrow, rows, cols, vals)
+    return {"n": n_body + n_arrow, "n_arrow": n_arrow, "colptr": colptr, "rowidx": rowidx, "values": values,
+            "rhs": rng.standard_normal((n_body + n_arrow, 1)), "name": f"nearsing{n_body}_{n_arrow}_{eps_rel}"}
 
 
 def batch_sweep(count=256, seed=0, n_lo=5_000, n_hi=50_000):

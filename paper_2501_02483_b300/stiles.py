@@ -78,6 +78,7 @@ def lib():
         L.stiles_factor_get_trace.argtypes = [P, c_int32, P, POINTER(c_int64)]
         L.stiles_plan_tasks.argtypes = [P, c_int32, P, POINTER(c_int64)]
         L.stiles_factor_refine_iters.argtypes = [P]
+        L.stiles_factor_cg_iters.argtypes = [P]
         L.stiles_factor_refine_iters.restype = c_int32
         L.stiles_batch_create.argtypes = [P, c_int32, POINTER(c_void_p)]
         L.stiles_batch_factorize.argtypes = [P, P, P, P, P]
@@ -271,6 +272,10 @@ class Factor:
     def refine_iters(self):
         """Refinement steps of the last solve (0 for FP64 factors)."""
         return int(lib().stiles_factor_refine_iters(self._h))
+
+    def cg_iters(self):
+        """Of those, preconditioned conjugate-gradient iterations (refinement stalled)."""
+        return int(lib().stiles_factor_cg_iters(self._h))
 
     def set_trace(self, enable=True):
         """Stamp every device task with the global timer (needs a factorization first)."""

@@ -119,3 +119,38 @@ def test_refinement_gives_up_with_not_converged():
     with pytest.raises(st.StilesError) as e:
         f.solve(m["rhs"])
     assert e.value.name == "NOT_CONVERGED"
+
+
+def test_stalled_refinement_switches_to_preconditioned_cg():
+    """A BF16 factor of a matrix whose Schur complement is 1e-3 of its norm is too
+    inaccurate for refinement to converge; the solve hands over to conjugate
+    gradients preconditioned by that factor and still reaches refine_tol."""
+    m = inputs.near_singular_arrowhead(3000, 40, 1e-3, 1)
+    p = st.Plan.from_matrix(m, tile=64, precision=st.PREC_BF16)
+    f = st.Factor(p)
+    f.factorize(m["values"])
+    x, rr = f.solve(m["rhs"], relres=True)
+    assert rr <= 1e-10
+    assert f.cg_iters() >= 1 and f.refine_iters() >= f.cg_iters()
+    A = inputs.dense_from_csc(m)
+    xo = np.linalg.solve(A, m["rhs"])
+    assert np.max(np.abs(x - xo)) <= 1e-5 * np.max(np.abs(xo))
+    # a well-conditioned one never leaves refinement
+    m2 = inputs.near_singular_arrowhead(3000, 40, 1e-1, 2)
+    p2 = st.Plan.from_matrix(m2, tile=64, precision=st.PREC_BF16)
+    f2 = st.Factor(p2)
+    f2.factorize(m2["values"])
+    _, rr2 = f2.solve(m2["rhs"], relres=True)
+    assert rr2 <= 1e-10 and f2.cg_iters() == 0
+
+
+def test_in_place_device_solve_keeps_b_for_residuals():
+    m = inputs.config_small()
+    p = st.Plan.from_matrix(m, tile=64, precision=st.PREC_F16)
+    f = st.Factor(p)
+    f.factorize(m["values"])
+    b = torch.from_numpy(np.asfortranarray(m["rhs"])).cuda()
+    ref, _ = f.solve(b.clone(), relres=True)
+    x, rr = f.solve(b, x=b, relres=True)
+    assert rr <= 1e-10
+    assert torch.allclose(x, ref, rtol=1e-9, atol=0)
