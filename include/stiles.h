@@ -90,8 +90,8 @@ typedef struct {
   int64_t nscratch;    /* tree-reduction partial tiles                                 */
   int64_t flops_potrf, flops_syrk, flops_gemm, flops_trsm, flops_total; /* at tile size T */
   int64_t factor_bytes;  /* device bytes of the tile buffer                            */
-  int32_t ordering_used; /* STILES_ORDER_NONE or STILES_ORDER_RCM                      */
-  int32_t reserved0;
+  int32_t ordering_used; /* STILES_ORDER_NONE, _RCM or _ND                             */
+  int32_t chain_split;  /* 1: a one-matrix FP64 launch runs the diagonal chain on reserved SMs (thin DAG) */
 } stiles_plan_info;
 
 /* Fill *opts with the defaults listed above. */

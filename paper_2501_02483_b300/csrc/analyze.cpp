@@ -261,6 +261,8 @@ struct TreeNode {
 };
 
 constexpr int kTargetShift = 30;  // bit of a pair/partial index naming the CHAIN accumulator
+constexpr int64_t kChainKeep = 3;  // newest terms a diagonal-chain task applies itself
+constexpr double kSplitFlopsPerStep = 1e7;  // below: the chain runs on reserved SMs
 constexpr int32_t kIndexMask = (1 << 30) - 1;
 
 inline void set_col(DevTask& t, int32_t c) { t.col = c; }
@@ -303,10 +305,16 @@ inline void clear_second(DevTask& t) {
 }
 inline void clear_second(SolveTask&) {}
 
+// keep_types / keep: primaries of a type in keep_types (a bit mask) keep only
+// their last `keep` terms; every earlier term goes to tree leaves.  Used for
+// the diagonal chain of the factorization: its tasks are the critical path,
+// so the sums of the old band terms are formed ahead of time by other CTAs
+// (Algorithm 3 applied to band rows) and the chain task applies only the
+// newest terms plus one partial.
 template <class Task>
 void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32_t leaf_type, int32_t comb_type,
                  std::vector<Task>& tasks, std::vector<int32_t>& pairs, std::vector<int32_t>& parts,
-                 int64_t& nscratch) {
+                 int64_t& nscratch, uint32_t keep_types = 0, int64_t keep = 0) {
   const int64_t np = int64_t(prim.size());
   std::vector<TreeNode> nodes;
   std::vector<int32_t> node_list;                     // which list of its owner a node belongs to
@@ -319,15 +327,22 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
     for (int l = 0; l < 2; ++l) {
       const PairList& pl = prim[t].list[l];
       const int64_t npairs = int64_t(pl.pairs.size() / 2);
-      if (npairs <= chunk) continue;
-      const int64_t nchunks = (npairs + chunk - 1) / chunk;
+      // terms [0, split) go to leaves of at most `chunk` terms, the owner keeps the rest
+      int64_t split = 0;
+      if (keep > 0 && ((keep_types >> prim[t].type) & 1u)) {
+        if (npairs > keep + 1) split = npairs - keep;
+      } else if (npairs > chunk) {
+        split = ((npairs + chunk - 1) / chunk - 1) * chunk;
+      }
+      if (split == 0) continue;
+      const int64_t nleaves = (split + chunk - 1) / chunk;
       std::vector<int32_t> level;
-      for (int64_t c = 0; c + 1 < nchunks; ++c) {
+      for (int64_t c = 0; c < nleaves; ++c) {
         TreeNode nd;
         nd.type = leaf_type;
         nd.scratch = int32_t(nscratch++);
         nd.pb = c * chunk;
-        nd.pe = (c + 1) * chunk;
+        nd.pe = std::min(split, (c + 1) * chunk);
         int64_t rel = 0;
         for (int64_t q = nd.pb; q < nd.pe; ++q) rel = std::max(rel, pl.producers[q]);
         nd.release = rel;
@@ -339,7 +354,7 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
         parent.push_back(-1);
         pending.push_back(0);
       }
-      own_begin[2 * t + l] = (nchunks - 1) * chunk;
+      own_begin[2 * t + l] = split;
       while (int64_t(level.size()) > fanin) {
         std::vector<int32_t> next;
         for (size_t g = 0; g < level.size(); g += size_t(fanin)) {
@@ -849,7 +864,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
         if (q < 0) { *err = "internal: producer missing"; return STILES_ERR_INVALID; }
   try {
     build_graph(prim, o.tree_chunk, o.tree_fanin, TASK_PARTIAL, TASK_COMBINE, p->graph.tasks, p->graph.pairs,
-                p->graph.parts, p->graph.nscratch);
+                p->graph.parts, p->graph.nscratch, (1u << TASK_DIAG) | (1u << TASK_CHAIN), kChainKeep);
   } catch (const std::exception& ex) {
     *err = ex.what();
     return STILES_ERR_INVALID;
@@ -899,6 +914,18 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
                 p->bwd.parts, p->bwd.nscratch);
   }
   if (p->graph.nscratch >= (int64_t(1) << 30)) { *err = "too many tree partials"; return STILES_ERR_UNSUPPORTED; }
+  // the two queues of a split launch (critical diagonal chain / everything else)
+  p->chain_order.clear();
+  p->bulk_order.clear();
+  for (size_t t = 0; t < p->graph.tasks.size(); ++t) {
+    const int32_t ty = p->graph.tasks[t].type;
+    (ty == TASK_DIAG || ty == TASK_CHAIN ? p->chain_order : p->bulk_order).push_back(int32_t(t));
+  }
+  // Reserving SMs for the chain pays when the chain is the bottleneck: when the
+  // tile work per chain step is small next to what the machine does during one
+  // step (a thin band); on a wide band the reserved SMs would idle.
+  const double flops_total = double(p->flops_potrf + p->flops_syrk + p->flops_gemm + p->flops_trsm);
+  p->split_queues = !p->chain_order.empty() && flops_total / double(p->chain_order.size()) < kSplitFlopsPerStep;
   // every dependency must carry a smaller ticket, or the persistent kernels could wait forever
   if (!check_order(p->graph.tasks, p->graph.pairs, p->graph.parts, p->nsub, p->graph.nscratch, TASK_PARTIAL,
                    TASK_COMBINE, false, err) ||

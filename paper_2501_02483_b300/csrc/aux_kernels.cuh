@@ -58,7 +58,7 @@ __global__ void init_ctl_kernel(Ctl* ctl, int count) {
     ctl[i].ticket = 0;
     ctl[i].status = 0;
     ctl[i].abort = 0;
-    ctl[i].pad = 0;
+    ctl[i].ticket2 = 0;
     ctl[i].info = ~0ull;
     ctl[i].where = -1;
   }

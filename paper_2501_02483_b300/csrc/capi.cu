@@ -73,6 +73,8 @@ struct DevGraph {
   SolveTask* stasks = nullptr;
   int32_t* pairs = nullptr;
   int32_t* parts = nullptr;
+  int32_t* chain = nullptr;  // factor graph: the two queues of a split launch
+  int32_t* bulk = nullptr;
   int ntasks = 0;
 };
 
@@ -111,6 +113,7 @@ struct stiles_factor {
   int last_refine_iters = 0;
   int last_cg_iters = 0;      // of those, conjugate-gradient iterations (refinement stalled)
   int* flags = nullptr;       // nsub + nscratch
+  int* claim = nullptr;       // reserved-SM claims of a split factor launch
   stiles::dev::Ctl* ctl = nullptr;  // [0] factor, [1] forward, [2] backward
   double* logdet_part = nullptr;    // LOGDET_BLOCKS + 1
   // solve workspace (grown on demand)
@@ -137,6 +140,8 @@ namespace {
 using namespace stiles;
 
 void free_graph(DevGraph& g) {
+  cudaFree(g.chain);
+  cudaFree(g.bulk);
   cudaFree(g.tasks);
   cudaFree(g.stasks);
   cudaFree(g.pairs);
@@ -185,6 +190,14 @@ cudaError_t solve_occupancy(int* blocks) {
 
 std::mutex g_plan_mutex;  // plans are shared between threads (plan caches); uploads happen once
 
+// SMs reserved for the diagonal chain of a one-matrix FP64 factor launch (one
+// CTA each, alone on its SM, so its POTRF does not share the SM's FP64 pipe
+// with band updates); used when the launch has at least two CTAs per SM.
+#ifndef STILES_CHAIN_SMS
+#define STILES_CHAIN_SMS 8
+#endif
+constexpr int kChainSms = STILES_CHAIN_SMS;
+
 #ifndef STILES_SOLVE_CTAS_PER_MATRIX
 #define STILES_SOLVE_CTAS_PER_MATRIX 128
 #endif
@@ -209,6 +222,7 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
             chk(upload(&d->diag_sub, p->diag_sub)) && chk(upload(&d->colptr, p->colptr)) &&
             chk(upload(&d->rowidx, p->rowidx)) && chk(upload(&d->rptr, p->rptr)) && chk(upload(&d->rcol, p->rcol)) &&
             chk(upload(&d->rval, p->rval)) && chk(upload(&d->fac.tasks, p->graph.tasks)) &&
+            chk(upload(&d->fac.chain, p->chain_order)) && chk(upload(&d->fac.bulk, p->bulk_order)) &&
             chk(upload(&d->fac.pairs, p->graph.pairs)) && chk(upload(&d->fac.parts, p->graph.parts)) &&
             chk(upload(&d->fwd.stasks, p->fwd.tasks)) && chk(upload(&d->fwd.pairs, p->fwd.pairs)) &&
             chk(upload(&d->fwd.parts, p->fwd.parts)) && chk(upload(&d->bwd.stasks, p->bwd.tasks)) &&
@@ -275,6 +289,7 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->irwork);
   cudaFree(f->cgs);
   cudaFree(f->flags);
+  cudaFree(f->claim);
   cudaFree(f->ctl);
   cudaFree(f->logdet_part);
   cudaFree(f->Y);
@@ -313,6 +328,7 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
+  if (e == cudaSuccess) e = cudaMalloc(&f->claim, kChainSms * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&f->norms, 2 * dev::SOLVE_MAXR * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
@@ -362,13 +378,27 @@ dev::LPMatCtx lp_mat_ctx(const stiles_plan* p, stiles_factor* f) {
 
 template <int B>
 cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
-  dev::FactorArgs a;
+  dev::FactorArgs a{};
   a.single = mat_ctx(p, f);
   a.mats = nullptr;
   a.tickets = nullptr;
   a.ntasks = p->dev->fac.ntasks;
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
+  a.chain = p->dev->fac.chain;
+  a.bulk = p->dev->fac.bulk;
+  a.nchain = int(p->chain_order.size());
+  a.nbulk = int(p->bulk_order.size());
+  a.sm_claim = f->claim;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
+  // split only when every SM hosts several CTAs and both queues have work
+  a.chain_sms = (p->split_queues && p->dev->grid_factor >= 2 * sms && sms > kChainSms && a.nchain > 0 && a.nbulk > 0)
+                    ? kChainSms : 0;
+  if (a.chain_sms) {
+    cudaError_t e = cudaMemsetAsync(f->claim, 0, kChainSms * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   dev::factor_f64_kernel<B><<<p->dev->grid_factor, 128, dev::FactorCfg<B>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
@@ -524,6 +554,7 @@ stiles_status stiles_plan_get_info(const stiles_plan* p, stiles_plan_info* info)
   info->flops_total = p->flops_potrf + p->flops_syrk + p->flops_gemm + p->flops_trsm;
   info->factor_bytes = p->nsub * int64_t(p->B) * p->B * int64_t(sizeof(double));
   info->ordering_used = p->ordering_used;
+  info->chain_split = (p->split_queues && p->opts.precision == STILES_PREC_F64) ? 1 : 0;
   return STILES_OK;
 }
 

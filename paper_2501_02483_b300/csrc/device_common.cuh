@@ -18,7 +18,7 @@ struct Ctl {
   int ticket;               // next ticket to hand out
   int status;               // 0 = ok, STILES_ERR_TIMEOUT when a wait gave up
   int abort;                // set on timeout: every CTA leaves at its next check
-  int pad;
+  int ticket2;              // next ticket of the second queue (critical-chain tasks)
   unsigned long long info;  // 1-based permuted column of the first bad pivot, ULLONG_MAX if none
   long long where;          // diagnostic: ticket that timed out
 };

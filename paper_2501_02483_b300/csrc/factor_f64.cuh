@@ -62,8 +62,19 @@ struct FactorArgs {
   const MatCtx* mats;   // batched launch: one context per matrix (device memory)
   const int2* tickets;  // batched launch: (matrix, task) per ticket; NULL: one matrix, ticket = task
   int ntasks;           // tickets in the launch
-  Ctl* ctl;             // ticket counter, timeout status, abort flag of the launch
+  Ctl* ctl;             // ticket counters, timeout status, abort flag of the launch
   long long spin_limit;
+  // Optional split of a one-matrix launch into two queues: the diagonal chain
+  // (DIAG and CHAIN tasks, `chain`) runs on `chain_sms` reserved SMs, one CTA
+  // each; every other task (`bulk`) on the remaining SMs.  Both lists follow
+  // the one topological ticket order, so each queue's first unfinished task
+  // always has its inputs produced or in progress: no deadlock while each
+  // queue keeps a CTA.  chain_sms == 0: one queue, ticket = task.
+  const int32_t* chain;
+  const int32_t* bulk;
+  int nchain, nbulk;
+  int chain_sms;
+  int* sm_claim;        // [chain_sms], zeroed per launch: first CTA on a reserved SM takes the chain
 };
 
 // All threads have stored the tile; after the barrier, thread 0's release
@@ -406,13 +417,31 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   uint32_t phase = 0;  // bit s: parity of the next completion of barrier s
   const long long limit = a.spin_limit;
 
+  // queue of this CTA: the single ticket order, or (split launch) the chain
+  // queue for the first CTA on each reserved SM, the bulk queue elsewhere; the
+  // other CTAs on a reserved SM leave so the chain has the SM to itself
+  __shared__ int sRole;
+  if (tid == 0) {
+    int role = 0;
+    if (a.chain_sms > 0) {
+      const int sm = int(smid());
+      role = (sm < a.chain_sms) ? ((atomicAdd(a.sm_claim + sm, 1) == 0) ? 1 : -1) : 2;
+    }
+    sRole = role;
+  }
+  __syncthreads();
+  const int role = sRole;
+  if (role < 0) return;
+  int* const counter = (role == 1) ? &a.ctl->ticket2 : &a.ctl->ticket;
+  const int nqueue = (role == 1) ? a.nchain : (role == 2 ? a.nbulk : a.ntasks);
+
   int next = 0;
-  if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
+  if (tid == 0) next = atomicAdd(counter, 1);
   while (true) {
     if (tid == 0) {
       int cur = next;
-      if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) {
-        next = atomicAdd(&a.ctl->ticket, 1);
+      if (cur < nqueue && ld_volatile(&a.ctl->abort) == 0) {
+        next = atomicAdd(counter, 1);
       } else {
         cur = -1;
       }
@@ -420,8 +449,9 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       sAbort = 0;
     }
     __syncthreads();
-    const int t = sTicket;
-    if (t < 0) break;
+    const int t0 = sTicket;
+    if (t0 < 0) break;
+    const int t = (role == 1) ? a.chain[t0] : (role == 2 ? a.bulk[t0] : t0);  // task index (one matrix)
     int mi = 0, ti = t;
     if (a.tickets) {
       const int2 v = a.tickets[t];

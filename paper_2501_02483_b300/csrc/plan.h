@@ -95,6 +95,9 @@ struct stiles_plan {
   std::vector<int64_t> scatter;  // [nnz] element offset of each input entry in the tile buffer
   std::vector<int64_t> pad;      // element offsets of padding diagonal entries (rows >= n)
   stiles::TaskGraph graph;
+  std::vector<int32_t> chain_order;  // factor tasks of the diagonal chain (DIAG, CHAIN), ticket order
+  std::vector<int32_t> bulk_order;   // every other factor task, ticket order
+  bool split_queues = false;         // thin DAG: run the chain on reserved SMs (little work per chain step)
   stiles::SolveGraph fwd, bwd;
   stiles::DevPlan* dev = nullptr;
 };

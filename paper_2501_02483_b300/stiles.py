@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [(k, c_int64) for k in ("n", "n_arrow", "nnz", "tile", "nt", "nnzt", "block", "nsub", "ntasks",
                                        "npairs", "nscratch", "flops_potrf", "flops_syrk", "flops_gemm",
                                        "flops_trsm", "flops_total", "factor_bytes")] + [
-        ("ordering_used", c_int32), ("reserved0", c_int32)]
+        ("ordering_used", c_int32), ("chain_split", c_int32)]
 
 
 _LIB = None
@@ -179,7 +179,7 @@ class Plan:
     def info(self):
         i = PlanInfo()
         _check(lib().stiles_plan_get_info(self._h, ctypes.byref(i)))
-        return {k: getattr(i, k) for k, _ in PlanInfo._fields_ if k != "reserved0"}
+        return {k: getattr(i, k) for k, _ in PlanInfo._fields_}
 
     def perm(self):
         out = np.empty(self.n, dtype=np.int64)
