@@ -11,6 +11,9 @@
 namespace stiles {
 namespace dev {
 
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 // tiles[map[e]] = values[e]  (tiles zeroed beforehand; each target written once)
 __global__ void scatter_kernel(double* __restrict__ tiles, const double* __restrict__ values,
                                const int64_t* __restrict__ map, int64_t nnz) {
@@ -255,6 +258,39 @@ __global__ void residual_norms_kernel(const double* __restrict__ y, const double
     atomicAdd(sums + 2 * r, rr[0]);
     atomicAdd(sums + 2 * r + 1, bb[0]);
   }
+}
+
+// L_kk^{-1} of one diagonal sub-tile (lower triangular, zeros above the
+// diagonal), so the sweeps apply a small matrix-vector product per block
+// instead of a B-step substitution on their critical path.  Lane c (and
+// c + 32) forms column c by forward substitution on e_c, with the factor's
+// 1/L_ii.  Called by one warp per sub-tile.
+template <int B, typename TF>
+__device__ __forceinline__ void diag_inverse_tile(TF* __restrict__ X, const TF* __restrict__ L,
+                                                  const TF* __restrict__ inv, int lane) {
+  for (int c = lane; c < B; c += 32) {
+    TF x[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      TF s = (i == c) ? TF(1) : TF(0);
+#pragma unroll
+      for (int p = 0; p < i; ++p) s = fma_t(-__ldg(L + i + p * B), x[p], s);
+      x[i] = (i >= c) ? s * __ldg(inv + i) : TF(0);
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) X[i + c * B] = x[i];
+  }
+}
+
+// Every diagonal sub-tile of one factor: one warp per sub-tile.
+template <int B, typename TF>
+__global__ void diag_inverse_kernel(TF* __restrict__ linv, const TF* __restrict__ tiles,
+                                    const TF* __restrict__ invdiag, const int32_t* __restrict__ diag_sub,
+                                    int64_t nsb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < nsb; k += nwarps)
+    diag_inverse_tile<B, TF>(linv + k * B * B, tiles + int64_t(diag_sub[k]) * B * B, invdiag + k * B, lane);
 }
 
 // out[c] += sum_i a(i, c) b(i, c) for c < nr (grid.y = column; out zeroed beforehand)

@@ -103,7 +103,9 @@ struct stiles_factor {
   double* tiles = nullptr;    // FP64 path
   double* scratch = nullptr;
   double* invdiag = nullptr;
+  double* linv = nullptr;     // L_kk^{-1} of every diagonal sub-tile (nsb * B * B), for the sweeps
   float* tiles32 = nullptr;   // mixed-precision path
+  float* linv32 = nullptr;
   uint16_t* tiles16 = nullptr;
   float* scratch32 = nullptr;
   float* invdiag32 = nullptr;
@@ -270,8 +272,8 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
 void free_factor(stiles_factor* f) {
   if (!f) return;
   if (f->view) {  // the batch owns the factor arrays; only the solve workspace is the view's
-    f->values = f->tiles = f->scratch = f->invdiag = f->ldiag = nullptr;
-    f->tiles32 = f->scratch32 = f->invdiag32 = nullptr;
+    f->values = f->tiles = f->scratch = f->invdiag = f->ldiag = f->linv = nullptr;
+    f->tiles32 = f->scratch32 = f->invdiag32 = f->linv32 = nullptr;
     f->tiles16 = nullptr;
     f->flags = nullptr;
     f->ctl = nullptr;
@@ -281,6 +283,8 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->tiles);
   cudaFree(f->scratch);
   cudaFree(f->invdiag);
+  cudaFree(f->linv);
+  cudaFree(f->linv32);
   cudaFree(f->tiles32);
   cudaFree(f->tiles16);
   cudaFree(f->scratch32);
@@ -319,12 +323,14 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->linv, size_t(p->nsb) * tile * sizeof(double));
   } else {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles16, size_t(p->nsub) * tile * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch32, size_t(nscr) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag32, size_t(p->nsb) * p->B * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->ldiag, size_t(p->nsb) * p->B * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->linv32, size_t(p->nsb) * tile * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
@@ -416,13 +422,38 @@ cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t launch_diag_inverse(const stiles_plan* p, stiles_factor* f, cudaStream_t st) {
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>((p->nsb * 32 + 255) / 256, 148 * 16)));
+  if (f->lp) {
+    dev::diag_inverse_kernel<64, float><<<grid, 256, 0, st>>>(f->linv32, f->tiles32, f->invdiag32,
+                                                              p->dev->diag_sub, p->nsb);
+  } else {
+    switch (p->B) {
+      case 16:
+        dev::diag_inverse_kernel<16, double><<<grid, 256, 0, st>>>(f->linv, f->tiles, f->invdiag, p->dev->diag_sub,
+                                                                   p->nsb);
+        break;
+      case 32:
+        dev::diag_inverse_kernel<32, double><<<grid, 256, 0, st>>>(f->linv, f->tiles, f->invdiag, p->dev->diag_sub,
+                                                                   p->nsb);
+        break;
+      default:
+        dev::diag_inverse_kernel<64, double><<<grid, 256, 0, st>>>(f->linv, f->tiles, f->invdiag, p->dev->diag_sub,
+                                                                   p->nsb);
+        break;
+    }
+  }
+  return cudaGetLastError();
+}
+
 template <typename TF>
 dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backward, int nr, const TF* tiles,
-                            const TF* invdiag, TF* Y, TF* scratch, int* flags) {
+                            const TF* invdiag, const TF* linv, TF* Y, TF* scratch, int* flags) {
   const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1);
   dev::SolveCtx<TF> c;
   c.tiles = tiles;
   c.invdiag = invdiag;
+  c.linv = linv;
   c.Y = Y;
   c.nr = nr;
   c.pad0 = 0;
@@ -448,20 +479,20 @@ dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backwar
 
 template <int B, typename TF>
 cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr, const TF* tiles,
-                         const TF* invdiag) {
+                         const TF* invdiag, const TF* linv) {
   dev::SolveArgs<TF> a;
   a.mats = nullptr;
   a.tickets = nullptr;
   a.spin_limit = p->opts.spin_limit;
   TF* Y = reinterpret_cast<TF*>(f->Y);  // the double-sized workspaces also hold FP32 sweeps
   TF* scr = reinterpret_cast<TF*>(f->sscratch);
-  a.single = solve_ctx<TF>(p, f, false, nr, tiles, invdiag, Y, scr, f->sflags);
+  a.single = solve_ctx<TF>(p, f, false, nr, tiles, invdiag, linv, Y, scr, f->sflags);
   a.ntasks = p->dev->fwd.ntasks;
   a.ctl = f->ctl + 1;
   dev::solve_kernel<B, false, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B, TF>::SMEM, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  a.single = solve_ctx<TF>(p, f, true, nr, tiles, invdiag, Y, scr, f->sflags);
+  a.single = solve_ctx<TF>(p, f, true, nr, tiles, invdiag, linv, Y, scr, f->sflags);
   a.ntasks = p->dev->bwd.ntasks;
   a.ctl = f->ctl + 2;
   dev::solve_kernel<B, true, TF><<<p->dev->grid_solve, 128, dev::SolveCfg<B, TF>::SMEM, s>>>(a);
@@ -629,6 +660,10 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(e));
   count_launch();
   CUDA_TRY(cudaEventRecord(f->ev[2], st));
+  // inverses of the diagonal blocks for the sweeps (after the kernel's timing window)
+  e = launch_diag_inverse(p, f, st);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("diagonal inverses: ") + cudaGetErrorString(e));
+  count_launch();
   CUDA_TRY(cudaEventRecord(f->done, st));
   f->pending = true;
   return STILES_OK;
@@ -691,11 +726,11 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl + 1, 2);
   CUDA_TRY(cudaGetLastError());
   cudaError_t e;
-  if (f->lp) e = launch_solve<64, float>(p, f, st, nr, f->tiles32, f->invdiag32);
+  if (f->lp) e = launch_solve<64, float>(p, f, st, nr, f->tiles32, f->invdiag32, f->linv32);
   else switch (p->B) {
-    case 16: e = launch_solve<16, double>(p, f, st, nr, f->tiles, f->invdiag); break;
-    case 32: e = launch_solve<32, double>(p, f, st, nr, f->tiles, f->invdiag); break;
-    default: e = launch_solve<64, double>(p, f, st, nr, f->tiles, f->invdiag); break;
+    case 16: e = launch_solve<16, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
+    case 32: e = launch_solve<32, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
+    default: e = launch_solve<64, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
   if (f->lp)
@@ -1085,13 +1120,17 @@ struct stiles_batch {
   double* values = nullptr;
   void* dscatter = nullptr;  // per-matrix BScatter descriptors (each plan's own device scatter map)
   int64_t max_scatter = 0;   // largest nnz + padding count of one matrix
+  int64_t max_nsb = 0;       // largest number of diagonal sub-tiles of one matrix
   double* tiles = nullptr;
   double* scratch = nullptr;
   double* invdiag = nullptr;
+  double* linv = nullptr;       // L_kk^{-1} per diagonal sub-tile, concatenated
+  void* dinv = nullptr;         // per-matrix BInverse descriptors
   float* tiles32 = nullptr;
   uint16_t* tiles16 = nullptr;
   float* scratch32 = nullptr;
   float* invdiag32 = nullptr;
+  float* linv32 = nullptr;
   double* ldiag = nullptr;
   int* flags = nullptr;
   unsigned long long* infos = nullptr;
@@ -1138,6 +1177,26 @@ struct stiles_batch {
 };
 
 namespace {
+
+// Per-matrix descriptor of the batched diagonal inverses (L_kk^{-1} for the sweeps).
+struct BInverse {
+  void* linv;
+  const void* tiles;
+  const void* invdiag;
+  const int32_t* diag_sub;
+  int64_t nsb;
+};
+
+template <int B, typename TF>
+__global__ void bdiag_inverse_kernel(const BInverse* desc) {
+  const BInverse c = desc[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < c.nsb; k += nwarps)
+    dev::diag_inverse_tile<B, TF>(static_cast<TF*>(c.linv) + k * B * B,
+                                  static_cast<const TF*>(c.tiles) + int64_t(c.diag_sub[k]) * B * B,
+                                  static_cast<const TF*>(c.invdiag) + k * B, lane);
+}
 
 // Per-matrix descriptor of the batched scatter: the plan's own device scatter
 // map and padding list, offset into the batch's concatenated values and tiles.
@@ -1318,6 +1377,9 @@ void free_batch(stiles_batch* b) {
   release(b->tiles);
   release(b->scratch);
   release(b->invdiag);
+  release(b->linv);
+  release(b->linv32);
+  release(b->dinv);
   release(b->tiles32);
   release(b->tiles16);
   release(b->scratch32);
@@ -1404,6 +1466,20 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaEventRecordWithFlags(b->ev_k1, st, cudaEventRecordExternal));
+  {
+    const int count = int(b->plans.size());
+    const dim3 g(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_nsb * 32 + 255) / 256,
+                                                                   std::max<int64_t>(1, 148 * 16 / count)))),
+                 unsigned(count));
+    const BInverse* di = static_cast<const BInverse*>(b->dinv);
+    if (b->lp) bdiag_inverse_kernel<64, float><<<g, 256, 0, st>>>(di);
+    else switch (b->B) {
+      case 16: bdiag_inverse_kernel<16, double><<<g, 256, 0, st>>>(di); break;
+      case 32: bdiag_inverse_kernel<32, double><<<g, 256, 0, st>>>(di); break;
+      default: bdiag_inverse_kernel<64, double><<<g, 256, 0, st>>>(di); break;
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
   return STILES_OK;
 }
 
@@ -1501,17 +1577,20 @@ stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cuda
     const stiles_factor* v = b->views[i];
     const TF* tiles;
     const TF* inv;
+    const TF* linv;
     if constexpr (sizeof(TF) == 4) {
       tiles = v->tiles32;
       inv = v->invdiag32;
+      linv = v->linv32;
     } else {
       tiles = v->tiles;
       inv = v->invdiag;
+      linv = v->linv;
     }
     TF* Y = reinterpret_cast<TF*>(b->sY) + b->y_off[i];  // double-sized buffers also hold FP32 sweeps
     TF* scr = reinterpret_cast<TF*>(b->sScr) + b->scr_off[i];
-    cf[i] = solve_ctx<TF>(p, nullptr, false, nr[i], tiles, inv, Y, scr, b->sFlags + b->flag_off[i]);
-    cb[i] = solve_ctx<TF>(p, nullptr, true, nr[i], tiles, inv, Y, scr, b->sFlags + b->flag_off[i]);
+    cf[i] = solve_ctx<TF>(p, nullptr, false, nr[i], tiles, inv, linv, Y, scr, b->sFlags + b->flag_off[i]);
+    cb[i] = solve_ctx<TF>(p, nullptr, true, nr[i], tiles, inv, linv, Y, scr, b->sFlags + b->flag_off[i]);
     BSolveDesc& d = desc[i];
     d.perm = p->dev->perm;
     d.n = p->n;
@@ -1703,11 +1782,13 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->tiles, size_t(b->tile_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->scratch, size_t(b->scratch_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->invdiag, size_t(b->diag_elems));
+  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->linv, size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles16, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->invdiag32, size_t(b->diag_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->ldiag, size_t(b->diag_elems));
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->linv32, size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess) e = batch_alloc(b, &b->flags, size_t(b->flag_total));
   if (e == cudaSuccess) e = batch_alloc(b, &b->infos, size_t(count));
   if (e == cudaSuccess) e = batch_alloc(b, &b->ctl, 1);
@@ -1724,6 +1805,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   std::vector<dev::MatCtx> mats;
   std::vector<dev::LPMatCtx> lmats;
   std::vector<BatchLogCtx> logs(count);
+  std::vector<BInverse> binv(count);
   for (int i = 0; i < count; ++i) {
     const stiles_plan* p = plans[i];
     stiles_factor* v = new (std::nothrow) stiles_factor();
@@ -1741,11 +1823,13 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       v->tiles16 = b->tiles16 + t_off[i];
       v->scratch32 = b->scratch32 + s_off[i];
       v->invdiag32 = b->invdiag32 + d_off[i];
+      v->linv32 = b->linv32 + d_off[i] * b->B;
       v->ldiag = b->ldiag + d_off[i];
     } else {
       v->tiles = b->tiles + t_off[i];
       v->scratch = b->scratch + s_off[i];
       v->invdiag = b->invdiag + d_off[i];
+      v->linv = b->linv + d_off[i] * b->B;
     }
     // the view's small arrays are slices of batch-wide ones; a view never
     // factorizes, so it has no events
@@ -1755,10 +1839,16 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     if (b->lp) lmats.push_back(lp_mat_ctx(p, v));
     else mats.push_back(mat_ctx(p, v));
     logs[i] = BatchLogCtx{v->tiles, p->dev->diag_sub, v->ldiag, p->n, b->B, 0};
+    binv[i] = BInverse{b->lp ? static_cast<void*>(v->linv32) : static_cast<void*>(v->linv),
+                       b->lp ? static_cast<const void*>(v->tiles32) : static_cast<const void*>(v->tiles),
+                       b->lp ? static_cast<const void*>(v->invdiag32) : static_cast<const void*>(v->invdiag),
+                       p->dev->diag_sub, p->nsb};
+    b->max_nsb = std::max<int64_t>(b->max_nsb, p->nsb);
   }
   if (b->lp) e = batch_upload(b, reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
   else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
+  if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BInverse**>(&b->dinv), binv);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   std::vector<int64_t> lens(count);
   for (int i = 0; i < count; ++i) lens[i] = int64_t(plans[i]->graph.tasks.size());
@@ -1820,7 +1910,7 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(3);  // scatter, init, persistent kernel
+  count_launch(4);  // scatter, init, persistent kernel, diagonal inverses
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));

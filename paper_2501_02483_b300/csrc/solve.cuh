@@ -17,6 +17,7 @@
 // (RP = B / W rows each); the NT / W lane groups take columns g, g + G, ...
 #pragma once
 
+#include "aux_kernels.cuh"
 #include "device_common.cuh"
 #include "plan.h"
 
@@ -39,14 +40,14 @@ struct SolveCfg {
   static constexpr size_t SMEM = ((SMEM_ELEMS * sizeof(TF) + 15) / 16) * 16 + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
 
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 
 // One matrix of a solve launch (a batched launch carries one per matrix).
 template <typename TF>
 struct SolveCtx {
   const TF* tiles;        // factor sub-tiles (FP64, or FP32 for a mixed-precision factor)
   const TF* invdiag;      // nsb * B
+  const TF* linv;         // nsb * B * B: L_kk^{-1} of every diagonal sub-tile
   TF* Y;                  // nsb blocks of B x nr
   TF* scratch;            // nscratch blocks
   const SolveTask* tasks;
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
   constexpr int W = Cfg::W, RP = Cfg::RP, G = Cfg::G, U = Cfg::U, TILE = Cfg::TILE, NSTAGE = Cfg::NSTAGE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TF* sStage = reinterpret_cast<TF*>(smem_raw);                    // NSTAGE * (TILE + BLK)
-  TF* sL = sStage + NSTAGE * (TILE + Cfg::BLK);                     // TILE
-  TF* sLt = sL + TILE;                                              // B x (B + 1), transposed L_kk
-  TF* sInv = sLt + B * (B + 1);                                     // B
+  TF* sL = sStage + NSTAGE * (TILE + Cfg::BLK);                     // TILE: L_kk^{-1}
+  TF* sLt = sL + TILE;                                              // B x (B + 1): the accumulated block
+  TF* sInv = sLt + B * (B + 1);                                     // B (unused)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ((Cfg::SMEM_ELEMS * sizeof(TF) + 15) / 16) * 16);
   __shared__ int sTicket, sAbort;
 
@@ -140,10 +141,10 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
         for (int s = 0; s < RP; ++s) acc[s][u] = TF(0);
     }
 
-    // the diagonal sub-tile does not depend on this sweep: fetch it first
+    // the diagonal block's inverse does not depend on this sweep: fetch it first
     if (tk.type == SOLVE_FINAL && tid == 0) {
       mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(TF)));
-      tma_load_1d(sL, mc.tiles + size_t(tk.diag) * TILE, TILE * sizeof(TF), &bars[NSTAGE]);
+      tma_load_1d(sL, mc.linv + size_t(tk.out) * TILE, TILE * sizeof(TF), &bars[NSTAGE]);
     }
     const int npairs = tk.pe - tk.pb;
     const int nitems = npairs + (tk.qe - tk.qb);
@@ -271,8 +272,7 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
       continue;
     }
 
-    // ---- triangular solve with the diagonal sub-tile (prefetched above) ----
-    if (tid < B) sInv[tid] = __ldcg(mc.invdiag + size_t(tk.out) * B + tid);
+    // ---- y = L_kk^{-1} acc (forward) or x = L_kk^{-T} acc (backward), L_kk^{-1} prefetched ----
     {
       long long spins = 0;
       while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
@@ -281,51 +281,29 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
     }
     if (aborted) break;
     phase ^= (1u << NSTAGE);
-    if (BACKWARD) {
-      for (int e = tid; e < TILE; e += Cfg::NT) {
-        const int r = e % B, c = e / B;
-        sLt[c + r * (B + 1)] = sL[e];  // sLt(c, r) = L(r, c)
-      }
+    TF* sAcc = sLt;  // B x nr block of the accumulated right-hand sides
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = grp + G * u;
+      if (r < nr)
+#pragma unroll
+        for (int s = 0; s < RP; ++s) sAcc[r * B + li + W * s] = acc[s][u];
     }
     __syncthreads();
     const int warp_grp0 = (tid & ~31) / W;  // first column group of this warp (warp-uniform guard)
-    if (!BACKWARD) {
-      // forward substitution: y_j = acc_j / L_jj, then acc_i -= L_ij y_j (i > j)
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        const int sj = j / W, lj = j % W;
-        const TF inv = sInv[j];
+    for (int u = 0; u < U; ++u) {
+      if (warp_grp0 + G * u >= nr) break;
+      const int r = grp + G * u;
+      const TF* a = sAcc + (r < nr ? r : 0) * B;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (warp_grp0 + G * u >= nr) break;
-          TF y = acc[sj][u] * inv;
-          y = __shfl_sync(0xffffffffu, y, (tid & 31) - li + lj);
-          if (li == lj) acc[sj][u] = y;
+      for (int s = 0; s < RP; ++s) {
+        const int i = li + W * s;
+        TF v = TF(0);
+        // the inverse is stored with zeros above its diagonal: full-length sums
 #pragma unroll
-          for (int s = 0; s < RP; ++s) {
-            const int i = li + W * s;
-            if (i > j) acc[s][u] = fma_t(-sL[i + j * B], y, acc[s][u]);
-          }
-        }
-      }
-    } else {
-      // backward substitution with L^T: x_j = acc_j / L_jj, then acc_i -= L_ji x_j (i < j)
-#pragma unroll
-      for (int j = B - 1; j >= 0; --j) {
-        const int sj = j / W, lj = j % W;
-        const TF inv = sInv[j];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (warp_grp0 + G * u >= nr) break;
-          TF x = acc[sj][u] * inv;
-          x = __shfl_sync(0xffffffffu, x, (tid & 31) - li + lj);
-          if (li == lj) acc[sj][u] = x;
-#pragma unroll
-          for (int s = 0; s < RP; ++s) {
-            const int i = li + W * s;
-            if (i < j) acc[s][u] = fma_t(-sLt[i + j * (B + 1)], x, acc[s][u]);
-          }
-        }
+        for (int p = 0; p < B; ++p) v = fma_t(BACKWARD ? sL[p + i * B] : sL[i + p * B], a[p], v);
+        acc[s][u] = v;
       }
     }
     {
