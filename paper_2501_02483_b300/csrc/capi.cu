@@ -243,8 +243,10 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
   int fb = 0, sb = 0;
   cudaError_t e = cudaSuccess;
   if (p->opts.precision != STILES_PREC_F64) {
-    e = cudaFuncSetAttribute(dev::factor_lp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dev::LP_SMEM));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, dev::factor_lp_kernel, 128, dev::LP_SMEM);
+    e = cudaFuncSetAttribute(dev::factor_lp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(dev::LP_KERNEL_SMEM));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, dev::factor_lp_kernel, dev::LP_THREADS, dev::LP_KERNEL_SMEM);
     // each resident CTA holds 128 TMEM columns of the SM's 512
     fb = std::min(fb, 4);
     if (e == cudaSuccess) e = solve_occupancy<64, float>(&sb);
@@ -418,7 +420,7 @@ cudaError_t launch_factor_lp(const stiles_plan* p, stiles_factor* f, cudaStream_
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
   a.fp16 = p->opts.precision == STILES_PREC_F16 ? 1 : 0;
-  dev::factor_lp_kernel<<<p->dev->grid_factor, 128, dev::LP_SMEM, s>>>(a);
+  dev::factor_lp_kernel<<<p->dev->grid_factor, dev::LP_THREADS, dev::LP_KERNEL_SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1450,7 +1452,7 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
     a.ctl = b->ctl;
     a.spin_limit = b->spin_limit;
     a.fp16 = b->fp16;
-    dev::factor_lp_kernel<<<b->grid, 128, dev::LP_SMEM, st>>>(a);
+    dev::factor_lp_kernel<<<b->grid, dev::LP_THREADS, dev::LP_KERNEL_SMEM, st>>>(a);
   } else {
     dev::FactorArgs a{};
     a.mats = static_cast<const dev::MatCtx*>(b->dmats);
@@ -1862,7 +1864,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   int per_sm = std::max(1, plans[0]->dev->grid_factor / std::max(1, sms));
   if (b->lp) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::factor_lp_kernel, 128, dev::LP_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::factor_lp_kernel, dev::LP_THREADS,
+                                                  dev::LP_KERNEL_SMEM);
     per_sm = std::min(per_sm, 4);
   } else {
     switch (b->B) {

@@ -194,17 +194,19 @@ __device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinte
 // nearly every lane of every FP64 instruction does useful work (an FP64 warp
 // instruction costs the same pipe time however many lanes are active).
 // Flags live in shared memory (PotrfFlags words); waits are bounded by
-// `limit` polls.  Returns -1, the first bad pivot (<= 0 or NaN; the tile is
+// `limit` polls.  `tid` counts the 128 participating threads from 0 and
+// `sync` is their barrier (the CTA's, or a named barrier of a task slot).  Returns -1, the first bad pivot (<= 0 or NaN; the tile is
 // then filled with NaN), or -2 when a wait gave up.  sInv receives 1/L_jj;
 // the strict upper triangle is zeroed.
-template <int B>
-__device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int* sF, int tid, long long limit) {
+template <int B, class Sync>
+__device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int* sF, int tid, long long limit,
+                              Sync sync) {
   using F = PotrfFlags<B>;
   constexpr int NE = B * (B + 1) / 2;
   constexpr int NK = (NE + 31) / 32;
   const int warp = tid >> 5, lane = tid & 31;
   for (int w = tid; w < F::WORDS; w += 128) sF[w] = (w == F::STATUS) ? -1 : 0;
-  __syncthreads();
+  sync();
   auto pivot_ok = [](double d) {
     const long long bits = __double_as_longlong(d);
     return bits > 0 && bits <= 0x7ff0000000000000LL;  // positive, at most +inf
@@ -354,7 +356,7 @@ __device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int*
       }
     }
   }
-  __syncthreads();
+  sync();
   const int bad = sF[F::STATUS];
   if (bad != -1) {
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
@@ -364,7 +366,7 @@ __device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int*
     for (int e = tid; e < B * B; e += 128)
       if ((e % B) < (e / B)) sD[e] = 0.0;  // strict upper triangle (row < column)
   }
-  __syncthreads();
+  sync();
   return bad;
 }
 

@@ -32,13 +32,17 @@ constexpr int LP_TILE = LP_B * LP_B;
 constexpr int LP_NSTAGE = 2;
 constexpr uint32_t LP_OP_BYTES = LP_TILE * 2;       // one 16-bit operand tile
 constexpr uint32_t LP_STAGE_BYTES = 3 * LP_OP_BYTES; // A (tile + 64 zero rows) + B
-constexpr uint32_t LP_TMEM_COLS = 128;              // two 64-column FP32 accumulators
+constexpr uint32_t LP_TMEM_COLS = 128;              // two 64-column FP32 accumulators (per slot)
+constexpr int LP_SLOTS = 2;                         // task slots per CTA
+constexpr int LP_THREADS = 128 * LP_SLOTS;
 
 // shared memory: stages | sD (FP64 64x64) | sL (FP32 64x64) | sInv/sPiv/sRs (FP64 x 64 each; sPiv and sRs
 // hold the POTRF's flag words) | barriers
 static_assert(PotrfFlags<64>::WORDS * sizeof(int) <= 2 * 64 * sizeof(double), "POTRF flags fit in sPiv/sRs");
 constexpr size_t LP_SMEM = size_t(LP_NSTAGE) * LP_STAGE_BYTES + LP_TILE * 8 + LP_TILE * 4 + 3 * LP_B * 8 +
                            (LP_NSTAGE * 2 + 2) * 8 + 64;
+constexpr size_t LP_SLOT_BYTES = (LP_SMEM + 1023) / 1024 * 1024;  // one slot's dynamic shared memory
+constexpr size_t LP_KERNEL_SMEM = LP_SLOTS * LP_SLOT_BYTES;
 
 struct LPMatCtx {
   float* tiles32;        // nsub * 64 * 64, column-major
@@ -133,8 +137,23 @@ __device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int s
   }
 }
 
-__global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+// One task slot: 128 threads (4 warps) running the persistent task loop on
+// their own shared-memory area, mbarriers, TMEM columns and ticket, with a
+// named barrier for the slot's own synchronisation.
+__shared__ uint16_t lp_sIC[LP_B * (LP_B + 1) / 2];  // lower-triangle numbering of the POTRF
+
+template <int SLOT>
+__device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid) {
+  extern __shared__ __align__(1024) unsigned char lp_dyn[];
+  __shared__ int sTicket, sAbort;  // one pair per instantiation, i.e. per slot
+  unsigned char* smem_raw = lp_dyn + SLOT * LP_SLOT_BYTES;
+  const uint16_t* sIC = lp_sIC;
+  __builtin_assume(tid >= 0 && tid < 128);
+  auto sync = []() { asm volatile("bar.sync %0, 128;" ::"n"(1 + SLOT) : "memory"); };
+  auto publish = [&](int* flag) {
+    sync();
+    if (tid == 0) st_release(flag, 1);
+  };
   unsigned char* sStage = smem_raw;                                    // LP_NSTAGE * LP_STAGE_BYTES
   double* sD = reinterpret_cast<double*>(sStage + LP_NSTAGE * LP_STAGE_BYTES);  // 64x64 FP64
   float* sL = reinterpret_cast<float*>(sD + LP_TILE);                 // 64x64 FP32
@@ -145,11 +164,8 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
   uint64_t* empty = full + LP_NSTAGE;                         // [LP_NSTAGE] MMAs done with the stage
   uint64_t* accbar = empty + LP_NSTAGE;                       // all MMAs of the task done
   uint64_t* lbar = accbar + 1;                                // L_kk landed
-  __shared__ uint32_t sTmem;
-  __shared__ int sTicket, sAbort;
-  __shared__ uint16_t sIC[LP_B * (LP_B + 1) / 2];  // lower-triangle numbering of the POTRF
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int warp = tid >> 5, lane = tid & 31;
+  (void)lane;
   if (tid == 0) {
     for (int s = 0; s < LP_NSTAGE; ++s) {
       mbar_init(&full[s], 1);
@@ -159,22 +175,13 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     mbar_init(lbar, 1);
     mbar_fence_init();
   }
-  init_lower_index<LP_B>(sIC, tid, 128);
   // the 64 zero rows below each A operand tile (the MMA is M = 128)
   for (int s = 0; s < LP_NSTAGE; ++s) {
     uint4* z = reinterpret_cast<uint4*>(sStage + s * LP_STAGE_BYTES + LP_OP_BYTES);
     for (int i = tid; i < int(LP_OP_BYTES / 16); i += 128) z[i] = make_uint4(0, 0, 0, 0);
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sTmem)),
-                 "r"(LP_TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   fence_proxy_async_shared();
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = sTmem;
+  sync();
   const long long limit = a.spin_limit;
   // kind::f16 instruction descriptor: D = F32, A/B = BF16 (1) or F16 (0), both K-major,
   // N = 64 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       sTicket = cur;
       sAbort = 0;
     }
-    __syncthreads();
+    sync();
     const int t = sTicket;
     if (t < 0) break;
     int mi = 0, ti = t;
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
       if (trace) trace[1] = (long long)globaltimer();
       sTicket = (used[0] ? 1 : 0) | (used[1] ? 2 : 0);
     }
-    __syncthreads();
+    sync();
     if (sAbort) { aborted = true; break; }
     const int used_mask = sTicket;
     if (!mbar_wait_bounded(accbar, ph_acc & 1u)) { aborted = true; break; }
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
         raise_timeout(a.ctl, t);
         sAbort = 1;
       }
-      __syncthreads();
+      sync();
       if (sAbort) { aborted = true; break; }
       if (warp < 2) {
         const float* src = mc.scratch + size_t(s) * LP_TILE;
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
           tma_load_1d(sL, mc.tiles32 + size_t(tk.diag) * LP_TILE, LP_TILE * 4, lbar);
         }
       }
-      __syncthreads();
+      sync();
       if (sAbort) { aborted = true; break; }
       if (!mbar_wait_bounded(lbar, ph_l & 1u)) { aborted = true; break; }
       ph_l ^= 1u;
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
         continue;
       }
       // CHAIN: the SYRK term of the just-solved tile, in FP32 from shared memory
-      __syncthreads();  // every row finished reading L_kk from sL
+      sync();  // every row finished reading L_kk from sL
       if (warp < 2) {
 #pragma unroll
         for (int c = 0; c < LP_B; ++c) sL[c * LP_B + r] = x1[c];
@@ -415,10 +422,10 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
 #pragma unroll
       for (int c = 0; c < LP_B; ++c) sD[c * LP_B + r] = double(x1[c]);
     }
-    __syncthreads();
+    sync();
     {
       // sPiv/sRs (2 x 64 doubles) hold the POTRF's flag words
-      const int bad = potrf_tile_ws<LP_B>(sD, sInv, sIC, reinterpret_cast<int*>(sPiv), tid, limit);
+      const int bad = potrf_tile_ws<LP_B>(sD, sInv, sIC, reinterpret_cast<int*>(sPiv), tid, limit, sync);
       if (bad == -2) {
         if (tid == 0) raise_timeout(a.ctl, t);
         aborted = true;
@@ -437,14 +444,37 @@ __global__ void __launch_bounds__(128) factor_lp_kernel(LPArgs a) {
     if (trace && tid == 0) trace[2] = (long long)globaltimer();
   }
 
-  // ---- leave: no MMA or copy may still target this CTA's memory ----
+  // ---- leave: no MMA or copy may still target this slot's memory ----
   if (tid == 0) {
     for (int s = 0; s < LP_NSTAGE; ++s)
       if ((pending >> s) & 1u) mbar_wait_bounded(&empty[s], (ph_empty >> s) & 1u);
   }
+}
+
+// Two task slots per CTA: a kernel that allocates tensor memory runs one CTA
+// per SM, so each CTA hosts two independent 128-thread slots (two tasks in
+// flight per SM).  TMEM: LP_TMEM_COLS columns per slot, allocated once.
+__global__ void __launch_bounds__(LP_THREADS) factor_lp_kernel(LPArgs a) {
+  __shared__ uint32_t sTmem;
+  const int slot = threadIdx.x >> 7, tid = threadIdx.x & 127;
+  init_lower_index<LP_B>(lp_sIC, threadIdx.x, LP_THREADS);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sTmem)),
+                 "r"(LP_SLOTS * LP_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LP_TMEM_COLS));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  static_assert(LP_SLOTS == 2, "one lp_slot instantiation per slot");
+  if (slot == 0)
+    lp_slot<0>(a, sTmem, tid);
+  else
+    lp_slot<1>(a, sTmem + LP_TMEM_COLS, tid);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sTmem), "r"(LP_SLOTS * LP_TMEM_COLS));
 }
 
 }  // namespace dev
