@@ -34,7 +34,8 @@ struct FactorCfg {
   static constexpr int CPT = B / RPT; // columns per thread
   static constexpr int TILE = B * B;
   static constexpr int NSTAGE = (B == 64) ? 2 : 3;
-  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 3 * B;
+  // stages | sC | sL | sInv, sPiv, sRs, sInvd, sInvL (B each; sInvL is a TMA target)
+  static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 5 * B;
   static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
 
@@ -151,6 +152,165 @@ __device__ __forceinline__ int potrf_tile(double (&acc)[FactorCfg<B>::CPT], doub
   }
   __syncthreads();
   return bad;
+}
+
+// Strictly-lower elements of a B x B tile cut into row chunks of PW_CS
+// columns: row i (1 <= i < B) holds chunks (i, 0), (i, PW_CS), ... below the
+// diagonal.  Entry k of the chunk table is (i << 8) | c0.  Filled once per CTA.
+constexpr int PW_CS = 2;
+template <int B>
+struct PotrfPw {
+  static constexpr int NCHUNK = [] {
+    int n = 0;
+    for (int i = 1; i < B; ++i) n += (i + PW_CS - 1) / PW_CS;
+    return n;
+  }();
+  static constexpr int NUPD = 96;                       // warps 0-2 update, warp 3 pivots
+  static constexpr int NCH = (NCHUNK + NUPD - 1) / NUPD;  // chunks per update thread
+};
+
+template <int B>
+__device__ __forceinline__ void init_chunks(uint16_t* sChunk, int tid, int nthreads) {
+  for (int k = tid; k < PotrfPw<B>::NCHUNK; k += nthreads) {
+    int i = 1, kk = k;
+    while (kk >= (i + PW_CS - 1) / PW_CS) {
+      kk -= (i + PW_CS - 1) / PW_CS;
+      ++i;
+    }
+    sChunk[k] = uint16_t((i << 8) | (kk * PW_CS));
+  }
+}
+
+// POTRF of a B x B FP64 tile (B <= 32) held in `acc` (row-quad layout), in
+// the LDL^T form of the right-looking algorithm with the pivots on their own
+// warp, so that the dependency chain of a step is one FMA and one reciprocal:
+//
+//   warp 3 holds the diagonal (lane i: d_i).  At step j it applies column j
+//     to the diagonal, d_i -= (a_ij / d_j) a_ij (in this order: a_ij^2 could
+//     leave the exponent range where the tile's entries do not), and takes
+//     1/d_{j+1} (fast_rcp) for the next step;
+//   warps 0-2 hold the strictly lower elements in registers, in row chunks,
+//     and apply step j, a_ic -= (a_ij / d_j) a_cj (c > j); the elements of
+//     column j+1 are then final and go to sC.
+//
+// One barrier per step.  The factor is L_ic = a_ic / sqrt(d_c), taken at the
+// end (the reciprocal square roots of all pivots in parallel, off the chain).
+// sStat[j] flags pivot j as bad (<= 0 or NaN); each flag is written one step
+// before it is read, so every warp leaves the loop at the same step.
+// Returns the first bad pivot (the tile is then NaN) or -1; sInv receives
+// 1/L_jj.  Shared scratch: sC (B x B), sPiv, sRs, sInvd (B each), sStat (B
+// ints), sChunk (the chunk table).
+template <int B>
+__device__ __forceinline__ int potrf_tile_pw(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv,
+                                             double* sInv, double* sRs, double* sInvd, int* sStat,
+                                             const uint16_t* sChunk, int row, int q, int tid) {
+  static_assert(B <= 32, "one pivot per lane of the pivot warp");
+  constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
+  constexpr int NCH = PotrfPw<B>::NCH, NCHUNK = PotrfPw<B>::NCHUNK, NUPD = PotrfPw<B>::NUPD;
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
+  if (tid < B) sStat[tid] = 0;
+  __syncthreads();
+
+  double d = 1.0;  // pivot warp: d_lane (lanes >= B keep 1)
+  double a[NCH][PW_CS];
+  int ci[NCH], c0[NCH];
+  if (warp == 3) {
+    if (lane < B) d = sC[lane * (B + 1)];
+    const double r = fast_rcp(lane == 0 ? d : 1.0);
+    if (lane == 0) {
+      sInvd[0] = r;
+      const long long bits = __double_as_longlong(d);
+      if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) sStat[0] = 1;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < NCH; ++u) {
+      const int k = tid + NUPD * u;
+      ci[u] = 0;
+      c0[u] = B;  // no chunk: never live
+      if (k < NCHUNK) {
+        const int v = sChunk[k];
+        ci[u] = v >> 8;
+        c0[u] = v & 255;
+      }
+#pragma unroll
+      for (int e = 0; e < PW_CS; ++e) a[u][e] = (c0[u] + e < ci[u]) ? sC[ci[u] + (c0[u] + e) * B] : 0.0;
+    }
+  }
+  __syncthreads();
+
+  int bad = -1;
+  for (int j = 0; j + 1 < B; ++j) {
+    if (sStat[j]) {
+      bad = j;
+      break;
+    }
+    if (warp == 3) {
+      const double aij = sC[(lane < B ? lane : 0) + j * B];
+      const double invj = sInvd[j];
+      if (lane > j && lane < B) d = fma(-(aij * invj), aij, d);
+      const double r = fast_rcp(lane == j + 1 ? d : 1.0);
+      if (lane == j + 1) {
+        sInvd[j + 1] = r;
+        const long long bits = __double_as_longlong(d);
+        if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) sStat[j + 1] = 1;
+      }
+    } else {
+      const double invj = sInvd[j];
+#pragma unroll
+      for (int u = 0; u < NCH; ++u) {
+        const int i = ci[u], cb = c0[u];
+        // live: some column c of the chunk with j < c < i
+        if (max(cb, j + 1) < min(cb + PW_CS, i)) {
+          const double tr = sC[i + j * B] * invj;
+#pragma unroll
+          for (int e = 0; e < PW_CS; ++e)
+            if (cb + e > j && cb + e < i) a[u][e] = fma(-tr, sC[cb + e + j * B], a[u][e]);
+#pragma unroll
+          for (int e = 0; e < PW_CS; ++e)
+            if (cb + e == j + 1) sC[i + (j + 1) * B] = a[u][e];  // column j+1 is final
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (bad < 0 && sStat[B - 1]) bad = B - 1;
+
+  if (bad >= 0) {
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = nanv;
+    if (tid < B) sInv[tid] = nanv;
+  } else {
+    if (warp == 3 && lane < B) {
+      sPiv[lane] = d;
+      sRs[lane] = rsqrt(d);
+    }
+    __syncthreads();
+    // L_ic = a_ic / sqrt(d_c) below the diagonal, L_cc = d_c / sqrt(d_c)
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      acc[m] = (c < row) ? sC[row + c * B] * sRs[c] : ((c == row) ? sPiv[c] * sRs[c] : 0.0);
+    }
+    if (tid < B) sInv[tid] = sRs[tid];
+  }
+  __syncthreads();
+  return bad;
+}
+
+// The tile POTRF of the FP64 kernel: the pivot-warp form up to B = 32, the
+// all-warps form for B = 64 (whose trailing update needs every warp).
+template <int B>
+__device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
+                                         double* sRs, double* sInvd, int* sStat, const uint16_t* sChunk, int row, int q,
+                                         int tid) {
+  if constexpr (B <= 32)
+    return potrf_tile_pw<B>(acc, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
+  else
+    return potrf_tile<B>(acc, sC, sPiv, sInv, sRs, row, q, tid);
 }
 
 // The lower triangle of a B x B tile numbered column by column: entry e of
@@ -402,14 +562,20 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   double* sInv = sL + TILE;
   double* sPiv = sInv + B;
   double* sRs = sPiv + B;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sRs + B);
+  double* sInvd = sRs + B;
+  double* sInvL = sInvd + B;  // 1/L_jj of the diagonal tile a TRSM applies (16-byte aligned)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sInvL + B);
   __shared__ int sTicket, sAbort;
+  constexpr bool PW = B <= 32;  // pivot-warp POTRF
+  __shared__ int sStat[B];
+  __shared__ uint16_t sChunk[PW ? PotrfPw<B>::NCHUNK : 1];
 
   const int tid = threadIdx.x;
   const int row = tid / RPT;
   const int q = tid % RPT;
   const int lane = tid & 31;
   const int row_lane0 = lane - (lane % RPT);  // first lane of this row inside the warp
+  if constexpr (PW) init_chunks<B>(sChunk, tid, 128);
 
   if (tid == 0) {
     for (int s = 0; s <= NSTAGE; ++s) mbar_init(&bars[s], 1);
@@ -605,7 +771,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
 
     if (tk.type == TASK_DIAG) {
-      const int bad = potrf_tile<B>(acc1, sC, sPiv, sInv, sRs, row, q, tid);
+      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col * B + bad + 1);
       double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
@@ -624,8 +790,9 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       } else {
         if (trace) t_ready = globaltimer();
         fence_proxy_async_global();
-        mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
+        mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t((TILE + B) * sizeof(double)));
         tma_load_1d(sL, mc.tiles + size_t(tk.diag) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+        tma_load_1d(sInvL, mc.invdiag + size_t(tk.col) * B, B * sizeof(double), &bars[NSTAGE]);
       }
     }
     __syncthreads();
@@ -639,11 +806,8 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
       phase ^= (1u << NSTAGE);
     }
     double inv[CPT];
-    {
-      const double* iv = mc.invdiag + size_t(tk.col) * B;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) inv[m] = __ldcg(iv + q + RPT * m);
-    }
+    for (int m = 0; m < CPT; ++m) inv[m] = sInvL[q + RPT * m];
     trsm_rows<B>(acc1, inv, sL, q, row_lane0);
     {
       double* dst = mc.tiles + size_t(tk.out) * TILE;
@@ -667,7 +831,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
     }
-    const int bad = potrf_tile<B>(acc2, sC, sPiv, sInv, sRs, row, q, tid);
+    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
     if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
     {
       double* dst = mc.tiles + size_t(tk.out2) * TILE;

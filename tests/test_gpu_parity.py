@@ -243,3 +243,47 @@ def test_nested_dissection_large_workload_logdet_and_solve():
     ld0 = out[st.ORDER_NONE]
     assert abs(out[st.ORDER_ND] - ld0) <= 1e-12 * abs(ld0)
     assert abs(ld0 - 988554.3111446832) <= 1e-12 * ld0  # oracle value at T = 32 (natural order)
+
+
+def test_pivot_reciprocal_error_bound():
+    """The POTRF pivot chains take 1/d from an FP32 seed and one third-order
+    Newton-Raphson step (error e^3 < 2^-66 before rounding): within 2 ulp of
+    the correctly rounded 1/v over the whole normal range, and exactly the IEEE
+    result (0, inf, NaN, subnormal-range quotients) outside it."""
+    rng = np.random.default_rng(7)
+    mant = rng.uniform(1.0, 2.0, 200_000)
+    expo = rng.integers(-1021, 1020, 200_000)
+    v = np.ldexp(mant, expo) * rng.choice([-1.0, 1.0], 200_000)
+    edges = np.array([1.0, 2.0, 1.5, np.nextafter(2.0, 0), np.nextafter(1.0, 2), 3.0, 7.0, 1e-300, 1e300,
+                      np.ldexp(1.0, -1022), np.ldexp(1.999, 1020), np.ldexp(1.0, 1021)])
+    v = np.concatenate([v, edges, -edges])
+    y = st.debug_reciprocal(v)
+    exact = 1.0 / v
+    ulp = np.abs(y - exact) / np.spacing(np.abs(exact))
+    assert ulp.max() <= 2.0, (ulp.max(), v[np.argmax(ulp)])
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, np.ldexp(1.0, 1023), 1.7e308])
+    ys = st.debug_reciprocal(special)
+    with np.errstate(divide="ignore", over="ignore"):
+        np.testing.assert_array_equal(ys, 1.0 / special)
+
+
+@pytest.mark.parametrize("scale", [1e-150, 1e150, 2.0 ** -1000])
+def test_extreme_scales_factor_and_logdet(scale):
+    """s A has factor sqrt(s) L and logdet logdet(A) + n log s: exercised at
+    scales where the squares of the entries would leave the exponent range,
+    for the tile sizes with the pivot-warp POTRF and the all-warps one."""
+    m = inputs.config_small(3)
+    ms = dict(m)
+    ms["values"] = m["values"] * scale
+    for T in (16, 32, 64):
+        plan, f = _gpu(m, T, st.ORDER_RCM, block=T, device_values=False)
+        ld = f.logdet()
+        plan_s, fs = _gpu(ms, T, st.ORDER_RCM, block=T, device_values=False)
+        lds = fs.logdet()
+        n = m["n"]
+        assert abs(lds - (ld + n * math.log(scale))) <= 1e-12 * abs(n * math.log(scale)) + 1e-10 * abs(ld)
+        # entries of the matrix only (the padding past n keeps an unscaled identity)
+        Ls, L = _gpu_tiles_dict(plan_s, fs, n), _gpu_tiles_dict(plan, f, n)
+        big = max(np.abs(t).max() for t in L.values())
+        for key, t in L.items():
+            np.testing.assert_allclose(Ls[key] / math.sqrt(scale), t, rtol=1e-12, atol=1e-12 * big)
