@@ -103,7 +103,8 @@ struct stiles_factor {
   double* tiles = nullptr;    // FP64 path
   double* scratch = nullptr;
   double* invdiag = nullptr;
-  double* linv = nullptr;     // L_kk^{-1} of every diagonal sub-tile (nsb * B * B), for the sweeps
+  double* linv = nullptr;     // L_kk^{-1} of every diagonal sub-tile (nsb * B * B), for the sweeps, then
+                              // the sweeps' folded terms M1 (fwd, bwd), M2 (fwd, bwd): nsb * B * B each
   float* tiles32 = nullptr;   // mixed-precision path
   float* linv32 = nullptr;
   uint16_t* tiles16 = nullptr;
@@ -325,14 +326,14 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&f->linv, size_t(p->nsb) * tile * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->linv, 5 * size_t(p->nsb) * tile * sizeof(double));
   } else {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles16, size_t(p->nsub) * tile * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch32, size_t(nscr) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag32, size_t(p->nsb) * p->B * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->ldiag, size_t(p->nsb) * p->B * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&f->linv32, size_t(p->nsb) * tile * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->linv32, 5 * size_t(p->nsb) * tile * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
@@ -445,6 +446,29 @@ cudaError_t launch_diag_inverse(const stiles_plan* p, stiles_factor* f, cudaStre
         break;
     }
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // then the folded newest term of every sweep task (reads the inverses)
+  const size_t nt = size_t(p->nsb) * p->B * p->B;
+  dev::MlastDesc md{};
+  md.mlast = f->lp ? static_cast<void*>(f->linv32 + nt) : static_cast<void*>(f->linv + nt);
+  md.mlast2 = f->lp ? static_cast<void*>(f->linv32 + 3 * nt) : static_cast<void*>(f->linv + 3 * nt);
+  md.linv = f->lp ? static_cast<const void*>(f->linv32) : static_cast<const void*>(f->linv);
+  md.tiles = f->lp ? static_cast<const void*>(f->tiles32) : static_cast<const void*>(f->tiles);
+  md.ftasks = p->dev->fwd.stasks;
+  md.fpairs = p->dev->fwd.pairs;
+  md.btasks = p->dev->bwd.stasks;
+  md.bpairs = p->dev->bwd.pairs;
+  md.nf = p->dev->fwd.ntasks;
+  md.nb = p->dev->bwd.ntasks;
+  md.nsb = p->nsb;
+  const int gm = std::max(1, std::min(2 * (md.nf + md.nb), 148 * 8));
+  if (f->lp) dev::mlast_kernel<64, float><<<gm, 128, 0, st>>>(md);
+  else switch (p->B) {
+    case 16: dev::mlast_kernel<16, double><<<gm, 128, 0, st>>>(md); break;
+    case 32: dev::mlast_kernel<32, double><<<gm, 128, 0, st>>>(md); break;
+    default: dev::mlast_kernel<64, double><<<gm, 128, 0, st>>>(md); break;
+  }
   return cudaGetLastError();
 }
 
@@ -456,6 +480,8 @@ dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backwar
   c.tiles = tiles;
   c.invdiag = invdiag;
   c.linv = linv;
+  c.mlast = linv + (backward ? 2 : 1) * size_t(p->nsb) * p->B * p->B;
+  c.mlast2 = linv + (backward ? 4 : 3) * size_t(p->nsb) * p->B * p->B;
   c.Y = Y;
   c.nr = nr;
   c.pad0 = 0;
@@ -665,7 +691,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   // inverses of the diagonal blocks for the sweeps (after the kernel's timing window)
   e = launch_diag_inverse(p, f, st);
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("diagonal inverses: ") + cudaGetErrorString(e));
-  count_launch();
+  count_launch(2);
   CUDA_TRY(cudaEventRecord(f->done, st));
   f->pending = true;
   return STILES_OK;
@@ -1145,8 +1171,10 @@ struct stiles_batch {
   double* tiles = nullptr;
   double* scratch = nullptr;
   double* invdiag = nullptr;
-  double* linv = nullptr;       // L_kk^{-1} per diagonal sub-tile, concatenated
+  double* linv = nullptr;       // per matrix: L_kk^{-1} and the sweeps' folded terms (5 nsb B^2)
   void* dinv = nullptr;         // per-matrix BInverse descriptors
+  void* dmlast = nullptr;       // per-matrix MlastDesc descriptors (the sweeps' folded newest terms)
+  int64_t max_stasks = 0;       // largest 2 x (forward + backward sweep tasks) of one matrix
   float* tiles32 = nullptr;
   uint16_t* tiles16 = nullptr;
   float* scratch32 = nullptr;
@@ -1401,6 +1429,7 @@ void free_batch(stiles_batch* b) {
   release(b->linv);
   release(b->linv32);
   release(b->dinv);
+  release(b->dmlast);
   release(b->tiles32);
   release(b->tiles16);
   release(b->scratch32);
@@ -1498,6 +1527,16 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
       case 16: bdiag_inverse_kernel<16, double><<<g, 256, 0, st>>>(di); break;
       case 32: bdiag_inverse_kernel<32, double><<<g, 256, 0, st>>>(di); break;
       default: bdiag_inverse_kernel<64, double><<<g, 256, 0, st>>>(di); break;
+    }
+    CUDA_TRY(cudaGetLastError());
+    const dim3 gm(unsigned(std::max<int64_t>(1, std::min<int64_t>(b->max_stasks, std::max(1, 148 * 8 / count)))),
+                  unsigned(count));
+    const dev::MlastDesc* dm = static_cast<const dev::MlastDesc*>(b->dmlast);
+    if (b->lp) dev::bmlast_kernel<64, float><<<gm, 128, 0, st>>>(dm);
+    else switch (b->B) {
+      case 16: dev::bmlast_kernel<16, double><<<gm, 128, 0, st>>>(dm); break;
+      case 32: dev::bmlast_kernel<32, double><<<gm, 128, 0, st>>>(dm); break;
+      default: dev::bmlast_kernel<64, double><<<gm, 128, 0, st>>>(dm); break;
     }
     CUDA_TRY(cudaGetLastError());
   }
@@ -1803,13 +1842,13 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->tiles, size_t(b->tile_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->scratch, size_t(b->scratch_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->invdiag, size_t(b->diag_elems));
-  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->linv, size_t(b->diag_elems) * b->B);
+  if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->linv, 5 * size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles16, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->invdiag32, size_t(b->diag_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->ldiag, size_t(b->diag_elems));
-  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->linv32, size_t(b->diag_elems) * b->B);
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->linv32, 5 * size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess) e = batch_alloc(b, &b->flags, size_t(b->flag_total));
   if (e == cudaSuccess) e = batch_alloc(b, &b->infos, size_t(count));
   if (e == cudaSuccess) e = batch_alloc(b, &b->ctl, 1);
@@ -1827,6 +1866,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   std::vector<dev::LPMatCtx> lmats;
   std::vector<BatchLogCtx> logs(count);
   std::vector<BInverse> binv(count);
+  std::vector<dev::MlastDesc> bml(count);
   for (int i = 0; i < count; ++i) {
     const stiles_plan* p = plans[i];
     stiles_factor* v = new (std::nothrow) stiles_factor();
@@ -1844,13 +1884,13 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       v->tiles16 = b->tiles16 + t_off[i];
       v->scratch32 = b->scratch32 + s_off[i];
       v->invdiag32 = b->invdiag32 + d_off[i];
-      v->linv32 = b->linv32 + d_off[i] * b->B;
+      v->linv32 = b->linv32 + 5 * d_off[i] * b->B;
       v->ldiag = b->ldiag + d_off[i];
     } else {
       v->tiles = b->tiles + t_off[i];
       v->scratch = b->scratch + s_off[i];
       v->invdiag = b->invdiag + d_off[i];
-      v->linv = b->linv + d_off[i] * b->B;
+      v->linv = b->linv + 5 * d_off[i] * b->B;
     }
     // the view's small arrays are slices of batch-wide ones; a view never
     // factorizes, so it has no events
@@ -1865,11 +1905,28 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
                        b->lp ? static_cast<const void*>(v->invdiag32) : static_cast<const void*>(v->invdiag),
                        p->dev->diag_sub, p->nsb};
     b->max_nsb = std::max<int64_t>(b->max_nsb, p->nsb);
+    {
+      dev::MlastDesc& md = bml[i];
+      const size_t nt = size_t(p->nsb) * b->B * b->B;
+      md.mlast = b->lp ? static_cast<void*>(v->linv32 + nt) : static_cast<void*>(v->linv + nt);
+      md.mlast2 = b->lp ? static_cast<void*>(v->linv32 + 3 * nt) : static_cast<void*>(v->linv + 3 * nt);
+      md.linv = binv[i].linv;
+      md.tiles = binv[i].tiles;
+      md.ftasks = p->dev->fwd.stasks;
+      md.fpairs = p->dev->fwd.pairs;
+      md.btasks = p->dev->bwd.stasks;
+      md.bpairs = p->dev->bwd.pairs;
+      md.nf = p->dev->fwd.ntasks;
+      md.nb = p->dev->bwd.ntasks;
+      md.nsb = p->nsb;
+      b->max_stasks = std::max<int64_t>(b->max_stasks, 2 * (int64_t(md.nf) + md.nb));
+    }
   }
   if (b->lp) e = batch_upload(b, reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
   else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BInverse**>(&b->dinv), binv);
+  if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<dev::MlastDesc**>(&b->dmlast), bml);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   std::vector<int64_t> lens(count);
   for (int i = 0; i < count; ++i) lens[i] = int64_t(plans[i]->graph.tasks.size());
@@ -1932,7 +1989,7 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(4);  // scatter, init, persistent kernel, diagonal inverses
+  count_launch(5);  // scatter, init, persistent kernel, diagonal inverses, folded sweep terms
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));

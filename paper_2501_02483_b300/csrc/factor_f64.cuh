@@ -530,25 +530,27 @@ __device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int*
   return bad;
 }
 
-// X L^T = acc, column by column (inv = 1/L_jj of this thread's columns); the
-// solved x_ij is broadcast to the row's RPT lanes with a shuffle.
+// X L^T = acc, column by column, with L's columns pre-scaled by 1/L_jj (sLs:
+// L_cj / L_jj below the diagonal) so that the dependency chain of a column is
+// a shuffle and one FMA: the unscaled y_j = x_j L_jj is broadcast to the row's
+// RPT lanes, and x = y / L_jj is taken for every column at the end
+// (inv = 1/L_jj of this thread's columns).
 template <int B>
 __device__ __forceinline__ void trsm_rows(double (&acc)[FactorCfg<B>::CPT], const double (&inv)[FactorCfg<B>::CPT],
-                                          const double* sL, int q, int row_lane0) {
+                                          const double* sLs, int q, int row_lane0) {
   constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     const int mj = j / RPT;
-    const bool owner = (q == j % RPT);
-    double x = owner ? acc[mj] * inv[mj] : 0.0;
-    x = __shfl_sync(0xffffffffu, x, row_lane0 + (j % RPT));
-    if (owner) acc[mj] = x;
+    const double y = __shfl_sync(0xffffffffu, acc[mj], row_lane0 + (j % RPT));
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
       const int c = q + RPT * m;
-      if (c > j) acc[m] = fma(-x, sL[c + j * B], acc[m]);
+      if (c > j) acc[m] = fma(-y, sLs[c + j * B], acc[m]);
     }
   }
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) acc[m] *= inv[m];
 }
 
 template <int B>
@@ -606,6 +608,9 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   int next = 0;
   if (tid == 0) next = atomicAdd(counter, 1);
   while (true) {
+    // generic-proxy writes of the previous task to shared buffers that TMA
+    // refills (in-place scaling, reused stage areas) before the next copies
+    fence_proxy_async_shared();
     if (tid == 0) {
       int cur = next;
       if (cur < nqueue && ld_volatile(&a.ctl->abort) == 0) {
@@ -808,6 +813,12 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     double inv[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) inv[m] = sInvL[q + RPT * m];
+    // L_kk's columns scaled by 1/L_jj below the diagonal, in place
+    for (int e = tid; e < TILE; e += 128) {
+      const int c = e % B, j = e / B;
+      if (c > j) sL[e] *= sInvL[j];
+    }
+    __syncthreads();
     trsm_rows<B>(acc1, inv, sL, q, row_lane0);
     {
       double* dst = mc.tiles + size_t(tk.out) * TILE;

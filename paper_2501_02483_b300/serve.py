@@ -113,8 +113,12 @@ class Server:
     @staticmethod
     def _bytes(plan):
         inf = plan.info()
-        # tiles (FP32 + 16-bit copy, or FP64) + values + flags + solve workspace, per matrix
-        return float(inf["factor_bytes"]) + 8.0 * inf["nnz"] + 4.0 * inf["nsub"] + 48.0 * MAX_RHS * inf["n"]
+        # tiles (FP32 + 16-bit copy, or FP64) + values + flags + solve workspace + the diagonal
+        # inverses and the sweeps' folded terms (5 B^2 per diagonal sub-tile), per matrix
+        B = inf["block"]
+        nsb = -(-inf["n"] // B)
+        return (float(inf["factor_bytes"]) + 8.0 * inf["nnz"] + 4.0 * inf["nsub"] + 48.0 * MAX_RHS * inf["n"]
+                + 40.0 * nsb * B * B)
 
     # -- residency (callers hold self.lock) ----------------------------------
     def _evict_until(self, need):
