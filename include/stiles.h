@@ -281,11 +281,6 @@ stiles_status stiles_autotune(int64_t n, const int64_t* colptr, const int32_t* r
  * on every SM, timed with CUDA events), used as the roofline denominator of the FP64 path. */
 stiles_status stiles_probe_fp64_peak(double* tflops);
 
-/* Diagnostic: out[i] = the reciprocal of v[i] as the POTRF pivot chains compute it (an FP32
- * seed refined by one third-order Newton-Raphson step; the IEEE division outside the normal
- * range).  v and out are HOST arrays of n doubles; the values go through device memory on
- * the default stream.  Lets a test bound the error of that reciprocal against exact division. */
-stiles_status stiles_debug_reciprocal(const double* v, double* out, int64_t n);
 
 #ifdef __cplusplus
 }

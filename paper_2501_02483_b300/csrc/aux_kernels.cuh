@@ -361,11 +361,5 @@ __global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
   if (s == 1.2345678e300) out[0] = s;
 }
 
-// out[i] = fast_rcp(v[i]) (diagnostic: the reciprocal of the POTRF pivot chains).
-__global__ void reciprocal_kernel(const double* v, double* out, int64_t n) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    out[i] = fast_rcp(v[i]);
-}
-
 }  // namespace dev
 }  // namespace stiles

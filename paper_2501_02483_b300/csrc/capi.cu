@@ -1125,25 +1125,6 @@ stiles_status stiles_probe_fp64_peak(double* tflops) {
   return STILES_OK;
 }
 
-stiles_status stiles_debug_reciprocal(const double* v, double* out, int64_t n) {
-  if (n < 0 || (n > 0 && (!v || !out))) return fail(STILES_ERR_INVALID, "bad argument");
-  if (n == 0) return STILES_OK;
-  double* d = nullptr;
-  CUDA_TRY(cudaMalloc(&d, size_t(n) * 2 * sizeof(double)));
-  cudaError_t e = cudaMemcpy(d, v, size_t(n) * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    const int threads = 256;
-    const int blocks = int(std::min<int64_t>((n + threads - 1) / threads, 65535));
-    dev::reciprocal_kernel<<<blocks, threads>>>(d, d + n, n);
-    count_launch();
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(out, d + n, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, cudaGetErrorString(e));
-  return STILES_OK;
-}
-
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -110,35 +110,5 @@ __device__ __forceinline__ void raise_timeout(Ctl* ctl, long long where) {
   atomicExch(&ctl->abort, 1);
 }
 
-// Reciprocal of a double on the pivot chain of the POTRFs, where the latency
-// of an IEEE division is the cost that matters.  Newton-Raphson refinement of
-// a single-precision seed, using the third-order member of the classical
-// reciprocal iteration, y' = y (1 + e + e^2) with e = 1 - v y, which cubes the
-// relative error (e' = e^3):
-//   * the seed is rcp.approx.ftz.f32 (at most 1 ulp, i.e. 2^-23 relative) of
-//     the mantissa of v as a float in [1, 2) (truncated to 23 bits, another
-//     2^-23), rescaled by 2^-(exponent of v) with integer arithmetic, so the
-//     seed error is below 2^-22 for every normal v without a float range limit;
-//   * one third-order step leaves |e|^3 < 2^-66, below the final rounding, so
-//     the result is within a few units in the last place of 1/v.
-// Positive or negative normal v with a biased exponent in [1, 2044]; anything
-// else (zero, subnormal, huge, inf, NaN) takes the IEEE division.
-__device__ __forceinline__ double fast_rcp(double v) {
-  const int hi = __double2hiint(v);
-  const unsigned lo = static_cast<unsigned>(__double2loint(v));
-  const int ex = (hi >> 20) & 0x7ff;
-  if (ex < 1 || ex > 2044) return 1.0 / v;
-  const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3) | int(lo >> 29));
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // r in (0.5, 1]
-  const int rb = __float_as_int(r);
-  // r = 2^(er - 127) * 1.f  ->  1/v ~ 2^(er - 127 - (ex - 1023)) * 1.f
-  const int yex = ((rb >> 23) & 0xff) - 127 + 1023 - (ex - 1023);
-  const int yhi = (hi & int(0x80000000u)) | (yex << 20) | ((rb & 0x7fffff) >> 3);
-  double y = __hiloint2double(yhi, rb << 29);
-  const double e = fma(-v, y, 1.0);
-  return fma(y, fma(e, e, e), y);
-}
-
 }  // namespace dev
 }  // namespace stiles

@@ -34,7 +34,7 @@ struct FactorCfg {
   static constexpr int CPT = B / RPT; // columns per thread
   static constexpr int TILE = B * B;
   static constexpr int NSTAGE = (B == 64) ? 2 : 3;
-  // stages | sC | sL | sInv, sPiv, sRs, sInvd, sInvL (B each; sInvL is a TMA target)
+  // stages | sC | sL | sInv, sPiv, sRs, sK (B ints in B doubles), sInvL (B each; sInvL is a TMA target)
   static constexpr size_t SMEM_DOUBLES = size_t(NSTAGE) * 2 * TILE + 2 * TILE + 5 * B;
   static constexpr size_t SMEM = SMEM_DOUBLES * sizeof(double) + (NSTAGE + 1) * sizeof(uint64_t) + 16;
 };
@@ -154,89 +154,93 @@ __device__ __forceinline__ int potrf_tile(double (&acc)[FactorCfg<B>::CPT], doub
   return bad;
 }
 
-// Strictly-lower elements of a B x B tile cut into row chunks of PW_CS
-// columns: row i (1 <= i < B) holds chunks (i, 0), (i, PW_CS), ... below the
-// diagonal.  Entry k of the chunk table is (i << 8) | c0.  Filled once per CTA.
-constexpr int PW_CS = 2;
+// The elements of a B x B tile that a POTRF updates (columns 1..B-1, on and
+// below the diagonal), numbered column by column: entry t of the table is
+// (i << 8) | c, held by thread t % 128 in register slot t / 128.  Column-major
+// numbering makes the live elements of step j (c > j) a suffix, so finished
+// warps skip whole steps.  Filled once per CTA.
 template <int B>
-struct PotrfPw {
-  static constexpr int NCHUNK = [] {
-    int n = 0;
-    for (int i = 1; i < B; ++i) n += (i + PW_CS - 1) / PW_CS;
-    return n;
-  }();
-  static constexpr int NUPD = 96;                       // warps 0-2 update, warp 3 pivots
-  static constexpr int NCH = (NCHUNK + NUPD - 1) / NUPD;  // chunks per update thread
+struct PotrfDf {
+  static constexpr int NLIVE = B * (B - 1) / 2;
+  static constexpr int NE = (NLIVE + 127) / 128;  // elements per thread
 };
 
 template <int B>
-__device__ __forceinline__ void init_chunks(uint16_t* sChunk, int tid, int nthreads) {
-  for (int k = tid; k < PotrfPw<B>::NCHUNK; k += nthreads) {
-    int i = 1, kk = k;
-    while (kk >= (i + PW_CS - 1) / PW_CS) {
-      kk -= (i + PW_CS - 1) / PW_CS;
-      ++i;
+__device__ __forceinline__ void init_df_elements(uint16_t* sElem, int tid, int nthreads) {
+  for (int t = tid; t < PotrfDf<B>::NLIVE; t += nthreads) {
+    int c = 1, off = 0;
+    while (off + (B - c) <= t) {
+      off += B - c;
+      ++c;
     }
-    sChunk[k] = uint16_t((i << 8) | (kk * PW_CS));
+    sElem[t] = uint16_t(((c + t - off) << 8) | c);
   }
 }
 
-// POTRF of a B x B FP64 tile (B <= 32) held in `acc` (row-quad layout), in
-// the LDL^T form of the right-looking algorithm with the pivots on their own
-// warp, so that the dependency chain of a step is one FMA and one reciprocal:
+// POTRF of a B x B FP64 tile (B <= 32), division-free on the dependency chain.
 //
-//   warp 3 holds the diagonal (lane i: d_i).  At step j it applies column j
-//     to the diagonal, d_i -= (a_ij / d_j) a_ij (in this order: a_ij^2 could
-//     leave the exponent range where the tile's entries do not), and takes
-//     1/d_{j+1} (fast_rcp) for the next step;
-//   warps 0-2 hold the strictly lower elements in registers, in row chunks,
-//     and apply step j, a_ic -= (a_ij / d_j) a_cj (c > j); the elements of
-//     column j+1 are then final and go to sC.
+// Right-looking elimination scaled so that no division is needed until the
+// end: with the pivot a_jj = m_j 2^e_j (m_j in [1, 2)), step j replaces every
+// trailing element (diagonal included) by
+//     a_ic <- m_j a_ic - (a_ij 2^-e_j) a_cj          (j < c <= i),
+// i.e. 2^-e_j (a_jj a_ic - a_ij a_cj): the trailing matrix stays the Schur
+// complement times sigma_{j+1} = m_0 ... m_j, which grows by less than 2 per
+// step.  A step is two multiplies and one FMA per element, with no reciprocal
+// on the chain; at the end
+//     L_ic = a_ic / sqrt(sigma_c a_cc),   L_cc = sqrt(a_cc / sigma_c).
+// Beforehand the tile is equilibrated by powers of two, a_ic 2^-(k_i + k_c)
+// with k_i = floor(log2(a_ii) / 2) (exact), so that the products stay in range
+// whatever the tile's scale; L is scaled back by 2^k_i at the end.
 //
-// One barrier per step.  The factor is L_ic = a_ic / sqrt(d_c), taken at the
-// end (the reciprocal square roots of all pivots in parallel, off the chain).
-// sStat[j] flags pivot j as bad (<= 0 or NaN); each flag is written one step
-// before it is read, so every warp leaves the loop at the same step.
-// Returns the first bad pivot (the tile is then NaN) or -1; sInv receives
-// 1/L_jj.  Shared scratch: sC (B x B), sPiv, sRs, sInvd (B each), sStat (B
-// ints), sChunk (the chunk table).
+// Every thread holds its elements (sElem) in registers and publishes an
+// element to sC when it becomes final (column j+1 after step j; a diagonal one
+// also as the next pivot, sPiv).  One barrier per step; sStat[j] flags pivot j
+// as bad (not a positive normal number below 2^1022), written one step before
+// every thread reads it.  Returns the first bad pivot (the tile is then NaN) or
+// -1; sInv receives 1/L_jj.  Shared scratch: sC (B x B), sPiv, sRs, sInv (B
+// each), sK, sStat (B ints), sElem.
 template <int B>
-__device__ __forceinline__ int potrf_tile_pw(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv,
-                                             double* sInv, double* sRs, double* sInvd, int* sStat,
-                                             const uint16_t* sChunk, int row, int q, int tid) {
-  static_assert(B <= 32, "one pivot per lane of the pivot warp");
+__device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv,
+                                             double* sInv, double* sRs, int* sK, int* sStat, const uint16_t* sElem,
+                                             int row, int q, int tid) {
+  static_assert(B <= 32, "one warp scans the pivots");
   constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
-  constexpr int NCH = PotrfPw<B>::NCH, NCHUNK = PotrfPw<B>::NCHUNK, NUPD = PotrfPw<B>::NUPD;
-  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int NE = PotrfDf<B>::NE, NLIVE = PotrfDf<B>::NLIVE;
+  auto pow2 = [](int e) { return __longlong_as_double((long long)(1023 + e) << 52); };  // 2^e, |e| <= 1022
+  auto pivot_ok = [](double v) {
+    const long long b = __double_as_longlong(v);
+    return b >= (1LL << 52) && b < (2046LL << 52);
+  };
 #pragma unroll
   for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
   if (tid < B) sStat[tid] = 0;
   __syncthreads();
-
-  double d = 1.0;  // pivot warp: d_lane (lanes >= B keep 1)
-  double a[NCH][PW_CS];
-  int ci[NCH], c0[NCH];
-  if (warp == 3) {
-    if (lane < B) d = sC[lane * (B + 1)];
-    const double r = fast_rcp(lane == 0 ? d : 1.0);
-    if (lane == 0) {
-      sInvd[0] = r;
-      const long long bits = __double_as_longlong(d);
-      if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) sStat[0] = 1;
+  if (tid < B) {  // equilibration exponents
+    const double v = sC[tid * (B + 1)];
+    sK[tid] = pivot_ok(v) ? ((int(__double_as_longlong(v) >> 52) - 1023) >> 1) : 0;
+  }
+  __syncthreads();
+  double a[NE];
+  int ei[NE], ec[NE];
+#pragma unroll
+  for (int u = 0; u < NE; ++u) {
+    const int t = tid + 128 * u;
+    ei[u] = 0;
+    ec[u] = B;  // no element: never live
+    a[u] = 0.0;
+    if (t < NLIVE) {
+      const int v = sElem[t];
+      ei[u] = v >> 8;
+      ec[u] = v & 255;
+      a[u] = sC[ei[u] + ec[u] * B] * pow2(-(sK[ei[u]] + sK[ec[u]]));
     }
-  } else {
-#pragma unroll
-    for (int u = 0; u < NCH; ++u) {
-      const int k = tid + NUPD * u;
-      ci[u] = 0;
-      c0[u] = B;  // no chunk: never live
-      if (k < NCHUNK) {
-        const int v = sChunk[k];
-        ci[u] = v >> 8;
-        c0[u] = v & 255;
-      }
-#pragma unroll
-      for (int e = 0; e < PW_CS; ++e) a[u][e] = (c0[u] + e < ci[u]) ? sC[ci[u] + (c0[u] + e) * B] : 0.0;
+  }
+  if (tid < B) {  // column 0 is final from the start
+    const double v = sC[tid] * pow2(-(sK[tid] + sK[0]));
+    sC[tid] = v;
+    if (tid == 0) {
+      sPiv[0] = v;
+      if (!pivot_ok(v)) sStat[0] = 1;
     }
   }
   __syncthreads();
@@ -247,30 +251,23 @@ __device__ __forceinline__ int potrf_tile_pw(double (&acc)[FactorCfg<B>::CPT], d
       bad = j;
       break;
     }
-    if (warp == 3) {
-      const double aij = sC[(lane < B ? lane : 0) + j * B];
-      const double invj = sInvd[j];
-      if (lane > j && lane < B) d = fma(-(aij * invj), aij, d);
-      const double r = fast_rcp(lane == j + 1 ? d : 1.0);
-      if (lane == j + 1) {
-        sInvd[j + 1] = r;
-        const long long bits = __double_as_longlong(d);
-        if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) sStat[j + 1] = 1;
-      }
-    } else {
-      const double invj = sInvd[j];
+    if (ec[NE - 1] > j) {  // this thread still has a live element (the last slot is the latest column)
+      const long long pb = __double_as_longlong(sPiv[j]);
+      const double pj = __longlong_as_double((2046LL - (pb >> 52)) << 52);                 // 2^-e_j
+      const double mj = __longlong_as_double((pb & 0x000fffffffffffffLL) | (1023LL << 52));  // m_j
 #pragma unroll
-      for (int u = 0; u < NCH; ++u) {
-        const int i = ci[u], cb = c0[u];
-        // live: some column c of the chunk with j < c < i
-        if (max(cb, j + 1) < min(cb + PW_CS, i)) {
-          const double tr = sC[i + j * B] * invj;
-#pragma unroll
-          for (int e = 0; e < PW_CS; ++e)
-            if (cb + e > j && cb + e < i) a[u][e] = fma(-tr, sC[cb + e + j * B], a[u][e]);
-#pragma unroll
-          for (int e = 0; e < PW_CS; ++e)
-            if (cb + e == j + 1) sC[i + (j + 1) * B] = a[u][e];  // column j+1 is final
+      for (int u = 0; u < NE; ++u) {
+        const int i = ei[u], c = ec[u];
+        if (c > j) {
+          const double g = sC[i + j * B] * pj;
+          a[u] = fma(-g, sC[c + j * B], mj * a[u]);
+          if (c == j + 1) {  // final: publish (the diagonal one is the next pivot)
+            sC[i + c * B] = a[u];
+            if (i == c) {
+              sPiv[c] = a[u];
+              if (!pivot_ok(a[u])) sStat[c] = 1;
+            }
+          }
         }
       }
     }
@@ -284,31 +281,45 @@ __device__ __forceinline__ int potrf_tile_pw(double (&acc)[FactorCfg<B>::CPT], d
     for (int m = 0; m < CPT; ++m) acc[m] = nanv;
     if (tid < B) sInv[tid] = nanv;
   } else {
-    if (warp == 3 && lane < B) {
-      sPiv[lane] = d;
-      sRs[lane] = rsqrt(d);
+    if (tid < 32) {
+      // sigma_c = m_0 ... m_{c-1}: exclusive product scan over the pivots' mantissas
+      const double pv = sPiv[tid < B ? tid : 0];
+      const double mc = __longlong_as_double((__double_as_longlong(pv) & 0x000fffffffffffffLL) | (1023LL << 52));
+      const double up = __shfl_up_sync(0xffffffffu, mc, 1);  // every lane takes part
+      double sg = (tid >= 1 && tid < B) ? up : 1.0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double x = __shfl_up_sync(0xffffffffu, sg, o);
+        if (tid >= o) sg *= x;
+      }
+      if (tid < B) {
+        const double r = rsqrt(sg * pv);  // 1 / sqrt(sigma_c a_cc)
+        const int k = sK[tid];
+        sRs[tid] = r;
+        sInv[tid] = sg * r * pow2(-k);  // 1 / L_cc
+        sPiv[tid] = pv * r * pow2(k);   // L_cc
+      }
     }
     __syncthreads();
-    // L_ic = a_ic / sqrt(d_c) below the diagonal, L_cc = d_c / sqrt(d_c)
+    const double sr = pow2(sK[row]);
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
       const int c = q + RPT * m;
-      acc[m] = (c < row) ? sC[row + c * B] * sRs[c] : ((c == row) ? sPiv[c] * sRs[c] : 0.0);
+      acc[m] = (c < row) ? sC[row + c * B] * sRs[c] * sr : ((c == row) ? sPiv[c] : 0.0);
     }
-    if (tid < B) sInv[tid] = sRs[tid];
   }
   __syncthreads();
   return bad;
 }
 
-// The tile POTRF of the FP64 kernel: the pivot-warp form up to B = 32, the
-// all-warps form for B = 64 (whose trailing update needs every warp).
+// The tile POTRF of the FP64 kernel: the division-free form up to B = 32, the
+// all-warps reciprocal form for B = 64.
 template <int B>
 __device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
-                                         double* sRs, double* sInvd, int* sStat, const uint16_t* sChunk, int row, int q,
+                                         double* sRs, int* sK, int* sStat, const uint16_t* sElem, int row, int q,
                                          int tid) {
   if constexpr (B <= 32)
-    return potrf_tile_pw<B>(acc, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
+    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
   else
     return potrf_tile<B>(acc, sC, sPiv, sInv, sRs, row, q, tid);
 }
@@ -564,20 +575,20 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   double* sInv = sL + TILE;
   double* sPiv = sInv + B;
   double* sRs = sPiv + B;
-  double* sInvd = sRs + B;
-  double* sInvL = sInvd + B;  // 1/L_jj of the diagonal tile a TRSM applies (16-byte aligned)
+  int* sK = reinterpret_cast<int*>(sRs + B);  // equilibration exponents of the POTRF
+  double* sInvL = sRs + 2 * B;                 // 1/L_jj of the diagonal tile a TRSM applies (16-byte aligned)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sInvL + B);
   __shared__ int sTicket, sAbort;
-  constexpr bool PW = B <= 32;  // pivot-warp POTRF
+  constexpr bool PW = B <= 32;  // division-free POTRF
   __shared__ int sStat[B];
-  __shared__ uint16_t sChunk[PW ? PotrfPw<B>::NCHUNK : 1];
+  __shared__ uint16_t sElem[PW ? PotrfDf<B>::NLIVE : 1];
 
   const int tid = threadIdx.x;
   const int row = tid / RPT;
   const int q = tid % RPT;
   const int lane = tid & 31;
   const int row_lane0 = lane - (lane % RPT);  // first lane of this row inside the warp
-  if constexpr (PW) init_chunks<B>(sChunk, tid, 128);
+  if constexpr (PW) init_df_elements<B>(sElem, tid, 128);
 
   if (tid == 0) {
     for (int s = 0; s <= NSTAGE; ++s) mbar_init(&bars[s], 1);
@@ -776,7 +787,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
 
     if (tk.type == TASK_DIAG) {
-      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
+      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col * B + bad + 1);
       double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
@@ -842,7 +853,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
     }
-    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sInvd, sStat, sChunk, row, q, tid);
+    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
     if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
     {
       double* dst = mc.tiles + size_t(tk.out2) * TILE;

@@ -17,7 +17,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
 
 import numpy as np
 
-__all__ = ["Plan", "Factor", "Batch", "autotune", "StilesError", "lib", "probe_fp64_peak", "debug_reciprocal", "kernel_launches", "ORDER_NONE", "ORDER_RCM", "ORDER_AUTO", "ORDER_ND",
+__all__ = ["Plan", "Factor", "Batch", "autotune", "StilesError", "lib", "probe_fp64_peak", "kernel_launches", "ORDER_NONE", "ORDER_RCM", "ORDER_AUTO", "ORDER_ND",
            "PREC_F64", "PREC_BF16", "PREC_F16", "LIB_PATH"]
 
 ORDER_NONE, ORDER_RCM, ORDER_AUTO, ORDER_ND = 0, 1, 2, 3
@@ -73,7 +73,6 @@ def lib():
         L.stiles_last_error.argtypes = []
         L.stiles_last_error.restype = c_char_p
         L.stiles_probe_fp64_peak.argtypes = [POINTER(c_double)]
-        L.stiles_debug_reciprocal.argtypes = [P, P, c_int64]
         L.stiles_factor_timing.argtypes = [P, POINTER(c_double), POINTER(c_double)]
         L.stiles_factor_set_trace.argtypes = [P, c_int32]
         L.stiles_factor_get_trace.argtypes = [P, c_int32, P, POINTER(c_int64)]
@@ -436,12 +435,3 @@ def probe_fp64_peak():
     out = c_double(0.0)
     _check(lib().stiles_probe_fp64_peak(ctypes.byref(out)))
     return out.value
-
-
-def debug_reciprocal(v):
-    """The pivot-chain reciprocal of every element of the float64 array ``v``
-    (diagnostic, host arrays)."""
-    v = np.ascontiguousarray(v, dtype=np.float64)
-    out = np.empty_like(v)
-    _check(lib().stiles_debug_reciprocal(v.ctypes.data, out.ctypes.data, v.size))
-    return out
