@@ -194,15 +194,15 @@ __device__ __forceinline__ void init_df_elements(uint16_t* sElem, int tid, int n
 //
 // Every thread holds its elements (sElem) in registers and publishes an
 // element to sC when it becomes final (column j+1 after step j; a diagonal one
-// also as the next pivot, sPiv).  One barrier per step; sStat[j] flags pivot j
-// as bad (not a positive normal number below 2^1022), written one step before
-// every thread reads it.  Returns the first bad pivot (the tile is then NaN) or
-// -1; sInv receives 1/L_jj.  Shared scratch: sC (B x B), sPiv, sRs, sInv (B
-// each), sK, sStat (B ints), sElem.
+// also as the next pivot, sPiv).  One barrier per step; every thread reads
+// pivot j after the barrier that follows its publication and stops at the
+// first bad one (not a positive normal number below 2^1022).  Returns that
+// pivot (the tile is then NaN) or -1; sInv receives 1/L_jj.  Shared scratch:
+// sC (B x B), sPiv, sRs, sInv (B each), sK (B ints), sElem.
 template <int B>
 __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv,
-                                             double* sInv, double* sRs, int* sK, int* sStat, const uint16_t* sElem,
-                                             int row, int q, int tid) {
+                                             double* sInv, double* sRs, int* sK, const uint16_t* sElem, int row,
+                                             int q, int tid) {
   static_assert(B <= 32, "one warp scans the pivots");
   constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
   constexpr int NE = PotrfDf<B>::NE, NLIVE = PotrfDf<B>::NLIVE;
@@ -213,7 +213,6 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
   };
 #pragma unroll
   for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
-  if (tid < B) sStat[tid] = 0;
   __syncthreads();
   if (tid < B) {  // equilibration exponents
     const double v = sC[tid * (B + 1)];
@@ -238,21 +237,20 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
   if (tid < B) {  // column 0 is final from the start
     const double v = sC[tid] * pow2(-(sK[tid] + sK[0]));
     sC[tid] = v;
-    if (tid == 0) {
-      sPiv[0] = v;
-      if (!pivot_ok(v)) sStat[0] = 1;
-    }
+    if (tid == 0) sPiv[0] = v;
   }
   __syncthreads();
 
   int bad = -1;
   for (int j = 0; j + 1 < B; ++j) {
-    if (sStat[j]) {
+    // every thread reads the pivot (published before the barrier) and checks it
+    const double piv = sPiv[j];
+    if (!pivot_ok(piv)) {
       bad = j;
       break;
     }
     if (ec[NE - 1] > j) {  // this thread still has a live element (the last slot is the latest column)
-      const long long pb = __double_as_longlong(sPiv[j]);
+      const long long pb = __double_as_longlong(piv);
       const double pj = __longlong_as_double((2046LL - (pb >> 52)) << 52);                 // 2^-e_j
       const double mj = __longlong_as_double((pb & 0x000fffffffffffffLL) | (1023LL << 52));  // m_j
 #pragma unroll
@@ -263,17 +261,14 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
           a[u] = fma(-g, sC[c + j * B], mj * a[u]);
           if (c == j + 1) {  // final: publish (the diagonal one is the next pivot)
             sC[i + c * B] = a[u];
-            if (i == c) {
-              sPiv[c] = a[u];
-              if (!pivot_ok(a[u])) sStat[c] = 1;
-            }
+            if (i == c) sPiv[c] = a[u];
           }
         }
       }
     }
     __syncthreads();
   }
-  if (bad < 0 && sStat[B - 1]) bad = B - 1;
+  if (bad < 0 && !pivot_ok(sPiv[B - 1])) bad = B - 1;
 
   if (bad >= 0) {
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
@@ -316,10 +311,10 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
 // all-warps reciprocal form for B = 64.
 template <int B>
 __device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
-                                         double* sRs, int* sK, int* sStat, const uint16_t* sElem, int row, int q,
+                                         double* sRs, int* sK, const uint16_t* sElem, int row, int q,
                                          int tid) {
   if constexpr (B <= 32)
-    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
+    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
   else
     return potrf_tile<B>(acc, sC, sPiv, sInv, sRs, row, q, tid);
 }
@@ -580,7 +575,6 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(sInvL + B);
   __shared__ int sTicket, sAbort;
   constexpr bool PW = B <= 32;  // division-free POTRF
-  __shared__ int sStat[B];
   __shared__ uint16_t sElem[PW ? PotrfDf<B>::NLIVE : 1];
 
   const int tid = threadIdx.x;
@@ -787,7 +781,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
 
     if (tk.type == TASK_DIAG) {
-      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
+      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col * B + bad + 1);
       double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
@@ -853,7 +847,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
     }
-    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sStat, sElem, row, q, tid);
+    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
     if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
     {
       double* dst = mc.tiles + size_t(tk.out2) * TILE;
