@@ -333,7 +333,7 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch32, size_t(nscr) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag32, size_t(p->nsb) * p->B * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->ldiag, size_t(p->nsb) * p->B * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&f->linv32, 5 * size_t(p->nsb) * tile * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->linv32, size_t(p->nsb) * tile * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
@@ -447,14 +447,14 @@ cudaError_t launch_diag_inverse(const stiles_plan* p, stiles_factor* f, cudaStre
     }
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // then the folded newest term of every sweep task (reads the inverses)
+  if (e != cudaSuccess || f->lp) return e;
+  // then the folded newest terms of every sweep task (reads the inverses; FP64 factors)
   const size_t nt = size_t(p->nsb) * p->B * p->B;
   dev::MlastDesc md{};
-  md.mlast = f->lp ? static_cast<void*>(f->linv32 + nt) : static_cast<void*>(f->linv + nt);
-  md.mlast2 = f->lp ? static_cast<void*>(f->linv32 + 3 * nt) : static_cast<void*>(f->linv + 3 * nt);
-  md.linv = f->lp ? static_cast<const void*>(f->linv32) : static_cast<const void*>(f->linv);
-  md.tiles = f->lp ? static_cast<const void*>(f->tiles32) : static_cast<const void*>(f->tiles);
+  md.mlast = f->linv + nt;
+  md.mlast2 = f->linv + 3 * nt;
+  md.linv = f->linv;
+  md.tiles = f->tiles;
   md.ftasks = p->dev->fwd.stasks;
   md.fpairs = p->dev->fwd.pairs;
   md.btasks = p->dev->bwd.stasks;
@@ -463,8 +463,7 @@ cudaError_t launch_diag_inverse(const stiles_plan* p, stiles_factor* f, cudaStre
   md.nb = p->dev->bwd.ntasks;
   md.nsb = p->nsb;
   const int gm = std::max(1, std::min(2 * (md.nf + md.nb), 148 * 8));
-  if (f->lp) dev::mlast_kernel<64, float><<<gm, 128, 0, st>>>(md);
-  else switch (p->B) {
+  switch (p->B) {
     case 16: dev::mlast_kernel<16, double><<<gm, 128, 0, st>>>(md); break;
     case 32: dev::mlast_kernel<32, double><<<gm, 128, 0, st>>>(md); break;
     default: dev::mlast_kernel<64, double><<<gm, 128, 0, st>>>(md); break;
@@ -480,8 +479,11 @@ dev::SolveCtx<TF> solve_ctx(const stiles_plan* p, stiles_factor* f, bool backwar
   c.tiles = tiles;
   c.invdiag = invdiag;
   c.linv = linv;
-  c.mlast = linv + (backward ? 2 : 1) * size_t(p->nsb) * p->B * p->B;
-  c.mlast2 = linv + (backward ? 4 : 3) * size_t(p->nsb) * p->B * p->B;
+  // folded sweep terms for FP64 factors only: the FP32 sweeps of a mixed-precision
+  // factor have short FMA chains, and their batches would pay the products' cost
+  const bool fold = sizeof(TF) == sizeof(double);
+  c.mlast = fold ? linv + (backward ? 2 : 1) * size_t(p->nsb) * p->B * p->B : nullptr;
+  c.mlast2 = fold ? linv + (backward ? 4 : 3) * size_t(p->nsb) * p->B * p->B : nullptr;
   c.Y = Y;
   c.nr = nr;
   c.pad0 = 0;
@@ -691,7 +693,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   // inverses of the diagonal blocks for the sweeps (after the kernel's timing window)
   e = launch_diag_inverse(p, f, st);
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("diagonal inverses: ") + cudaGetErrorString(e));
-  count_launch(2);
+  count_launch(f->lp ? 1 : 2);
   CUDA_TRY(cudaEventRecord(f->done, st));
   f->pending = true;
   return STILES_OK;
@@ -1513,8 +1515,7 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
     const dim3 gm(unsigned(std::max<int64_t>(1, std::min<int64_t>(b->max_stasks, std::max(1, 148 * 8 / count)))),
                   unsigned(count));
     const dev::MlastDesc* dm = static_cast<const dev::MlastDesc*>(b->dmlast);
-    if (b->lp) dev::bmlast_kernel<64, float><<<gm, 128, 0, st>>>(dm);
-    else switch (b->B) {
+    if (!b->lp) switch (b->B) {
       case 16: dev::bmlast_kernel<16, double><<<gm, 128, 0, st>>>(dm); break;
       case 32: dev::bmlast_kernel<32, double><<<gm, 128, 0, st>>>(dm); break;
       default: dev::bmlast_kernel<64, double><<<gm, 128, 0, st>>>(dm); break;
@@ -1829,7 +1830,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->invdiag32, size_t(b->diag_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->ldiag, size_t(b->diag_elems));
-  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->linv32, 5 * size_t(b->diag_elems) * b->B);
+  if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->linv32, size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess) e = batch_alloc(b, &b->flags, size_t(b->flag_total));
   if (e == cudaSuccess) e = batch_alloc(b, &b->infos, size_t(count));
   if (e == cudaSuccess) e = batch_alloc(b, &b->ctl, 1);
@@ -1865,7 +1866,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       v->tiles16 = b->tiles16 + t_off[i];
       v->scratch32 = b->scratch32 + s_off[i];
       v->invdiag32 = b->invdiag32 + d_off[i];
-      v->linv32 = b->linv32 + 5 * d_off[i] * b->B;
+      v->linv32 = b->linv32 + d_off[i] * b->B;
       v->ldiag = b->ldiag + d_off[i];
     } else {
       v->tiles = b->tiles + t_off[i];
@@ -1889,8 +1890,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     {
       dev::MlastDesc& md = bml[i];
       const size_t nt = size_t(p->nsb) * b->B * b->B;
-      md.mlast = b->lp ? static_cast<void*>(v->linv32 + nt) : static_cast<void*>(v->linv + nt);
-      md.mlast2 = b->lp ? static_cast<void*>(v->linv32 + 3 * nt) : static_cast<void*>(v->linv + 3 * nt);
+      md.mlast = b->lp ? nullptr : static_cast<void*>(v->linv + nt);  // FP64 factors only
+      md.mlast2 = b->lp ? nullptr : static_cast<void*>(v->linv + 3 * nt);
       md.linv = binv[i].linv;
       md.tiles = binv[i].tiles;
       md.ftasks = p->dev->fwd.stasks;
@@ -1970,7 +1971,7 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(5);  // scatter, init, persistent kernel, diagonal inverses, folded sweep terms
+  count_launch(b->lp ? 4 : 5);  // scatter, init, persistent kernel, diagonal inverses, folded terms (FP64)
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));

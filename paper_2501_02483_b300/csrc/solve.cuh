@@ -460,7 +460,8 @@ struct MlastDesc {
 
 template <int B, typename TF>
 __device__ __forceinline__ void mlast_task(const MlastDesc& d, int t) {
-  const int task = t >> 1, which = t & 1;  // which: 0 = M1 (newest pair), 1 = M2
+  constexpr int NF = SolveCfg<B, TF>::NFOLD;
+  const int task = t / NF, which = t % NF;  // which: 0 = M1 (newest pair), 1 = M2
   const bool backward = task >= d.nf;
   const SolveTask tk = backward ? d.btasks[task - d.nf] : d.ftasks[task];
   if (tk.type != SOLVE_FINAL || tk.pe - tk.pb <= which) return;
@@ -484,13 +485,15 @@ __device__ __forceinline__ void mlast_task(const MlastDesc& d, int t) {
 
 template <int B, typename TF>
 __global__ void mlast_kernel(MlastDesc d) {
-  for (int t = blockIdx.x; t < 2 * (d.nf + d.nb); t += gridDim.x) mlast_task<B, TF>(d, t);
+  constexpr int NF = SolveCfg<B, TF>::NFOLD;
+  for (int t = blockIdx.x; t < NF * (d.nf + d.nb); t += gridDim.x) mlast_task<B, TF>(d, t);
 }
 
 template <int B, typename TF>
 __global__ void bmlast_kernel(const MlastDesc* descs) {
+  constexpr int NF = SolveCfg<B, TF>::NFOLD;
   const MlastDesc d = descs[blockIdx.y];
-  for (int t = blockIdx.x; t < 2 * (d.nf + d.nb); t += gridDim.x) mlast_task<B, TF>(d, t);
+  for (int t = blockIdx.x; t < NF * (d.nf + d.nb); t += gridDim.x) mlast_task<B, TF>(d, t);
 }
 
 }  // namespace dev

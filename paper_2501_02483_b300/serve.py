@@ -110,15 +110,15 @@ class Server:
             self.plans.setdefault(req.key, p)
             return self.plans[req.key]
 
-    @staticmethod
-    def _bytes(plan):
+    def _bytes(self, plan):
         inf = plan.info()
         # tiles (FP32 + 16-bit copy, or FP64) + values + flags + solve workspace + the diagonal
-        # inverses and the sweeps' folded terms (5 B^2 per diagonal sub-tile), per matrix
+        # inverses and, for FP64 factors, the sweeps' folded terms (5 B^2 per diagonal sub-tile)
         B = inf["block"]
         nsb = -(-inf["n"] // B)
+        per_diag = 40.0 if self.opts["precision"] == st.PREC_F64 else 4.0
         return (float(inf["factor_bytes"]) + 8.0 * inf["nnz"] + 4.0 * inf["nsub"] + 48.0 * MAX_RHS * inf["n"]
-                + 40.0 * nsb * B * B)
+                + per_diag * nsb * B * B)
 
     # -- residency (callers hold self.lock) ----------------------------------
     def _evict_until(self, need):
