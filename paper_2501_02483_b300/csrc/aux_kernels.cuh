@@ -162,8 +162,8 @@ template <int NR>
 __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* __restrict__ colptr,
                                            const int32_t* __restrict__ rowidx, const int64_t* __restrict__ rptr,
                                            const int32_t* __restrict__ rcol, const int64_t* __restrict__ rval,
-                                           const double* __restrict__ val, const double* __restrict__ x, int64_t ldx,
-                                           double* __restrict__ y, int64_t ldy, int nr) {
+                                           const double* __restrict__ val, const double* __restrict__ x, int64_t sx,
+                                           int64_t ldx, double* __restrict__ y, int64_t ldy, int nr) {
   static_assert(NR == 1 || NR == 2 || NR == 4 || NR == 8 || NR == 16, "NR is a power of two <= 16");
   double v[NR];
 #pragma unroll
@@ -174,7 +174,7 @@ __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* _
     const int64_t i = __ldg(rowidx + e);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      if (r < nr) v[r] = fma(a, __ldg(x + i + r * ldx), v[r]);
+      if (r < nr) v[r] = fma(a, __ldg(x + i * sx + r * ldx), v[r]);
   }
   const int64_t r1 = rptr[k + 1];
   for (int64_t e = rptr[k] + lane; e < r1; e += 32) {
@@ -182,7 +182,7 @@ __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* _
     const int64_t j = __ldg(rcol + e);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      if (r < nr) v[r] = fma(a, __ldg(x + j + r * ldx), v[r]);
+      if (r < nr) v[r] = fma(a, __ldg(x + j * sx + r * ldx), v[r]);
   }
   // butterfly reduce-scatter over the 32 lanes
   int cnt = NR;
@@ -213,13 +213,13 @@ __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* _
 // predicated off still takes its pipe slot, so the group fits nr)
 __device__ __forceinline__ void symv_index_any(int64_t k, int lane, const int64_t* colptr, const int32_t* rowidx,
                                                const int64_t* rptr, const int32_t* rcol, const int64_t* rval,
-                                               const double* val, const double* x, int64_t ldx, double* y,
+                                               const double* val, const double* x, int64_t sx, int64_t ldx, double* y,
                                                int64_t ldy, int nr) {
-  if (nr <= 1) symv_index<1>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
-  else if (nr <= 2) symv_index<2>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
-  else if (nr <= 4) symv_index<4>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
-  else if (nr <= 8) symv_index<8>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
-  else symv_index<16>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, ldy, nr);
+  if (nr <= 1) symv_index<1>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
+  else if (nr <= 2) symv_index<2>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
+  else if (nr <= 4) symv_index<4>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
+  else if (nr <= 8) symv_index<8>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
+  else symv_index<16>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
 }
 
 // y = A x (n x nr, leading dimensions ldx / n), one warp per index
@@ -230,7 +230,7 @@ __global__ void symv_kernel(double* __restrict__ y, const double* __restrict__ x
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps)
-    symv_index_any(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, ldx, y, n, nr);
+    symv_index_any(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, 1, ldx, y, n, nr);
 }
 
 __global__ void residual_norms_kernel(const double* __restrict__ y, const double* __restrict__ b, int64_t n, int64_t ldb,

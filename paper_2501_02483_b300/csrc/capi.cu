@@ -1297,14 +1297,26 @@ __global__ void bpermute_out_kernel(const BSolveDesc* desc, int which) {
   }
 }
 
-// y = A x for matrix blockIdx.y, one warp per index (no atomics)
+// d = x with the right-hand sides interleaved (d[i nr + r] = x[i + r n]): the
+// SpMV's gathers of one entry then read one contiguous run instead of nr
+// sectors n elements apart.  d is free here (the next correction overwrites it).
+__global__ void binterleave_kernel(const BSolveDesc* desc) {
+  const BSolveDesc c = desc[blockIdx.y];
+  const int64_t total = c.n * c.nr;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / c.nr, r = e % c.nr;
+    c.d[e] = c.x[i + r * c.n];
+  }
+}
+
+// y = A x for matrix blockIdx.y (x read interleaved from d), one warp per index (no atomics)
 __global__ void bspmv_kernel(const BSolveDesc* desc) {
   const BSolveDesc c = desc[blockIdx.y];
   if (c.nr == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c.n; k += warps)
-    dev::symv_index_any(k, lane, c.colptr, c.rowidx, c.rptr, c.rcol, c.rval, c.values, c.x, c.n, c.y, c.n, c.nr);
+    dev::symv_index_any(k, lane, c.colptr, c.rowidx, c.rptr, c.rcol, c.rval, c.values, c.d, c.nr, 1, c.y, c.n, c.nr);
 }
 
 // r = b - y and the squared norms per right-hand side (grid.z = right-hand side)
@@ -1739,13 +1751,14 @@ stiles_status batch_residual(stiles_batch* b, cudaStream_t st, int64_t max_rows,
   const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
   const int count = int(b->plans.size());
   CUDA_TRY(cudaMemsetAsync(b->vnorms, 0, size_t(count) * 2 * dev::SOLVE_MAXR * sizeof(double), st));
+  binterleave_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(desc);
   bspmv_kernel<<<batch_grid(b, max_rows * 32), 256, 0, st>>>(desc);
   CUDA_TRY(cudaGetLastError());
   dim3 g = batch_grid(b, max_rows);
   g.z = dev::SOLVE_MAXR;
   bresidual_kernel<<<g, 256, 0, st>>>(desc);
   CUDA_TRY(cudaGetLastError());
-  count_launch(2);
+  count_launch(3);
   std::vector<double> h(size_t(count) * 2 * dev::SOLVE_MAXR);
   CUDA_TRY(cudaMemcpyAsync(h.data(), b->vnorms, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
