@@ -195,6 +195,9 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
   if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
   bool aborted = false;
   while (!aborted) {
+    // generic-proxy writes of the previous task to shared buffers that TMA
+    // refills (sL, sRs) before the next copies
+    fence_proxy_async_shared();
     if (tid == 0) {
       int cur = next;
       if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(&a.ctl->ticket, 1);
@@ -372,8 +375,10 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
         } else {
           if (trace) trace[1] = (long long)globaltimer();
           fence_proxy_async_global();
-          mbar_arrive_expect_tx(lbar, LP_TILE * 4);
+          // L_kk and its 1/L_jj (into sRs, free until the POTRF) in one transaction
+          mbar_arrive_expect_tx(lbar, LP_TILE * 4 + LP_B * 4);
           tma_load_1d(sL, mc.tiles32 + size_t(tk.diag) * LP_TILE, LP_TILE * 4, lbar);
+          tma_load_1d(sRs, mc.invdiag32 + size_t(tk.col) * LP_B, LP_B * 4, lbar);
         }
       }
       sync();
@@ -381,13 +386,13 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
       if (!mbar_wait_bounded(lbar, ph_l & 1u)) { aborted = true; break; }
       ph_l ^= 1u;
       if (warp < 2) {
-        const float* iv = mc.invdiag32 + size_t(tk.col) * LP_B;
+        const float* iv = reinterpret_cast<const float*>(sRs);
 #pragma unroll
         for (int j = 0; j < LP_B; ++j) {
           float s = x1[j];
 #pragma unroll
           for (int p = 0; p < j; ++p) s = fmaf(-x1[p], sL[j + p * LP_B], s);
-          x1[j] = s * __ldcg(iv + j);
+          x1[j] = s * iv[j];
         }
         lp_store_row(mc, a.fp16, tk.out, r, x1);
       }
