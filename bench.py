@@ -87,8 +87,8 @@ def parse():
     ap.add_argument("--f64-tile", type=int, default=16, help="sweep/serve: tile of the FP64 arm")
     ap.add_argument("--requests", type=int, default=1500, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=500.0, help="serve: mean arrivals per second")
-    ap.add_argument("--max-batch", type=int, default=64, help="serve: matrices per batched launch")
-    ap.add_argument("--gpu-workers", type=int, default=3, help="serve: GPU jobs in flight (one stream each)")
+    ap.add_argument("--max-batch", type=int, default=256, help="serve: matrices per batched launch")
+    ap.add_argument("--gpu-workers", type=int, default=2, help="serve: GPU jobs in flight (one stream each)")
     ap.add_argument("--serve-ordering", choices=["none", "rcm", "auto", "nd"], default="nd",
                     help="serve: ordering of every plan (nd halves the chains of the large matrices)")
     return ap.parse_args()

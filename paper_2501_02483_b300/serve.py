@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
+import os
 import threading
 import time
 
@@ -75,13 +76,15 @@ class _Resident:
 
 
 class Server:
-    def __init__(self, precision=st.PREC_BF16, tile=64, ordering=st.ORDER_NONE, hbm_budget=150e9, max_batch=64,
-                 analyze_threads=8, refine_tol=1e-10, gpu_workers=3):
+    def __init__(self, precision=st.PREC_BF16, tile=64, ordering=st.ORDER_NONE, hbm_budget=150e9, max_batch=256,
+                 analyze_threads=None, refine_tol=1e-10, gpu_workers=2):
         import torch
 
         self.opts = dict(tile=tile, ordering=ordering, precision=precision, refine_tol=refine_tol)
         self.hbm_budget = float(hbm_budget)
         self.max_batch = max_batch
+        if analyze_threads is None:  # the C analysis releases the GIL: one thread per core, up to 32
+            analyze_threads = max(1, min(32, os.cpu_count() or 1))
         self.pool = cf.ThreadPoolExecutor(max_workers=analyze_threads)
         self.gpu_pool = cf.ThreadPoolExecutor(max_workers=gpu_workers)
         self.streams = [torch.cuda.Stream() for _ in range(gpu_workers)]
