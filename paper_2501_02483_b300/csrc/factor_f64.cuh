@@ -841,11 +841,40 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
 #pragma unroll
     for (int m = 0; m < CPT; ++m) sL[(q + RPT * m) * B + row] = acc1[m];
     publish(mc.flags + tk.out);  // includes the barrier that makes sL visible to the CTA
-#pragma unroll 4
-    for (int p = 0; p < B; ++p) {
-      const double av = sL[row + p * B];
+    if constexpr (B == 16) {
+      // the SYRK term on the FP64 tensor cores (mma.sync m8n8k4, 256 FMAs per
+      // warp instruction): the three lower 8 x 8 blocks of L_{k,k-1} L_{k,k-1}^T,
+      // one per warp, into a free stage area, then subtracted row by row
+      double* sS = sStage;  // 16 x 16, column-major
+      const int warp = tid >> 5;
+      if (warp < 3) {
+        const int bi = (warp == 0) ? 0 : 8, bj = (warp == 2) ? 8 : 0;
+        const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
+        double d0 = 0.0, d1 = 0.0;
 #pragma unroll
-      for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
+        for (int ks = 0; ks < B; ks += 4) {
+          const double fa = sL[(bi + g) + (ks + tq) * B];  // A(g, tq) = L(bi + g, ks + tq)
+          const double fb = sL[(bj + g) + (ks + tq) * B];  // B(tq, g) = L(bj + g, ks + tq)
+          asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                       : "+d"(d0), "+d"(d1)
+                       : "d"(fa), "d"(fb));
+        }
+        sS[(bi + g) + (bj + 2 * tq) * B] = d0;
+        sS[(bi + g) + (bj + 2 * tq + 1) * B] = d1;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) {
+        const int c = q + RPT * m;
+        if (c <= row) acc2[m] -= sS[row + c * B];
+      }
+    } else {
+#pragma unroll 4
+      for (int p = 0; p < B; ++p) {
+        const double av = sL[row + p * B];
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
+      }
     }
     const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
     if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
