@@ -267,6 +267,22 @@ stiles_status stiles_batch_solve(stiles_batch* batch, const double* const* rhs, 
 stiles_status stiles_batch_timing(const stiles_batch* batch, double* ms_kernel);
 void stiles_batch_destroy(stiles_batch* batch);
 
+/* Marginal variances diag(A^{-1}) of an FP64 factor (the inverses that Section I lists among
+ * the standard tasks on arrowhead precision matrices; INLA's marginal variances).  Computes,
+ * once per factorization, the selected inverse Sigma = (P A P^T)^{-1} on the filled sub-tile map
+ * of L from Sigma L = L^{-T} in reverse column order (Sigma_mk = -sum_j Sigma_mj L_jk L_kk^{-1},
+ * Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_j Sigma_jk^T L_jk L_kk^{-1}) in one persistent launch, then
+ * writes out[i] = (A^{-1})_ii for i < n in the original order.  out: n doubles, host or device.
+ * stream: NULL = the factor's stream.  The factor keeps Sigma and the products L_jk L_kk^{-1}
+ * (two arrays of its tile size) until it is destroyed.  STILES_ERR_UNSUPPORTED for a
+ * mixed-precision factor; STILES_ERR_TIMEOUT if a device wait gave up. */
+stiles_status stiles_marginal_variances(stiles_factor* factor, double* out, void* stream);
+
+/* The selected inverse itself: T x T column-major tiles of Sigma on L's tile map, in tile-CSC
+ * order (the layout of stiles_factor_tiles), computed as above if it is not current.  out:
+ * nnzt * T * T doubles, host or device. */
+stiles_status stiles_selected_inverse_tiles(stiles_factor* factor, double* out, void* stream);
+
 /* Tile-size autotuner (Section IV.B and Appendix B: the tile size trades the extra flops of
  * padded tiles against the parallelism of the task graph).  For each candidate in tiles[ntiles]
  * the pattern is analysed with opts (opts->tile ignored); candidates whose task flops exceed 4x

@@ -937,4 +937,84 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   return STILES_OK;
 }
 
+// Task graph of the selected inverse (Sigma L = L^{-T}, column blocks in
+// reverse): for sub-column k = nsb-1 .. 0, first Sigma_mk = -sum_j Sigma_mj U_jk
+// for every sub-row m > k present in column k, then
+// Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_j Sigma_jk^T U_jk, with j over the same
+// sub-rows and U_jk = L_jk L_kk^{-1}.  Sigma_mj (m, j > k) lies on the filled map
+// (the tile closure makes the sub-rows of a column a clique); it is stored as
+// (max, min) and read transposed when m < j.  Pairs run from the oldest
+// producer (largest j) to the newest, and every dependency carries a smaller
+// ticket, so the persistent kernel cannot wait on work that has not started.
+stiles_status build_selinv(stiles_plan* p, std::string* err) {
+  if (p->selinv_built) return STILES_OK;
+  if (!p->executable) { *err = "the plan has no sub-tile executor"; return STILES_ERR_UNSUPPORTED; }
+  const int64_t nsb = p->nsb, R = p->R, nt = p->nt;
+  auto tile_index = [&](int64_t I, int64_t J) -> int64_t {
+    if (I == J) return p->tcolptr[J];
+    const int32_t* b0 = p->trowidx.data() + p->tcolptr[J] + 1;
+    const int32_t* e0 = p->trowidx.data() + p->tcolptr[J + 1];
+    const int32_t* it = std::lower_bound(b0, e0, int32_t(I));
+    if (it == e0 || *it != I) return -1;
+    return int64_t(it - p->trowidx.data());
+  };
+  auto sub_index = [&](int64_t ii, int64_t jj) -> int64_t {  // ii >= jj
+    const int64_t e = tile_index(ii / R, jj / R);
+    return e < 0 ? -1 : e * R * R + (jj % R) * R + (ii % R);
+  };
+  // sub-rows below the diagonal of every sub-column, ascending
+  std::vector<std::vector<int32_t>> below(nsb);
+  for (int64_t J = 0; J < nt; ++J)
+    for (int64_t e = p->tcolptr[J]; e < p->tcolptr[J + 1]; ++e) {
+      const int64_t I = p->trowidx[e];
+      for (int64_t q = 0; q < R; ++q) {
+        const int64_t jj = J * R + q;
+        if (jj >= nsb) break;
+        for (int64_t pp = 0; pp < R; ++pp) {
+          const int64_t ii = I * R + pp;
+          if (ii >= nsb) break;
+          if (ii > jj) below[jj].push_back(int32_t(ii));
+        }
+      }
+    }
+  SelinvGraph g;
+  for (int64_t k = nsb - 1; k >= 0; --k) {
+    auto& S = below[k];
+    std::sort(S.begin(), S.end());
+    for (int32_t j : S) {
+      const int64_t u = sub_index(j, k);
+      if (u < 0) { *err = "internal: missing sub-tile"; return STILES_ERR_INVALID; }
+      g.ulist.push_back(int32_t(u));
+      g.ulist.push_back(int32_t(k));
+    }
+    auto add_task = [&](int64_t m) -> bool {  // m == k: the diagonal sub-tile
+      const int64_t out = sub_index(m, k);
+      if (out < 0) return false;
+      g.tasks.push_back(int32_t(out));
+      g.tasks.push_back(m == k ? int32_t(k) : -1);
+      g.tasks.push_back(int32_t(g.pairs.size() / 2));
+      for (size_t a = S.size(); a-- > 0;) {  // oldest producer (largest j) first
+        const int64_t j = S[a];
+        int64_t sig;
+        bool tr;
+        if (m == k) { sig = sub_index(j, k); tr = true; }
+        else if (m >= j) { sig = sub_index(m, j); tr = false; }
+        else { sig = sub_index(j, m); tr = true; }
+        if (sig < 0) return false;
+        g.pairs.push_back(int32_t(sig) | (tr ? (1 << 30) : 0));
+        g.pairs.push_back(int32_t(sub_index(j, k)));
+      }
+      g.tasks.push_back(int32_t(g.pairs.size() / 2));
+      return true;
+    };
+    for (int32_t m : S)
+      if (!add_task(m)) { *err = "internal: selected-inverse operand off the filled map"; return STILES_ERR_INVALID; }
+    if (!add_task(k)) { *err = "internal: missing diagonal sub-tile"; return STILES_ERR_INVALID; }
+  }
+  if (g.pairs.size() / 2 >= (size_t(1) << 31)) { *err = "selected inverse too large"; return STILES_ERR_UNSUPPORTED; }
+  p->selinv = std::move(g);
+  p->selinv_built = true;
+  return STILES_OK;
+}
+
 }  // namespace stiles

@@ -18,6 +18,7 @@
 #include "factor_f64.cuh"
 #include "factor_lp.cuh"
 #include "plan.h"
+#include "selinv.cuh"
 #include "solve.cuh"
 
 namespace {
@@ -91,6 +92,13 @@ struct DevPlan {
   int64_t* rval = nullptr;
   DevGraph fac, fwd, bwd;
   int grid_factor = 0, grid_solve = 0;
+  // selected inverse (uploaded on first use)
+  int32_t* sinv_tasks = nullptr;
+  int32_t* sinv_pairs = nullptr;
+  int32_t* sinv_ulist = nullptr;
+  int sinv_ntasks = 0;
+  int64_t sinv_nu = 0;
+  bool sinv_ready = false;
 };
 
 }  // namespace stiles
@@ -136,6 +144,12 @@ struct stiles_factor {
   unsigned long long* info = nullptr;  // first bad pivot column (&ctl[0].info, or a batch slot)
   bool view = false;                   // tiles and values belong to a stiles_batch
   bool pending = false;
+  // selected inverse (allocated on first use): Sigma and U sub-tiles, Sigma flags
+  double* sigma = nullptr;
+  double* sinv_u = nullptr;
+  int* sinv_flags = nullptr;
+  stiles::dev::Ctl* sinv_ctl = nullptr;
+  bool sinv_valid = false;             // Sigma belongs to the current factorization
 };
 
 namespace {
@@ -167,6 +181,9 @@ void free_dev_plan(stiles_plan* p) {
   free_graph(d->fac);
   free_graph(d->fwd);
   free_graph(d->bwd);
+  cudaFree(d->sinv_tasks);
+  cudaFree(d->sinv_pairs);
+  cudaFree(d->sinv_ulist);
   delete d;
   p->dev = nullptr;
 }
@@ -306,6 +323,10 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->xstage);
   cudaFree(f->ywork);
   cudaFree(f->norms);
+  cudaFree(f->sigma);
+  cudaFree(f->sinv_u);
+  cudaFree(f->sinv_flags);
+  cudaFree(f->sinv_ctl);
   if (f->done) cudaEventDestroy(f->done);
   for (cudaEvent_t e : f->ev)
     if (e) cudaEventDestroy(e);
@@ -696,6 +717,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   count_launch(f->lp ? 1 : 2);
   CUDA_TRY(cudaEventRecord(f->done, st));
   f->pending = true;
+  f->sinv_valid = false;
   return STILES_OK;
 }
 
@@ -1043,6 +1065,146 @@ stiles_status stiles_factor_tiles(const stiles_factor* cf, double* out, void* st
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (!odev) cudaFree(dst);
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("tile export: ") + cudaGetErrorString(e));
+  return STILES_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <int B>
+stiles_status launch_selinv(const stiles_plan* p, stiles_factor* f, cudaStream_t st) {
+  const DevPlan* d = p->dev;
+  const int64_t nu = d->sinv_nu;
+  if (nu > 0) {
+    const int gu = int(std::max<int64_t>(1, std::min<int64_t>(nu, 148 * 16)));
+    dev::selinv_u_kernel<B><<<gu, 128, 0, st>>>(f->sinv_u, f->tiles, f->linv, d->sinv_ulist, nu);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  static int per_sm = 0;  // resident CTAs of the persistent kernel (per B instantiation)
+  if (per_sm == 0) {
+    CUDA_TRY(cudaFuncSetAttribute(dev::selinv_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(dev::SelinvCfg<B>::SMEM)));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::selinv_kernel<B>, 128,
+                                                           dev::SelinvCfg<B>::SMEM));
+    per_sm = std::max(per_sm, 1);
+  }
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
+  dev::SelinvArgs a{};
+  a.sigma = f->sigma;
+  a.U = f->sinv_u;
+  a.linv = f->linv;
+  a.tasks = d->sinv_tasks;
+  a.pairs = d->sinv_pairs;
+  a.ntasks = d->sinv_ntasks;
+  a.flags = f->sinv_flags;
+  a.ctl = f->sinv_ctl;
+  a.spin_limit = p->opts.spin_limit;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(per_sm) * sms, d->sinv_ntasks)));
+  dev::selinv_kernel<B><<<grid, 128, dev::SelinvCfg<B>::SMEM, st>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return STILES_OK;
+}
+
+// Sigma on the filled sub-tile map for the factor's current values (FP64 factors).
+stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
+  const stiles_plan* p = f->plan;
+  if (f->lp) return fail(STILES_ERR_UNSUPPORTED, "the selected inverse needs an FP64 factor");
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    stiles_plan* pm = const_cast<stiles_plan*>(p);
+    std::string err;
+    stiles_status s = build_selinv(pm, &err);
+    if (s != STILES_OK) return fail(s, err);
+    DevPlan* d = pm->dev;
+    if (!d->sinv_ready) {
+      cudaError_t e = upload(&d->sinv_tasks, pm->selinv.tasks);
+      if (e == cudaSuccess) e = upload(&d->sinv_pairs, pm->selinv.pairs);
+      if (e == cudaSuccess) e = upload(&d->sinv_ulist, pm->selinv.ulist);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                    std::string("selected-inverse upload: ") + cudaGetErrorString(e));
+      }
+      d->sinv_ntasks = int(pm->selinv.tasks.size() / 4);
+      d->sinv_nu = int64_t(pm->selinv.ulist.size() / 2);
+      d->sinv_ready = true;
+    }
+  }
+  if (f->sinv_valid) return STILES_OK;
+  const size_t tile = size_t(p->B) * p->B;
+  if (!f->sigma) CUDA_TRY(cudaMalloc(&f->sigma, size_t(p->nsub) * tile * sizeof(double)));
+  if (!f->sinv_u) CUDA_TRY(cudaMalloc(&f->sinv_u, size_t(p->nsub) * tile * sizeof(double)));
+  if (!f->sinv_flags) CUDA_TRY(cudaMalloc(&f->sinv_flags, size_t(p->nsub) * sizeof(int)));
+  if (!f->sinv_ctl) CUDA_TRY(cudaMalloc(&f->sinv_ctl, sizeof(dev::Ctl)));
+  if (f->done) CUDA_TRY(cudaStreamWaitEvent(st, f->done, 0));  // the factorization has finished
+  CUDA_TRY(cudaMemsetAsync(f->sinv_flags, 0, size_t(p->nsub) * sizeof(int), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->sinv_ctl, 1);
+  CUDA_TRY(cudaGetLastError());
+  count_launch();
+  stiles_status s;
+  switch (p->B) {
+    case 16: s = launch_selinv<16>(p, f, st); break;
+    case 32: s = launch_selinv<32>(p, f, st); break;
+    default: s = launch_selinv<64>(p, f, st); break;
+  }
+  if (s != STILES_OK) return s;
+  dev::Ctl c;
+  CUDA_TRY(cudaMemcpyAsync(&c, f->sinv_ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (c.status != 0) return fail(STILES_ERR_TIMEOUT, "device wait timed out in the selected inverse");
+  f->sinv_valid = true;
+  return STILES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stiles_status stiles_marginal_variances(stiles_factor* f, double* out, void* stream) {
+  if (!f || !out) return fail(STILES_ERR_INVALID, "null argument");
+  const stiles_plan* p = f->plan;
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : f->stream;
+  stiles_status s = ensure_selinv(f, st);
+  if (s != STILES_OK) return s;
+  const bool odev = is_device_ptr(out);
+  double* dst = out;
+  if (!odev) CUDA_TRY(cudaMalloc(&dst, size_t(p->n) * sizeof(double)));
+  const int g = grid_for(p->n, 256);
+  switch (p->B) {
+    case 16: dev::selinv_diag_kernel<16><<<g, 256, 0, st>>>(dst, f->sigma, p->dev->diag_sub, p->dev->perm, p->n); break;
+    case 32: dev::selinv_diag_kernel<32><<<g, 256, 0, st>>>(dst, f->sigma, p->dev->diag_sub, p->dev->perm, p->n); break;
+    default: dev::selinv_diag_kernel<64><<<g, 256, 0, st>>>(dst, f->sigma, p->dev->diag_sub, p->dev->perm, p->n); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  count_launch();
+  if (e == cudaSuccess && !odev) e = cudaMemcpyAsync(out, dst, size_t(p->n) * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!odev) cudaFree(dst);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("marginal variances: ") + cudaGetErrorString(e));
+  return STILES_OK;
+}
+
+stiles_status stiles_selected_inverse_tiles(stiles_factor* f, double* out, void* stream) {
+  if (!f || !out) return fail(STILES_ERR_INVALID, "null argument");
+  const stiles_plan* p = f->plan;
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : f->stream;
+  stiles_status s = ensure_selinv(f, st);
+  if (s != STILES_OK) return s;
+  const size_t elems = size_t(p->nnzt) * p->T * p->T;
+  const bool odev = is_device_ptr(out);
+  double* dst = out;
+  if (!odev) CUDA_TRY(cudaMalloc(&dst, elems * sizeof(double)));
+  dev::export_tiles_kernel<double><<<grid_for(int64_t(elems), 256), 256, 0, st>>>(dst, f->sigma, p->nnzt, p->T, p->B);
+  cudaError_t e = cudaGetLastError();
+  count_launch();
+  if (e == cudaSuccess && !odev) e = cudaMemcpyAsync(out, dst, elems * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!odev) cudaFree(dst);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("selected-inverse export: ") + cudaGetErrorString(e));
   return STILES_OK;
 }
 
@@ -1988,7 +2150,10 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));
-  for (stiles_factor* v : b->views) v->stream = st;
+  for (stiles_factor* v : b->views) {
+    v->stream = st;
+    v->sinv_valid = false;
+  }
   dev::Ctl c;
   CUDA_TRY(cudaMemcpy(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost));
   std::vector<unsigned long long> hinfo(count);

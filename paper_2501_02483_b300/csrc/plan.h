@@ -66,6 +66,17 @@ struct SolveGraph {
   int64_t nscratch = 0;
 };
 
+// Selected inverse (Sigma = (P A P^T)^{-1} on the filled sub-tile map), reverse
+// column order: per task 4 int32 (output sub-tile, its sub-column if it is a
+// diagonal sub-tile else -1, first pair, end pair); per pair 2 int32 (Sigma
+// sub-tile with bit 30 set when it is read transposed, U sub-tile); per
+// off-diagonal sub-tile 2 int32 (sub-tile, sub-column) for U = L_jk L_kk^{-1}.
+struct SelinvGraph {
+  std::vector<int32_t> tasks;
+  std::vector<int32_t> pairs;
+  std::vector<int32_t> ulist;
+};
+
 struct DevPlan;  // device copies, defined in capi.cu
 
 }  // namespace stiles
@@ -99,6 +110,8 @@ struct stiles_plan {
   std::vector<int32_t> bulk_order;   // every other factor task, ticket order
   bool split_queues = false;         // thin DAG: run the chain on reserved SMs (little work per chain step)
   stiles::SolveGraph fwd, bwd;
+  stiles::SelinvGraph selinv;        // built on first use (stiles_marginal_variances)
+  bool selinv_built = false;
   stiles::DevPlan* dev = nullptr;
 };
 
@@ -106,5 +119,6 @@ namespace stiles {
 // analyze.cpp
 stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
                          const stiles_opts& opts, stiles_plan* p, std::string* err);
+stiles_status build_selinv(stiles_plan* p, std::string* err);
 void default_opts(stiles_opts* o);
 }  // namespace stiles

@@ -73,6 +73,8 @@ def lib():
         L.stiles_last_error.argtypes = []
         L.stiles_last_error.restype = c_char_p
         L.stiles_probe_fp64_peak.argtypes = [POINTER(c_double)]
+        L.stiles_marginal_variances.argtypes = [P, P, P]
+        L.stiles_selected_inverse_tiles.argtypes = [P, P, P]
         L.stiles_factor_timing.argtypes = [P, POINTER(c_double), POINTER(c_double)]
         L.stiles_factor_set_trace.argtypes = [P, c_int32]
         L.stiles_factor_get_trace.argtypes = [P, c_int32, P, POINTER(c_int64)]
@@ -287,6 +289,22 @@ class Factor:
         _check(lib().stiles_factor_get_trace(self._h, which, None, ctypes.byref(n)))
         out = np.empty((n.value, 4), dtype=np.int64)
         _check(lib().stiles_factor_get_trace(self._h, which, _ptr(out), ctypes.byref(n)))
+        return out
+
+    def marginal_variances(self, out=None, stream=None):
+        """diag(A^{-1}) in the original order (FP64 factors): host numpy unless ``out`` is given."""
+        if out is None:
+            out = np.empty(self.plan.n, dtype=np.float64)
+        _check(lib().stiles_marginal_variances(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def selected_inverse_tiles(self, out=None, stream=None):
+        """T x T tiles of Sigma = (P A P^T)^{-1} on L's tile map, tile-CSC order."""
+        inf = self.plan.info()
+        T = inf["tile"]
+        if out is None:
+            out = np.empty((inf["nnzt"], T, T), dtype=np.float64)
+        _check(lib().stiles_selected_inverse_tiles(self._h, _ptr(out), _stream(stream)))
         return out
 
     def tiles(self, out=None, stream=None):
