@@ -218,6 +218,28 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _selinv_flops(plan):
+    """Useful flops of the selected inverse at the plan's sub-tile size B: per
+    sub-column with s sub-rows below the diagonal, s^2 + s operand pairs of
+    2 B^3 (Sigma_mj U_jk, Sigma_jk^T U_jk), s products L_jk L_kk^{-1} and one
+    L_kk^{-T} L_kk^{-1} of B^3 each."""
+    inf = plan.info()
+    T, B, n = inf["tile"], inf["block"], inf["n"]
+    R = T // B
+    nsb = -(-n // B)
+    tc, tr = plan.tilemap()
+    total = 0
+    for K in range(tc.size - 1):
+        below_tiles = int(tc[K + 1] - tc[K] - 1)
+        for q in range(R):
+            jj = K * R + q
+            if jj >= nsb:
+                break
+            s = below_tiles * R + (R - 1 - q)
+            total += (s * s + s) * 2 * B ** 3 + (s + 1) * B ** 3
+    return total
+
+
 def run_ours(args):
     import torch
 
@@ -315,6 +337,23 @@ def run_ours(args):
     # correctness of what was timed
     _, relres = f.solve(b_d, stream=stream, relres=True)
 
+    # marginal variances diag(A^{-1}) through the selected inverse (FP64 factors):
+    # the first call builds and uploads its task graph; a new factorization
+    # invalidates Sigma, so the timed call recomputes all of it
+    sinv = None
+    if prec == st.PREC_F64 and rank == 0:
+        f.marginal_variances(stream=stream)
+        f.factorize(vals_d, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        var = f.marginal_variances(stream=stream)
+        ms_sinv = (time.perf_counter() - t0) * 1e3
+        sfl = _selinv_flops(plan)
+        sinv = {"ms": round(ms_sinv, 2), "flops": sfl, "tflops": round(sfl / ms_sinv / 1e9, 4),
+                "frac_of_fp64_peak": round(sfl / ms_sinv / 1e9 / peak, 4),
+                "min_variance": float(var.min()), "max_variance": float(var.max()),
+                "flops_rule": "2 B^3 per operand pair, B^3 per L_jk L_kk^{-1} and per L_kk^{-T} L_kk^{-1}"}
+
     # tile-size sweep (the workload names 128/256/512; 32/64 added)
     sweep = {}
     if rank == 0 and args.sweep:
@@ -352,7 +391,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": dict(workload_config(args, info), analyze_s=round(analyze_s, 3), logdet=ld,
                        relres=relres, tile_sweep=sweep, percent_of_fp64_peak=round(100 * value / peak, 2),
-                       refine_iters=f.refine_iters()),
+                       refine_iters=f.refine_iters(), marginal_variances=sinv),
         "roofline": roof,
         "e2e": e2e, "gpu_launches": launches, "clocks": clk.result,
     }

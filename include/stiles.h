@@ -273,8 +273,8 @@ void stiles_batch_destroy(stiles_batch* batch);
  * of L from Sigma L = L^{-T} in reverse column order (Sigma_mk = -sum_j Sigma_mj L_jk L_kk^{-1},
  * Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_j Sigma_jk^T L_jk L_kk^{-1}) in one persistent launch, then
  * writes out[i] = (A^{-1})_ii for i < n in the original order.  out: n doubles, host or device.
- * stream: NULL = the factor's stream.  The factor keeps Sigma and the products L_jk L_kk^{-1}
- * (two arrays of its tile size) until it is destroyed.  STILES_ERR_UNSUPPORTED for a
+ * stream: NULL = the factor's stream.  The factor keeps Sigma, its transpose and the products
+ * L_jk L_kk^{-1} (three arrays of its tile size) until it is destroyed.  STILES_ERR_UNSUPPORTED for a
  * mixed-precision factor; STILES_ERR_TIMEOUT if a device wait gave up. */
 stiles_status stiles_marginal_variances(stiles_factor* factor, double* out, void* stream);
 

@@ -146,7 +146,8 @@ struct stiles_factor {
   bool pending = false;
   // selected inverse (allocated on first use): Sigma and U sub-tiles, Sigma flags
   double* sigma = nullptr;
-  double* sinv_u = nullptr;
+  double* sigmaT = nullptr;            // Sigma's sub-tiles transposed
+  double* sinv_u = nullptr;            // (L_jk L_kk^{-1})^T
   int* sinv_flags = nullptr;
   stiles::dev::Ctl* sinv_ctl = nullptr;
   bool sinv_valid = false;             // Sigma belongs to the current factorization
@@ -324,6 +325,7 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->ywork);
   cudaFree(f->norms);
   cudaFree(f->sigma);
+  cudaFree(f->sigmaT);
   cudaFree(f->sinv_u);
   cudaFree(f->sinv_flags);
   cudaFree(f->sinv_ctl);
@@ -1094,7 +1096,8 @@ stiles_status launch_selinv(const stiles_plan* p, stiles_factor* f, cudaStream_t
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device));
   dev::SelinvArgs a{};
   a.sigma = f->sigma;
-  a.U = f->sinv_u;
+  a.sigmaT = f->sigmaT;
+  a.V = f->sinv_u;
   a.linv = f->linv;
   a.tasks = d->sinv_tasks;
   a.pairs = d->sinv_pairs;
@@ -1137,6 +1140,7 @@ stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
   if (f->sinv_valid) return STILES_OK;
   const size_t tile = size_t(p->B) * p->B;
   if (!f->sigma) CUDA_TRY(cudaMalloc(&f->sigma, size_t(p->nsub) * tile * sizeof(double)));
+  if (!f->sigmaT) CUDA_TRY(cudaMalloc(&f->sigmaT, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_u) CUDA_TRY(cudaMalloc(&f->sinv_u, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_flags) CUDA_TRY(cudaMalloc(&f->sinv_flags, size_t(p->nsub) * sizeof(int)));
   if (!f->sinv_ctl) CUDA_TRY(cudaMalloc(&f->sinv_ctl, sizeof(dev::Ctl)));

@@ -10,9 +10,11 @@ namespace stiles {
 namespace dev {
 
 // U_jk = L_jk L_kk^{-1} for every off-diagonal sub-tile (ulist: sub-tile,
-// sub-column), one CTA per sub-tile.  L_kk^{-1} is lower triangular.
+// sub-column), one CTA per sub-tile, stored transposed (V = U^T, column-major),
+// so that the products read it along its rows without bank conflicts.
+// L_kk^{-1} is lower triangular.
 template <int B>
-__global__ void selinv_u_kernel(double* __restrict__ U, const double* __restrict__ tiles,
+__global__ void selinv_u_kernel(double* __restrict__ V, const double* __restrict__ tiles,
                                 const double* __restrict__ linv, const int32_t* __restrict__ ulist, int64_t nu) {
   for (int64_t e = blockIdx.x; e < nu; e += gridDim.x) {
     const int64_t s = ulist[2 * e], k = ulist[2 * e + 1];
@@ -22,14 +24,15 @@ __global__ void selinv_u_kernel(double* __restrict__ U, const double* __restrict
       const int i = o % B, c = o / B;
       double v = 0.0;
       for (int p = c; p < B; ++p) v = fma(__ldg(Ls + i + p * B), __ldg(Li + p + c * B), v);
-      U[s * B * B + o] = v;
+      V[s * B * B + c + i * B] = v;
     }
   }
 }
 
 struct SelinvArgs {
   double* sigma;          // nsub * B * B, same layout as the factor's sub-tiles
-  const double* U;        // nsub * B * B: U_jk at the off-diagonal sub-tiles
+  double* sigmaT;         // the same sub-tiles transposed (read where a pair wants Sigma^T)
+  const double* V;        // nsub * B * B: U_jk^T at the off-diagonal sub-tiles
   const double* linv;     // nsb * B * B: L_kk^{-1}
   const int32_t* tasks;   // 4 per task (see SelinvGraph)
   const int32_t* pairs;   // 2 per pair
@@ -48,10 +51,12 @@ struct SelinvCfg {
 
 // Persistent over the tasks in ticket order (every dependency carries a
 // smaller ticket).  A task accumulates sum_j S_j U_j over its pairs (S_j a
-// Sigma sub-tile, transposed when bit 30 says so; U_j an U sub-tile), with
-// the pairs staged by TMA once the Sigma sub-tile's flag is set, and stores
-// -sum (off-diagonal) or L_kk^{-T} L_kk^{-1} - sum (diagonal).  Thread layout
-// as the FP64 factorization: thread (row, q) holds columns q + RPT m.
+// Sigma sub-tile, or its transpose -- kept as a second copy -- when bit 30
+// says so; U_j from the transposed U array), with the pairs staged by TMA
+// once the Sigma sub-tile's flag is set, and stores -sum (off-diagonal) or
+// L_kk^{-T} L_kk^{-1} - sum (diagonal), and its transpose.  Thread layout as
+// the FP64 factorization (thread (row, q) holds columns q + RPT m), so both
+// operands are read along rows of the stored tiles (no bank conflicts).
 template <int B>
 __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
   using Cfg = FactorCfg<B>;
@@ -115,8 +120,9 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
           const int st = issued % NSTAGE;
           double* dst = sStage + st * 2 * TILE;
           mbar_arrive_expect_tx(&bars[st], uint32_t(2 * TILE * sizeof(double)));
-          tma_load_1d(dst, a.sigma + size_t(sg) * TILE, TILE * sizeof(double), &bars[st]);
-          tma_load_1d(dst + TILE, a.U + size_t(su) * TILE, TILE * sizeof(double), &bars[st]);
+          const double* src = ((raw >> 30) & 1) ? a.sigmaT : a.sigma;
+          tma_load_1d(dst, src + size_t(sg) * TILE, TILE * sizeof(double), &bars[st]);
+          tma_load_1d(dst + TILE, a.V + size_t(su) * TILE, TILE * sizeof(double), &bars[st]);
           ++issued;
         }
       }
@@ -132,13 +138,12 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
       if (aborted) { stop = it; break; }
       phase ^= (1u << st);
       const double* sS = sStage + st * 2 * TILE;
-      const double* sU = sS + TILE;
-      const bool tr = (a.pairs[2 * (pb + it)] >> 30) & 1;
+      const double* sV = sS + TILE;
 #pragma unroll 4
       for (int p = 0; p < B; ++p) {
-        const double sv = tr ? sS[p + row * B] : sS[row + p * B];
+        const double sv = sS[row + p * B];
 #pragma unroll
-        for (int m = 0; m < CPT; ++m) acc[m] = fma(sv, sU[p + (q + RPT * m) * B], acc[m]);
+        for (int m = 0; m < CPT; ++m) acc[m] = fma(sv, sV[q + RPT * m + p * B], acc[m]);
       }
       __syncthreads();  // stage `st` may be refilled
     }
@@ -182,8 +187,12 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
       for (int m = 0; m < CPT; ++m) v[m] = -acc[m];
     }
     double* dst = a.sigma + size_t(out) * TILE;
+    double* dstT = a.sigmaT + size_t(out) * TILE;
 #pragma unroll
-    for (int m = 0; m < CPT; ++m) dst[(q + RPT * m) * B + row] = v[m];
+    for (int m = 0; m < CPT; ++m) {
+      dst[(q + RPT * m) * B + row] = v[m];
+      dstT[row * B + q + RPT * m] = v[m];
+    }
     publish(a.flags + out);
   }
 }
