@@ -58,8 +58,8 @@ METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set res
 # DRAM bytes per launch of the factorization kernel, from an ncu capture (see
 # profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
 # changed after the capture.
-TRAFFIC = {("factor_f64_v7", "large", 16, 16): 1.350e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
-KERNEL_TAG = "factor_f64_v7"
+TRAFFIC = {("factor_f64_v8", "large", 16, 16): 1.352e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
+KERNEL_TAG = "factor_f64_v8"
 
 
 def parse():
