@@ -6,9 +6,11 @@
 // Nothing here touches the GPU; stiles_analyze can run on any host.
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
+#include <thread>
 
 #include "plan.h"
 
@@ -977,41 +979,83 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
         }
       }
     }
-  SelinvGraph g;
-  for (int64_t k = nsb - 1; k >= 0; --k) {
-    auto& S = below[k];
-    std::sort(S.begin(), S.end());
-    for (int32_t j : S) {
-      const int64_t u = sub_index(j, k);
-      if (u < 0) { *err = "internal: missing sub-tile"; return STILES_ERR_INVALID; }
-      g.ulist.push_back(int32_t(u));
-      g.ulist.push_back(int32_t(k));
-    }
-    auto add_task = [&](int64_t m) -> bool {  // m == k: the diagonal sub-tile
-      const int64_t out = sub_index(m, k);
-      if (out < 0) return false;
-      g.tasks.push_back(int32_t(out));
-      g.tasks.push_back(m == k ? int32_t(k) : -1);
-      g.tasks.push_back(int32_t(g.pairs.size() / 2));
-      for (size_t a = S.size(); a-- > 0;) {  // oldest producer (largest j) first
-        const int64_t j = S[a];
-        int64_t sig;
-        bool tr;
-        if (m == k) { sig = sub_index(j, k); tr = true; }
-        else if (m >= j) { sig = sub_index(m, j); tr = false; }
-        else { sig = sub_index(j, m); tr = true; }
-        if (sig < 0) return false;
-        g.pairs.push_back(int32_t(sig) | (tr ? (1 << 30) : 0));
-        g.pairs.push_back(int32_t(sub_index(j, k)));
-      }
-      g.tasks.push_back(int32_t(g.pairs.size() / 2));
-      return true;
-    };
-    for (int32_t m : S)
-      if (!add_task(m)) { *err = "internal: selected-inverse operand off the filled map"; return STILES_ERR_INVALID; }
-    if (!add_task(k)) { *err = "internal: missing diagonal sub-tile"; return STILES_ERR_INVALID; }
+  // Offsets first (columns in reverse: |S_k| + 1 tasks, (|S_k| + 1) |S_k| pairs,
+  // |S_k| U products each), then every column filled independently on host
+  // threads (the largest graphs hold a few hundred million pairs).
+  std::vector<int64_t> t_off(nsb + 1, 0), p_off(nsb + 1, 0), u_off(nsb + 1, 0);
+  for (int64_t r = 0; r < nsb; ++r) {  // r-th column in ticket order is k = nsb - 1 - r
+    const int64_t sk = int64_t(below[nsb - 1 - r].size());
+    t_off[r + 1] = t_off[r] + sk + 1;
+    p_off[r + 1] = p_off[r] + (sk + 1) * sk;
+    u_off[r + 1] = u_off[r] + sk;
   }
-  if (g.pairs.size() / 2 >= (size_t(1) << 31)) { *err = "selected inverse too large"; return STILES_ERR_UNSUPPORTED; }
+  if (p_off[nsb] >= (int64_t(1) << 31)) { *err = "selected inverse too large"; return STILES_ERR_UNSUPPORTED; }
+  SelinvGraph g;
+  g.tasks.resize(size_t(4 * t_off[nsb]));
+  g.pairs.resize(size_t(2 * p_off[nsb]));
+  g.ulist.resize(size_t(2 * u_off[nsb]));
+  std::atomic<int> bad{0};
+  auto fill = [&](int64_t r0, int64_t r1) {
+    for (int64_t r = r0; r < r1 && !bad.load(std::memory_order_relaxed); ++r) {
+      const int64_t k = nsb - 1 - r;
+      std::vector<int32_t>& S = below[k];
+      std::sort(S.begin(), S.end());
+      int64_t u = u_off[r];
+      for (int32_t j : S) {
+        const int64_t sj = sub_index(j, k);
+        if (sj < 0) { bad = 1; return; }
+        g.ulist[2 * u] = int32_t(sj);
+        g.ulist[2 * u + 1] = int32_t(k);
+        ++u;
+      }
+      int64_t t = t_off[r], q = p_off[r];
+      auto add_task = [&](int64_t m) -> bool {  // m == k: the diagonal sub-tile
+        const int64_t out = sub_index(m, k);
+        if (out < 0) return false;
+        g.tasks[4 * t] = int32_t(out);
+        g.tasks[4 * t + 1] = (m == k) ? int32_t(k) : -1;
+        g.tasks[4 * t + 2] = int32_t(q);
+        for (size_t c = S.size(); c-- > 0;) {  // oldest producer (largest j) first
+          const int64_t j = S[c];
+          int64_t sig;
+          bool tr;
+          if (m == k) { sig = sub_index(j, k); tr = true; }
+          else if (m >= j) { sig = sub_index(m, j); tr = false; }
+          else { sig = sub_index(j, m); tr = true; }
+          if (sig < 0) return false;
+          g.pairs[2 * q] = int32_t(sig) | (tr ? (1 << 30) : 0);
+          g.pairs[2 * q + 1] = int32_t(sub_index(j, k));
+          ++q;
+        }
+        g.tasks[4 * t + 3] = int32_t(q);
+        ++t;
+        return true;
+      };
+      for (int32_t m : S)
+        if (!add_task(m)) { bad = 2; return; }
+      if (!add_task(k)) { bad = 2; return; }
+    }
+  };
+  const int64_t nthreads =
+      std::max<int64_t>(1, std::min<int64_t>({int64_t(std::thread::hardware_concurrency()), 32, p_off[nsb] / 100000 + 1}));
+  if (nthreads == 1) {
+    fill(0, nsb);
+  } else {
+    // split the columns into chunks of about equal pair counts
+    std::vector<std::thread> pool;
+    int64_t r0 = 0;
+    for (int64_t w = 0; w < nthreads; ++w) {
+      const int64_t target = p_off[nsb] * (w + 1) / nthreads;
+      int64_t r1 = (w + 1 == nthreads) ? nsb
+                                        : int64_t(std::lower_bound(p_off.begin(), p_off.end(), target) - p_off.begin());
+      r1 = std::min<int64_t>(std::max<int64_t>(r1, r0), nsb);
+      pool.emplace_back(fill, r0, r1);
+      r0 = r1;
+    }
+    for (auto& th : pool) th.join();
+  }
+  if (bad == 1) { *err = "internal: missing sub-tile"; return STILES_ERR_INVALID; }
+  if (bad == 2) { *err = "internal: selected-inverse operand off the filled map"; return STILES_ERR_INVALID; }
   p->selinv = std::move(g);
   p->selinv_built = true;
   return STILES_OK;
