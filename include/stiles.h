@@ -193,7 +193,12 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
  * 4 CHAIN), output, diagonal sub-tile, column, pair range [pb, pe), partial range [qb, qe),
  * second output, its column, its pair range, its partial range, 2 unused.  Solve tasks are
  * 8 int32: type (0 block, 2 leaf, 3 node), output block, diagonal sub-tile, column, pair
- * range, partial range.  out may be NULL to query ntasks. */
+ * range, partial range.  which = 3 and 4 give the selected inverse's graph (Sigma L = L^{-T}
+ * on the filled sub-tile map, built on the host at the first call): 3 = tasks, 4 int32 each
+ * (output sub-tile, sub-column for the diagonal task else -1, pair range [pb, pe)); 4 = pairs,
+ * 2 int32 each (Sigma sub-tile, bit 30 set when read transposed; U sub-tile; a diagonal task's
+ * pairs name the column's sub-tiles (j, k) twice).  *ntasks receives the number of tasks or
+ * pairs.  out may be NULL to query ntasks. */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */

@@ -939,15 +939,18 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   return STILES_OK;
 }
 
-// Task graph of the selected inverse (Sigma L = L^{-T}, column blocks in
-// reverse): for sub-column k = nsb-1 .. 0, first Sigma_mk = -sum_j Sigma_mj U_jk
+// Task graph of the selected inverse (Sigma L = L^{-T}, every column block
+// after its ancestors): for sub-column k, first Sigma_mk = -sum_j Sigma_mj U_jk
 // for every sub-row m > k present in column k, then
 // Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_j Sigma_jk^T U_jk, with j over the same
 // sub-rows and U_jk = L_jk L_kk^{-1}.  Sigma_mj (m, j > k) lies on the filled map
 // (the tile closure makes the sub-rows of a column a clique); it is stored as
 // (max, min) and read transposed when m < j.  Pairs run from the oldest
-// producer (largest j) to the newest, and every dependency carries a smaller
-// ticket, so the persistent kernel cannot wait on work that has not started.
+// producer (largest j) to the newest.  The task of Sigma_jk also forms the term
+// W(j, k) = Sigma_jk^T U_jk, so the diagonal task's list names the sub-tiles
+// (j, k) whose W it sums (both indices of its pairs are sub(j, k)).  Every
+// dependency carries a smaller ticket, so the persistent kernel cannot wait on
+// work that has not started.
 stiles_status build_selinv(stiles_plan* p, std::string* err) {
   if (p->selinv_built) return STILES_OK;
   if (!p->executable) { *err = "the plan has no sub-tile executor"; return STILES_ERR_UNSUPPORTED; }
@@ -979,12 +982,26 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
         }
       }
     }
-  // Offsets first (columns in reverse: |S_k| + 1 tasks, (|S_k| + 1) |S_k| pairs,
-  // |S_k| U products each), then every column filled independently on host
-  // threads (the largest graphs hold a few hundred million pairs).
+  // Column order: by depth in the sub-column elimination tree (parent = first
+  // sub-row below the diagonal), root first, ties by descending index.  Every
+  // sub-row of S_k is an ancestor of k, so it comes earlier; independent
+  // branches (the two halves of a nested dissection) interleave instead of
+  // running one after the other.
+  std::vector<int64_t> depth(nsb, 0), order(nsb);
+  for (int64_t k = nsb - 1; k >= 0; --k) {
+    int64_t par = -1;
+    for (int32_t j : below[k])
+      if (par < 0 || j < par) par = j;
+    depth[k] = par < 0 ? 0 : depth[par] + 1;
+  }
+  for (int64_t r = 0; r < nsb; ++r) order[r] = nsb - 1 - r;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return depth[x] < depth[y]; });
+  // Offsets next (per column: |S_k| + 1 tasks, (|S_k| + 1) |S_k| pairs, |S_k| U
+  // products), then every column filled independently on host threads (the
+  // largest graphs hold a few hundred million pairs).
   std::vector<int64_t> t_off(nsb + 1, 0), p_off(nsb + 1, 0), u_off(nsb + 1, 0);
-  for (int64_t r = 0; r < nsb; ++r) {  // r-th column in ticket order is k = nsb - 1 - r
-    const int64_t sk = int64_t(below[nsb - 1 - r].size());
+  for (int64_t r = 0; r < nsb; ++r) {  // r-th column in ticket order is order[r]
+    const int64_t sk = int64_t(below[order[r]].size());
     t_off[r + 1] = t_off[r] + sk + 1;
     p_off[r + 1] = p_off[r] + (sk + 1) * sk;
     u_off[r + 1] = u_off[r] + sk;
@@ -997,7 +1014,7 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
   std::atomic<int> bad{0};
   auto fill = [&](int64_t r0, int64_t r1) {
     for (int64_t r = r0; r < r1 && !bad.load(std::memory_order_relaxed); ++r) {
-      const int64_t k = nsb - 1 - r;
+      const int64_t k = order[r];
       std::vector<int32_t>& S = below[k];
       std::sort(S.begin(), S.end());
       int64_t u = u_off[r];
@@ -1019,7 +1036,7 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
           const int64_t j = S[c];
           int64_t sig;
           bool tr;
-          if (m == k) { sig = sub_index(j, k); tr = true; }
+          if (m == k) { sig = sub_index(j, k); tr = false; }  // W(j, k), behind the flag of Sigma_jk
           else if (m >= j) { sig = sub_index(m, j); tr = false; }
           else { sig = sub_index(j, m); tr = true; }
           if (sig < 0) return false;
@@ -1056,6 +1073,23 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
   }
   if (bad == 1) { *err = "internal: missing sub-tile"; return STILES_ERR_INVALID; }
   if (bad == 2) { *err = "internal: selected-inverse operand off the filled map"; return STILES_ERR_INVALID; }
+  // every operand must be produced by a task with a smaller ticket
+  const int64_t ntasks = t_off[nsb];
+  std::vector<int32_t> producer(size_t(p->nsub), INT32_MAX);
+  for (int64_t t = 0; t < ntasks; ++t) producer[size_t(g.tasks[4 * t])] = int32_t(t);
+  auto check = [&](int64_t r0, int64_t r1) {
+    for (int64_t t = t_off[r0]; t < t_off[r1]; ++t)
+      for (int64_t q = g.tasks[4 * t + 2]; q < g.tasks[4 * t + 3]; ++q)
+        if (producer[size_t(g.pairs[2 * q] & ((1 << 30) - 1))] >= t) { bad = 3; return; }
+  };
+  if (nthreads == 1) {
+    check(0, nsb);
+  } else {
+    std::vector<std::thread> pool;
+    for (int64_t w = 0; w < nthreads; ++w) pool.emplace_back(check, nsb * w / nthreads, nsb * (w + 1) / nthreads);
+    for (auto& th : pool) th.join();
+  }
+  if (bad == 3) { *err = "internal: selected-inverse operand not produced earlier"; return STILES_ERR_INVALID; }
   p->selinv = std::move(g);
   p->selinv_built = true;
   return STILES_OK;

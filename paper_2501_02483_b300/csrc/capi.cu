@@ -148,6 +148,7 @@ struct stiles_factor {
   double* sigma = nullptr;
   double* sigmaT = nullptr;            // Sigma's sub-tiles transposed
   double* sinv_u = nullptr;            // (L_jk L_kk^{-1})^T
+  double* sinv_w = nullptr;            // Sigma_jk^T L_jk L_kk^{-1} (terms of Sigma_kk)
   int* sinv_flags = nullptr;
   stiles::dev::Ctl* sinv_ctl = nullptr;
   bool sinv_valid = false;             // Sigma belongs to the current factorization
@@ -327,6 +328,7 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->sigma);
   cudaFree(f->sigmaT);
   cudaFree(f->sinv_u);
+  cudaFree(f->sinv_w);
   cudaFree(f->sinv_flags);
   cudaFree(f->sinv_ctl);
   if (f->done) cudaEventDestroy(f->done);
@@ -1084,6 +1086,12 @@ stiles_status launch_selinv(const stiles_plan* p, stiles_factor* f, cudaStream_t
     CUDA_TRY(cudaGetLastError());
     count_launch();
   }
+  {
+    const int gg = int(std::max<int64_t>(1, std::min<int64_t>(p->nsb, 148 * 16)));
+    dev::selinv_g_kernel<B><<<gg, 128, 0, st>>>(f->sigma, f->linv, d->diag_sub, p->nsb);
+    CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
   static int per_sm = 0;  // resident CTAs of the persistent kernel (per B instantiation)
   if (per_sm == 0) {
     CUDA_TRY(cudaFuncSetAttribute(dev::selinv_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1098,7 +1106,7 @@ stiles_status launch_selinv(const stiles_plan* p, stiles_factor* f, cudaStream_t
   a.sigma = f->sigma;
   a.sigmaT = f->sigmaT;
   a.V = f->sinv_u;
-  a.linv = f->linv;
+  a.W = f->sinv_w;
   a.tasks = d->sinv_tasks;
   a.pairs = d->sinv_pairs;
   a.ntasks = d->sinv_ntasks;
@@ -1142,6 +1150,7 @@ stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
   if (!f->sigma) CUDA_TRY(cudaMalloc(&f->sigma, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sigmaT) CUDA_TRY(cudaMalloc(&f->sigmaT, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_u) CUDA_TRY(cudaMalloc(&f->sinv_u, size_t(p->nsub) * tile * sizeof(double)));
+  if (!f->sinv_w) CUDA_TRY(cudaMalloc(&f->sinv_w, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_flags) CUDA_TRY(cudaMalloc(&f->sinv_flags, size_t(p->nsub) * sizeof(int)));
   if (!f->sinv_ctl) CUDA_TRY(cudaMalloc(&f->sinv_ctl, sizeof(dev::Ctl)));
   if (f->done) CUDA_TRY(cudaStreamWaitEvent(st, f->done, 0));  // the factorization has finished
@@ -1252,7 +1261,19 @@ stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int
 }
 
 stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
-  if (!p || which < 0 || which > 2) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!p || which < 0 || which > 4) return fail(STILES_ERR_INVALID, "bad argument");
+  if (which >= 3) {  // the selected inverse's graph (host only; built on first use)
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    stiles_plan* pm = const_cast<stiles_plan*>(p);
+    std::string err;
+    stiles_status s = build_selinv(pm, &err);
+    if (s != STILES_OK) return fail(s, err);
+    const std::vector<int32_t>& v = which == 3 ? pm->selinv.tasks : pm->selinv.pairs;
+    const size_t width = which == 3 ? 4 : 2;
+    if (ntasks) *ntasks = int64_t(v.size() / width);
+    if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+    return STILES_OK;
+  }
   const void* src;
   size_t n;
   if (which == 0) { src = p->graph.tasks.data(); n = p->graph.tasks.size(); }

@@ -29,11 +29,27 @@ __global__ void selinv_u_kernel(double* __restrict__ V, const double* __restrict
   }
 }
 
+// G_k = L_kk^{-T} L_kk^{-1} into Sigma's diagonal sub-tile of every sub-column
+// (the first term of Sigma_kk), ahead of the persistent launch.
+template <int B>
+__global__ void selinv_g_kernel(double* __restrict__ sigma, const double* __restrict__ linv,
+                                const int32_t* __restrict__ diag_sub, int64_t nsb) {
+  for (int64_t k = blockIdx.x; k < nsb; k += gridDim.x) {
+    const double* Li = linv + k * B * B;
+    for (int o = threadIdx.x; o < B * B; o += blockDim.x) {
+      const int r = o % B, c = o / B;
+      double v = 0.0;
+      for (int p = (r > c ? r : c); p < B; ++p) v = fma(__ldg(Li + p + r * B), __ldg(Li + p + c * B), v);
+      sigma[int64_t(diag_sub[k]) * B * B + o] = v;
+    }
+  }
+}
+
 struct SelinvArgs {
   double* sigma;          // nsub * B * B, same layout as the factor's sub-tiles
   double* sigmaT;         // the same sub-tiles transposed (read where a pair wants Sigma^T)
   const double* V;        // nsub * B * B: U_jk^T at the off-diagonal sub-tiles
-  const double* linv;     // nsb * B * B: L_kk^{-1}
+  double* W;              // nsub * B * B: Sigma_jk^T U_jk at the off-diagonal sub-tiles
   const int32_t* tasks;   // 4 per task (see SelinvGraph)
   const int32_t* pairs;   // 2 per pair
   int ntasks;
@@ -50,13 +66,19 @@ struct SelinvCfg {
 };
 
 // Persistent over the tasks in ticket order (every dependency carries a
-// smaller ticket).  A task accumulates sum_j S_j U_j over its pairs (S_j a
-// Sigma sub-tile, or its transpose -- kept as a second copy -- when bit 30
-// says so; U_j from the transposed U array), with the pairs staged by TMA
-// once the Sigma sub-tile's flag is set, and stores -sum (off-diagonal) or
-// L_kk^{-T} L_kk^{-1} - sum (diagonal), and its transpose.  Thread layout as
-// the FP64 factorization (thread (row, q) holds columns q + RPT m), so both
-// operands are read along rows of the stored tiles (no bank conflicts).
+// smaller ticket).
+//  - Off-diagonal task (m, k): accumulates sum_j S_j U_jk over its pairs (S_j a
+//    Sigma sub-tile, or its transpose -- kept as a second copy -- when bit 30
+//    says so; U from the transposed U array), staged by TMA once the Sigma
+//    sub-tile's flag is set; stores Sigma_mk = -sum and its transpose, and the
+//    term Sigma_mk^T U_mk of the diagonal sub-tile Sigma_kk into W, then
+//    publishes them together.
+//  - Diagonal task k: Sigma_kk = G_k - sum_m W(m, k) over the sub-rows m of
+//    the column (G_k stored in place beforehand), so the column's last step on
+//    the dependency chain is a sum of finished products, not a run of products.
+// Thread layout as the FP64 factorization (thread (row, q) holds columns
+// q + RPT m), so both operands are read along rows of the stored tiles (no
+// bank conflicts).
 template <int B>
 __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
   using Cfg = FactorCfg<B>;
@@ -64,8 +86,8 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
   constexpr int NSTAGE = SelinvCfg<B>::NSTAGE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   double* sStage = reinterpret_cast<double*>(smem_raw);  // NSTAGE * 2 * TILE
-  double* sLi = sStage + NSTAGE * 2 * TILE;               // TILE: L_kk^{-1} of a diagonal task
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sLi + TILE);
+  double* sU = sStage + NSTAGE * 2 * TILE;                // TILE: U_mk^T of an off-diagonal task
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sU + TILE);
   __shared__ int sTicket, sAbort;
   const int tid = threadIdx.x;
   const int row = tid / RPT, q = tid % RPT;
@@ -91,13 +113,57 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
     const int t = sTicket;
     if (t < 0) break;
     const int out = a.tasks[4 * t], dcol = a.tasks[4 * t + 1], pb = a.tasks[4 * t + 2], pe = a.tasks[4 * t + 3];
-    if (dcol >= 0 && tid == 0) {
-      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
-      tma_load_1d(sLi, a.linv + size_t(dcol) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
-    }
+    double* dst = a.sigma + size_t(out) * TILE;
+    double* dstT = a.sigmaT + size_t(out) * TILE;
     double acc[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) acc[m] = 0.0;
+
+    if (dcol >= 0) {
+      // ---- diagonal task: the column's W terms, each behind its sub-tile's flag ----
+      if (tid == 0) {
+        for (int i = pb; i < pe; ++i)
+          if (!wait_flag(a.flags + (a.pairs[2 * i] & kIndexMask), 1, limit, a.ctl)) {
+            raise_timeout(a.ctl, t);
+            sAbort = 1;
+            break;
+          }
+      }
+      __syncthreads();
+      if (sAbort) break;
+      int i = pb;
+      for (; i + 4 <= pe; i += 4) {  // four sub-tiles' loads in flight per thread
+        const double* w0 = a.W + size_t(a.pairs[2 * i] & kIndexMask) * TILE;
+        const double* w1 = a.W + size_t(a.pairs[2 * i + 2] & kIndexMask) * TILE;
+        const double* w2 = a.W + size_t(a.pairs[2 * i + 4] & kIndexMask) * TILE;
+        const double* w3 = a.W + size_t(a.pairs[2 * i + 6] & kIndexMask) * TILE;
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+          const int o = (q + RPT * m) * B + row;
+          acc[m] += (__ldcg(w0 + o) + __ldcg(w1 + o)) + (__ldcg(w2 + o) + __ldcg(w3 + o));
+        }
+      }
+      for (; i < pe; ++i) {
+        const double* w0 = a.W + size_t(a.pairs[2 * i] & kIndexMask) * TILE;
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) acc[m] += __ldcg(w0 + (q + RPT * m) * B + row);
+      }
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) {
+        const int o = (q + RPT * m) * B + row;
+        const double v = dst[o] - acc[m];  // dst holds G_k
+        dst[o] = v;
+        dstT[row * B + q + RPT * m] = v;
+      }
+      publish(a.flags + out);
+      continue;
+    }
+
+    // ---- off-diagonal task ----
+    if (tid == 0) {  // U_mk^T for the W term, into its own buffer
+      mbar_arrive_expect_tx(&bars[NSTAGE], uint32_t(TILE * sizeof(double)));
+      tma_load_1d(sU, a.V + size_t(out) * TILE, TILE * sizeof(double), &bars[NSTAGE]);
+    }
     const int nitems = pe - pb;
     int issued = 0, stop = nitems;
     bool aborted = false;
@@ -118,11 +184,11 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
           }
           fence_proxy_async_global();
           const int st = issued % NSTAGE;
-          double* dst = sStage + st * 2 * TILE;
+          double* d = sStage + st * 2 * TILE;
           mbar_arrive_expect_tx(&bars[st], uint32_t(2 * TILE * sizeof(double)));
           const double* src = ((raw >> 30) & 1) ? a.sigmaT : a.sigma;
-          tma_load_1d(dst, src + size_t(sg) * TILE, TILE * sizeof(double), &bars[st]);
-          tma_load_1d(dst + TILE, a.V + size_t(su) * TILE, TILE * sizeof(double), &bars[st]);
+          tma_load_1d(d, src + size_t(sg) * TILE, TILE * sizeof(double), &bars[st]);
+          tma_load_1d(d + TILE, a.V + size_t(su) * TILE, TILE * sizeof(double), &bars[st]);
           ++issued;
         }
       }
@@ -147,6 +213,12 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
       }
       __syncthreads();  // stage `st` may be refilled
     }
+    if (!aborted) {
+      long long spins = 0;
+      while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
+        if (++spins > kTmaWaitLimit) { aborted = true; break; }
+      }
+    }
     if (aborted) {
       if (tid == 0) {
         for (int j = stop; j < issued; ++j) {
@@ -155,44 +227,36 @@ __global__ void __launch_bounds__(128) selinv_kernel(SelinvArgs a) {
           while (!mbar_try_wait(&bars[st], (phase >> st) & 1u) && ++spins < kTmaWaitLimit) {
           }
         }
-        if (dcol >= 0) {
-          long long spins = 0;
-          while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u) && ++spins < kTmaWaitLimit) {
-          }
+        long long spins = 0;
+        while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u) && ++spins < kTmaWaitLimit) {
         }
       }
       break;
     }
-    double v[CPT];
-    if (dcol >= 0) {
-      {
-        long long spins = 0;
-        while (!mbar_try_wait(&bars[NSTAGE], (phase >> NSTAGE) & 1u)) {
-          if (++spins > kTmaWaitLimit) { aborted = true; break; }
-        }
-      }
-      if (aborted) break;
-      phase ^= (1u << NSTAGE);
-      // L_kk^{-T} L_kk^{-1} (row, c) = sum_p Li(p, row) Li(p, c)
-#pragma unroll
-      for (int m = 0; m < CPT; ++m) v[m] = -acc[m];
-#pragma unroll 4
-      for (int p = 0; p < B; ++p) {
-        const double lr = sLi[p + row * B];
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) v[m] = fma(lr, sLi[p + (q + RPT * m) * B], v[m]);
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < CPT; ++m) v[m] = -acc[m];
-    }
-    double* dst = a.sigma + size_t(out) * TILE;
-    double* dstT = a.sigmaT + size_t(out) * TILE;
+    phase ^= (1u << NSTAGE);
+    // Sigma_mk = -acc; its transpose goes to stage 0 (every stage has been
+    // consumed) as the left operand of W = Sigma_mk^T U_mk
+    double* sT = sStage;
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
-      dst[(q + RPT * m) * B + row] = v[m];
-      dstT[row * B + q + RPT * m] = v[m];
+      const double v = -acc[m];
+      dst[(q + RPT * m) * B + row] = v;
+      dstT[row * B + q + RPT * m] = v;
+      sT[q + RPT * m + row * B] = v;
     }
+    __syncthreads();
+    double w[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) w[m] = 0.0;
+#pragma unroll 4
+    for (int p = 0; p < B; ++p) {
+      const double sv = sT[row + p * B];
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) w[m] = fma(sv, sU[q + RPT * m + p * B], w[m]);
+    }
+    double* dW = a.W + size_t(out) * TILE;
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) dW[(q + RPT * m) * B + row] = w[m];
     publish(a.flags + out);
   }
 }

@@ -196,10 +196,13 @@ class Plan:
         return tc, tr
 
     def tasks(self, which=0):
-        """Device task list (ticket order): int32 (ntasks, 16) for the factorization, (ntasks, 8) for a sweep."""
+        """Device task list (ticket order): int32 (ntasks, 16) for the factorization, (ntasks, 8)
+        for a sweep (which 1, 2); the selected inverse's tasks (which 3: (ntasks, 4)) and pairs
+        (which 4: (npairs, 2))."""
         n = c_int64(0)
         _check(lib().stiles_plan_tasks(self._h, which, None, ctypes.byref(n)))
-        out = np.empty((n.value, 16 if which == 0 else 8), dtype=np.int32)
+        width = {0: 16, 1: 8, 2: 8, 3: 4, 4: 2}[which]
+        out = np.empty((n.value, width), dtype=np.int32)
         _check(lib().stiles_plan_tasks(self._h, which, _ptr(out), ctypes.byref(n)))
         return out
 

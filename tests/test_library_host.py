@@ -171,3 +171,83 @@ def test_task_order_is_topological_and_interleaves_nd_parts():
     half = 2000 // 16
     first = diag_cols[:40]
     assert np.any(first < half) and np.any((first >= half) & (first < 2 * half))
+
+
+def _selinv_graph_case(T, B, order):
+    m = inputs.band_arrow(1000, 24, 40, 0.3, 5)  # n = 1024: no padding at T, B in {16, 32}
+    plan = st.Plan.from_matrix(m, tile=T, block=B, ordering=order)
+    return m, plan
+
+
+@pytest.mark.parametrize("T,B,order", [(16, 16, st.ORDER_ND), (32, 16, st.ORDER_ND), (32, 32, st.ORDER_RCM),
+                                       (16, 16, st.ORDER_NONE)])
+def test_selected_inverse_graph_executes_to_the_dense_inverse(T, B, order):
+    """Runs the selected inverse's host-built task graph in ticket order with
+    numpy (the semantics the persistent kernel implements: off-diagonal tasks
+    Sigma_mk = -sum S U and W = Sigma_mk^T U_mk, diagonal tasks
+    L_kk^{-T} L_kk^{-1} - sum W) and checks every Sigma sub-tile against the
+    dense inverse of P A P^T.  Also checks that each operand is produced by an
+    earlier ticket and that every sub-tile is produced once."""
+    m, plan = _selinv_graph_case(T, B, order)
+    n = m["n"]
+    A = inputs.dense_from_csc(m)
+    perm = plan.perm()
+    Ap = A[np.ix_(perm, perm)]
+    Lf = np.linalg.cholesky(Ap)
+    Sig = np.linalg.inv(Ap)
+    tc, tr = plan.tilemap()
+    R = T // B
+    nsb = n // B
+    # sub-tile index -> (sub-row, sub-column), as the library numbers them
+    where = {}
+    for J in range(len(tc) - 1):
+        for e in range(tc[J], tc[J + 1]):
+            I = tr[e]
+            for q in range(R):
+                for p in range(R):
+                    ii, jj = I * R + p, J * R + q
+                    if ii >= jj and ii < nsb and jj < nsb:
+                        where[e * R * R + q * R + p] = (ii, jj)
+    blk = lambda M, ii, jj: M[ii * B:(ii + 1) * B, jj * B:(jj + 1) * B]
+    tasks, pairs = plan.tasks(3), plan.tasks(4)
+    outs = tasks[:, 0]
+    assert len(np.unique(outs)) == len(outs) == len(where)
+    ticket = {int(o): t for t, o in enumerate(outs)}
+    mask = (1 << 30) - 1
+    linv = {k: np.linalg.inv(blk(Lf, k, k)) for k in range(nsb)}
+    S, W = {}, {}
+    for t, (out, dcol, pb, pe) in enumerate(tasks):
+        ii, k = where[int(out)]
+        for sg, su in pairs[pb:pe]:
+            assert ticket[int(sg) & mask] < t
+        if dcol >= 0:
+            assert dcol == k == ii
+            assert np.all(pairs[pb:pe, 0] == pairs[pb:pe, 1]) and not np.any(pairs[pb:pe, 0] >> 30)
+            v = linv[k].T @ linv[k]
+            for sg, _ in pairs[pb:pe]:
+                v = v - W[int(sg)]
+        else:
+            acc = np.zeros((B, B))
+            for sg, su in pairs[pb:pe]:
+                s = S[int(sg) & mask]
+                j, kk = where[int(su)]
+                assert kk == k
+                acc += (s.T if (int(sg) >> 30) & 1 else s) @ (blk(Lf, j, k) @ linv[k])
+            v = -acc
+            W[int(out)] = v.T @ (blk(Lf, ii, k) @ linv[k])
+        S[int(out)] = v
+        assert np.allclose(v, blk(Sig, ii, k), rtol=1e-9, atol=1e-12 * np.abs(Sig).max())
+
+
+def test_selected_inverse_graph_interleaves_nd_halves():
+    """Columns are ordered by elimination-tree depth, so the two nested-dissection
+    halves' diagonal tasks alternate rather than one half waiting for the other."""
+    m = inputs.band_arrow(4000, 10, 20, 0.5, 2)
+    plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_ND)
+    tasks = plan.tasks(3)
+    cols = tasks[tasks[:, 1] >= 0, 1]
+    assert len(cols) == -(-m["n"] // 16) and len(np.unique(cols)) == len(cols)
+    half = 2000 // 16
+    body = cols[cols < 4000 // 16]
+    first = body[:40]
+    assert np.any(first < half) and np.any((first >= half) & (first < 2 * half))
