@@ -181,10 +181,11 @@ const char* stiles_last_error(void);
 stiles_status stiles_factor_timing(const stiles_factor* factor, double* ms_call, double* ms_kernel);
 
 /* Tracing (profiling aid).  When enabled, every persistent launch of `factor` (factorization,
- * forward and backward sweeps) stamps each ticket with the device global timer: 4 int64 per
- * task = start, all dependencies ready, done (ns), SM id.  Tracing costs a few global stores
- * per task.  stiles_factor_get_trace copies the stamps of launch `which` (0 factorization,
- * 1 forward, 2 backward) to the host array out[4 * ntasks]; out may be NULL to query ntasks. */
+ * forward and backward sweeps, selected inverse) stamps each ticket with the device global
+ * timer: 4 int64 per task = start, all dependencies ready, done (ns), SM id.  Tracing costs a
+ * few global stores per task.  stiles_factor_get_trace copies the stamps of launch `which`
+ * (0 factorization, 1 forward, 2 backward, 3 selected inverse) to the host array
+ * out[4 * ntasks]; out may be NULL to query ntasks. */
 stiles_status stiles_factor_set_trace(stiles_factor* factor, int32_t enable);
 stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which, int64_t* out, int64_t* ntasks);
 
@@ -193,12 +194,15 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
  * 4 CHAIN), output, diagonal sub-tile, column, pair range [pb, pe), partial range [qb, qe),
  * second output, its column, its pair range, its partial range, 2 unused.  Solve tasks are
  * 8 int32: type (0 block, 2 leaf, 3 node), output block, diagonal sub-tile, column, pair
- * range, partial range.  which = 3 and 4 give the selected inverse's graph (Sigma L = L^{-T}
- * on the filled sub-tile map, built on the host at the first call): 3 = tasks, 4 int32 each
- * (output sub-tile, sub-column for the diagonal task else -1, pair range [pb, pe)); 4 = pairs,
- * 2 int32 each (Sigma sub-tile, bit 30 set when read transposed; U sub-tile; a diagonal task's
- * pairs name the column's sub-tiles (j, k) twice).  *ntasks receives the number of tasks or
- * pairs.  out may be NULL to query ntasks. */
+ * range, partial range.  which = 3..6 give the selected inverse's graph (Sigma L = L^{-T} on
+ * the filled sub-tile map, built on the host at the first call): 3 = tasks, 8 int32 each
+ * (output sub-tile; the sub-column for a diagonal task, else -1; product range [pb, pe); load
+ * range [lb, le); X-product range [xb, xe)); 4 = products, 2 int32 each (Sigma sub-tile, bit 30
+ * set when read transposed; U sub-tile); 5 = loads of finished terms, 3 int32 each (the Sigma
+ * sub-tile whose flag guards the term; the flag value it waits for (1); term sub-tile, bit 30
+ * set when the term is in W (a diagonal task's terms), else in X);
+ * 6 = X products, 1 int32 each (sub-tile of U and X).  *ntasks receives the number of
+ * entries.  out may be NULL to query ntasks. */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */

@@ -940,16 +940,19 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
 }
 
 // Task graph of the selected inverse (Sigma L = L^{-T}, every column block
-// after its ancestors): for sub-column k, first Sigma_mk = -sum_j Sigma_mj U_jk
-// for every sub-row m > k present in column k, then
-// Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_j Sigma_jk^T U_jk, with j over the same
-// sub-rows and U_jk = L_jk L_kk^{-1}.  Sigma_mj (m, j > k) lies on the filled map
-// (the tile closure makes the sub-rows of a column a clique); it is stored as
-// (max, min) and read transposed when m < j.  Pairs run from the oldest
-// producer (largest j) to the newest.  The task of Sigma_jk also forms the term
-// W(j, k) = Sigma_jk^T U_jk, so the diagonal task's list names the sub-tiles
-// (j, k) whose W it sums (both indices of its pairs are sub(j, k)).  Every
-// dependency carries a smaller ticket, so the persistent kernel cannot wait on
+// after its ancestors).  For sub-column k with sub-rows S_k (p = min S_k, its
+// parent in the sub-column elimination tree) and U_jk = L_jk L_kk^{-1}:
+//   Sigma_mk = -sum_{j in S_k} Sigma_mj U_jk   (m in S_k),
+//   Sigma_kk = L_kk^{-T} L_kk^{-1} - sum_{j in S_k} Sigma_jk^T U_jk.
+// Sigma_mj (m, j > k) lies on the filled map (the tile closure makes S_k a
+// clique); it is stored as (max, min) and read transposed when m < j.  For the
+// parent row m = p every term but Sigma_pp U_pk comes from column p itself, so
+// those terms X(j, k) = Sigma_jp^T U_jk are formed by the tasks of column p
+// (their X products) and the task of Sigma_pk only loads them; likewise the
+// task of Sigma_jk forms W(j, k) = Sigma_jk^T U_jk and the diagonal task loads
+// the W terms.  Products run from the oldest producer (largest j) to the
+// newest.  Every operand and every loaded term is published by a task with a
+// smaller ticket (checked below), so the persistent kernel cannot wait on
 // work that has not started.
 stiles_status build_selinv(stiles_plan* p, std::string* err) {
   if (p->selinv_built) return STILES_OK;
@@ -987,36 +990,53 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
   // sub-row of S_k is an ancestor of k, so it comes earlier; independent
   // branches (the two halves of a nested dissection) interleave instead of
   // running one after the other.
-  std::vector<int64_t> depth(nsb, 0), order(nsb);
+  std::vector<int64_t> depth(nsb, 0), parent(nsb, -1), order(nsb);
+  std::vector<std::vector<int32_t>> children(nsb);
   for (int64_t k = nsb - 1; k >= 0; --k) {
-    int64_t par = -1;
-    for (int32_t j : below[k])
-      if (par < 0 || j < par) par = j;
-    depth[k] = par < 0 ? 0 : depth[par] + 1;
+    std::vector<int32_t>& S = below[k];
+    std::sort(S.begin(), S.end());
+    parent[k] = S.empty() ? -1 : S[0];
+    depth[k] = S.empty() ? 0 : depth[S[0]] + 1;
   }
+  for (int64_t c = 0; c < nsb; ++c)
+    if (parent[c] >= 0) children[parent[c]].push_back(int32_t(c));
   for (int64_t r = 0; r < nsb; ++r) order[r] = nsb - 1 - r;
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return depth[x] < depth[y]; });
-  // Offsets next (per column: |S_k| + 1 tasks, (|S_k| + 1) |S_k| pairs, |S_k| U
-  // products), then every column filled independently on host threads (the
-  // largest graphs hold a few hundred million pairs).
-  std::vector<int64_t> t_off(nsb + 1, 0), p_off(nsb + 1, 0), u_off(nsb + 1, 0);
-  for (int64_t r = 0; r < nsb; ++r) {  // r-th column in ticket order is order[r]
-    const int64_t sk = int64_t(below[order[r]].size());
+  // Per column (s = |S_k|): s + 1 tasks, 1 + (s - 1) s products, 2 s - 1 loads,
+  // sum over the children c of (|S_c| - 1) X products, s U products.  Every
+  // column is filled independently on host threads (the largest graphs hold a
+  // few hundred million products).
+  std::vector<int64_t> t_off(nsb + 1, 0), p_off(nsb + 1, 0), l_off(nsb + 1, 0), x_off(nsb + 1, 0),
+      u_off(nsb + 1, 0);
+  for (int64_t r = 0; r < nsb; ++r) {  // r-th column in depth order is order[r]
+    const int64_t k = order[r];
+    const int64_t sk = int64_t(below[k].size());
+    int64_t nx = 0;
+    for (int32_t c : children[k]) nx += int64_t(below[c].size()) - 1;
     t_off[r + 1] = t_off[r] + sk + 1;
-    p_off[r + 1] = p_off[r] + (sk + 1) * sk;
+    p_off[r + 1] = p_off[r] + (sk ? 1 + (sk - 1) * sk : 0);
+    l_off[r + 1] = l_off[r] + (sk ? 2 * sk - 1 : 0);
+    x_off[r + 1] = x_off[r] + nx;
     u_off[r + 1] = u_off[r] + sk;
   }
-  if (p_off[nsb] >= (int64_t(1) << 31)) { *err = "selected inverse too large"; return STILES_ERR_UNSUPPORTED; }
+  if (p_off[nsb] >= (int64_t(1) << 31) || t_off[nsb] >= (int64_t(1) << 31) || l_off[nsb] >= (int64_t(1) << 31)) {
+    *err = "selected inverse too large";
+    return STILES_ERR_UNSUPPORTED;
+  }
+  const int64_t ntasks = t_off[nsb];
+  std::vector<int64_t> producer(size_t(p->nsub), -1);  // ticket of the task that publishes a sub-tile
   SelinvGraph g;
-  g.tasks.resize(size_t(4 * t_off[nsb]));
+  g.tasks.resize(size_t(8 * ntasks));
   g.pairs.resize(size_t(2 * p_off[nsb]));
+  g.loads.resize(size_t(3 * l_off[nsb]));
+  g.posts.resize(size_t(x_off[nsb]));
   g.ulist.resize(size_t(2 * u_off[nsb]));
   std::atomic<int> bad{0};
+  const int64_t WBIT = int64_t(1) << 30;  // term index flag: the term lives in W (else X)
   auto fill = [&](int64_t r0, int64_t r1) {
     for (int64_t r = r0; r < r1 && !bad.load(std::memory_order_relaxed); ++r) {
       const int64_t k = order[r];
-      std::vector<int32_t>& S = below[k];
-      std::sort(S.begin(), S.end());
+      const std::vector<int32_t>& S = below[k];
       int64_t u = u_off[r];
       for (int32_t j : S) {
         const int64_t sj = sub_index(j, k);
@@ -1025,40 +1045,96 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
         g.ulist[2 * u + 1] = int32_t(k);
         ++u;
       }
-      int64_t t = t_off[r], q = p_off[r];
-      auto add_task = [&](int64_t m) -> bool {  // m == k: the diagonal sub-tile
+      int64_t t = t_off[r], q = p_off[r], l = l_off[r], x = x_off[r];
+      auto load = [&](int64_t flag, int64_t want, int64_t term) {
+        g.loads[3 * l] = int32_t(flag);
+        g.loads[3 * l + 1] = int32_t(want);
+        g.loads[3 * l + 2] = int32_t(term);
+        ++l;
+      };
+      // opens task t; close() records its ranges' ends
+      auto open = [&](int64_t out, int32_t kind) -> int32_t* {
+        int32_t* tk = &g.tasks[8 * t];
+        tk[0] = int32_t(out);
+        tk[1] = kind;
+        tk[2] = int32_t(q);
+        tk[4] = int32_t(l);
+        tk[6] = int32_t(x);
+        producer[size_t(out)] = t;
+        return tk;
+      };
+      auto close = [&](int32_t* tk) {
+        tk[3] = int32_t(q);
+        tk[5] = int32_t(l);
+        tk[7] = int32_t(x);
+        ++t;
+      };
+      auto posts = [&](int64_t m) -> bool {
+        // X(m, c) = Sigma_mk^T U_mc for every child c of k whose column holds row m
+        for (int32_t c : children[k]) {
+          const std::vector<int32_t>& Sc = below[c];
+          if (std::binary_search(Sc.begin() + 1, Sc.end(), int32_t(m))) {
+            const int64_t xs = sub_index(m, c);
+            if (xs < 0) return false;
+            g.posts[x++] = int32_t(xs);
+          }
+        }
+        return true;
+      };
+      for (int32_t m : S) {
         const int64_t out = sub_index(m, k);
-        if (out < 0) return false;
-        g.tasks[4 * t] = int32_t(out);
-        g.tasks[4 * t + 1] = (m == k) ? int32_t(k) : -1;
-        g.tasks[4 * t + 2] = int32_t(q);
-        for (size_t c = S.size(); c-- > 0;) {  // oldest producer (largest j) first
+        if (out < 0) { bad = 2; return; }
+        if (m == S[0]) {
+          // the parent row: Sigma_pk = -(Sigma_pp U_pk + sum_{j > p} X(j, k)),
+          // X(j, k) = Sigma_jp^T U_jk formed by the task of Sigma_jp
+          const int64_t pp = sub_index(m, m);
+          if (pp < 0) { bad = 2; return; }
+          int32_t* tk = open(out, -1);
+          g.pairs[2 * q] = int32_t(pp);
+          g.pairs[2 * q + 1] = int32_t(sub_index(m, k));
+          ++q;
+          for (size_t c = 1; c < S.size(); ++c) {
+            const int64_t fj = sub_index(S[c], m), xj = sub_index(S[c], k);
+            if (fj < 0 || xj < 0) { bad = 2; return; }
+            load(fj, 1, xj);
+          }
+          if (!posts(m)) { bad = 2; return; }
+          close(tk);
+          continue;
+        }
+        // products, oldest producer (largest j) first
+        int32_t* tk = open(out, -1);
+        for (size_t c = S.size(); c-- > 0;) {
           const int64_t j = S[c];
           int64_t sig;
           bool tr;
-          if (m == k) { sig = sub_index(j, k); tr = false; }  // W(j, k), behind the flag of Sigma_jk
-          else if (m >= j) { sig = sub_index(m, j); tr = false; }
+          if (m >= j) { sig = sub_index(m, j); tr = false; }
           else { sig = sub_index(j, m); tr = true; }
-          if (sig < 0) return false;
-          g.pairs[2 * q] = int32_t(sig) | (tr ? (1 << 30) : 0);
+          if (sig < 0) { bad = 2; return; }
+          g.pairs[2 * q] = int32_t(sig | (tr ? WBIT : 0));
           g.pairs[2 * q + 1] = int32_t(sub_index(j, k));
           ++q;
         }
-        g.tasks[4 * t + 3] = int32_t(q);
-        ++t;
-        return true;
-      };
-      for (int32_t m : S)
-        if (!add_task(m)) { bad = 2; return; }
-      if (!add_task(k)) { bad = 2; return; }
+        if (!posts(m)) { bad = 2; return; }
+        close(tk);
+      }
+      // Sigma_kk = G_k - sum_j W(j, k), each behind the flag of Sigma_jk
+      const int64_t outd = sub_index(k, k);
+      if (outd < 0) { bad = 2; return; }
+      int32_t* tk = open(outd, int32_t(k));
+      for (int32_t j : S) load(sub_index(j, k), 1, sub_index(j, k) | WBIT);
+      close(tk);
+      if (t != t_off[r + 1] || q != p_off[r + 1] || l != l_off[r + 1] || x != x_off[r + 1]) { bad = 4; return; }
     }
   };
   const int64_t nthreads =
       std::max<int64_t>(1, std::min<int64_t>({int64_t(std::thread::hardware_concurrency()), 32, p_off[nsb] / 100000 + 1}));
-  if (nthreads == 1) {
-    fill(0, nsb);
-  } else {
-    // split the columns into chunks of about equal pair counts
+  auto run = [&](auto&& fn) {
+    if (nthreads == 1) {
+      fn(0, nsb);
+      return;
+    }
+    // chunks of about equal product counts
     std::vector<std::thread> pool;
     int64_t r0 = 0;
     for (int64_t w = 0; w < nthreads; ++w) {
@@ -1066,27 +1142,32 @@ stiles_status build_selinv(stiles_plan* p, std::string* err) {
       int64_t r1 = (w + 1 == nthreads) ? nsb
                                         : int64_t(std::lower_bound(p_off.begin(), p_off.end(), target) - p_off.begin());
       r1 = std::min<int64_t>(std::max<int64_t>(r1, r0), nsb);
-      pool.emplace_back(fill, r0, r1);
+      pool.emplace_back(fn, r0, r1);
       r0 = r1;
     }
     for (auto& th : pool) th.join();
-  }
+  };
+  run(fill);
   if (bad == 1) { *err = "internal: missing sub-tile"; return STILES_ERR_INVALID; }
   if (bad == 2) { *err = "internal: selected-inverse operand off the filled map"; return STILES_ERR_INVALID; }
-  // every operand must be produced by a task with a smaller ticket
-  const int64_t ntasks = t_off[nsb];
-  std::vector<int32_t> producer(size_t(p->nsub), INT32_MAX);
-  for (int64_t t = 0; t < ntasks; ++t) producer[size_t(g.tasks[4 * t])] = int32_t(t);
-  auto check = [&](int64_t r0, int64_t r1) {
-    for (int64_t t = t_off[r0]; t < t_off[r1]; ++t)
-      for (int64_t q = g.tasks[4 * t + 2]; q < g.tasks[4 * t + 3]; ++q)
-        if (producer[size_t(g.pairs[2 * q] & ((1 << 30) - 1))] >= t) { bad = 3; return; }
+  if (bad == 4) { *err = "internal: selected-inverse counts"; return STILES_ERR_INVALID; }
+  // every operand and every loaded term must come from a task with a smaller ticket
+  auto check = [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const int32_t* tk = &g.tasks[8 * i];
+      for (int64_t q = tk[2]; q < tk[3]; ++q) {
+        const int64_t pt = producer[size_t(g.pairs[2 * q] & ((1 << 30) - 1))];
+        if (pt < 0 || pt >= i) { bad = 3; return; }
+      }
+      for (int64_t l = tk[4]; l < tk[5]; ++l) {
+        const int64_t pt = producer[size_t(g.loads[3 * l])];
+        if (pt < 0 || pt >= i || g.loads[3 * l + 1] != 1) { bad = 3; return; }
+      }
+    }
   };
-  if (nthreads == 1) {
-    check(0, nsb);
-  } else {
+  {
     std::vector<std::thread> pool;
-    for (int64_t w = 0; w < nthreads; ++w) pool.emplace_back(check, nsb * w / nthreads, nsb * (w + 1) / nthreads);
+    for (int64_t w = 0; w < nthreads; ++w) pool.emplace_back(check, ntasks * w / nthreads, ntasks * (w + 1) / nthreads);
     for (auto& th : pool) th.join();
   }
   if (bad == 3) { *err = "internal: selected-inverse operand not produced earlier"; return STILES_ERR_INVALID; }

@@ -95,6 +95,8 @@ struct DevPlan {
   // selected inverse (uploaded on first use)
   int32_t* sinv_tasks = nullptr;
   int32_t* sinv_pairs = nullptr;
+  int32_t* sinv_loads = nullptr;
+  int32_t* sinv_posts = nullptr;
   int32_t* sinv_ulist = nullptr;
   int sinv_ntasks = 0;
   int64_t sinv_nu = 0;
@@ -140,7 +142,9 @@ struct stiles_factor {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, persistent kernel start / end
-  long long* trace[3] = {nullptr, nullptr, nullptr};  // per-ticket stamps: factor, forward, backward
+  long long* trace[4] = {nullptr, nullptr, nullptr, nullptr};  // per-ticket stamps: factor, forward, backward,
+                                                              // selected inverse (allocated at its launch)
+  bool trace_on = false;
   unsigned long long* info = nullptr;  // first bad pivot column (&ctl[0].info, or a batch slot)
   bool view = false;                   // tiles and values belong to a stiles_batch
   bool pending = false;
@@ -149,6 +153,7 @@ struct stiles_factor {
   double* sigmaT = nullptr;            // Sigma's sub-tiles transposed
   double* sinv_u = nullptr;            // (L_jk L_kk^{-1})^T
   double* sinv_w = nullptr;            // Sigma_jk^T L_jk L_kk^{-1} (terms of Sigma_kk)
+  double* sinv_x = nullptr;            // Sigma_mp^T L_mc L_cc^{-1}, p the parent of c (terms of Sigma_pc)
   int* sinv_flags = nullptr;
   stiles::dev::Ctl* sinv_ctl = nullptr;
   bool sinv_valid = false;             // Sigma belongs to the current factorization
@@ -185,6 +190,8 @@ void free_dev_plan(stiles_plan* p) {
   free_graph(d->bwd);
   cudaFree(d->sinv_tasks);
   cudaFree(d->sinv_pairs);
+  cudaFree(d->sinv_loads);
+  cudaFree(d->sinv_posts);
   cudaFree(d->sinv_ulist);
   delete d;
   p->dev = nullptr;
@@ -329,6 +336,7 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->sigmaT);
   cudaFree(f->sinv_u);
   cudaFree(f->sinv_w);
+  cudaFree(f->sinv_x);
   cudaFree(f->sinv_flags);
   cudaFree(f->sinv_ctl);
   if (f->done) cudaEventDestroy(f->done);
@@ -1107,12 +1115,21 @@ stiles_status launch_selinv(const stiles_plan* p, stiles_factor* f, cudaStream_t
   a.sigmaT = f->sigmaT;
   a.V = f->sinv_u;
   a.W = f->sinv_w;
+  a.X = f->sinv_x;
   a.tasks = d->sinv_tasks;
   a.pairs = d->sinv_pairs;
+  a.loads = d->sinv_loads;
+  a.posts = d->sinv_posts;
   a.ntasks = d->sinv_ntasks;
   a.flags = f->sinv_flags;
   a.ctl = f->sinv_ctl;
   a.spin_limit = p->opts.spin_limit;
+  if (f->trace_on && !f->trace[3]) {
+    const size_t bytes = size_t(d->sinv_ntasks) * 4 * sizeof(long long);
+    CUDA_TRY(cudaMalloc(&f->trace[3], bytes));
+    CUDA_TRY(cudaMemsetAsync(f->trace[3], 0, bytes, st));
+  }
+  a.trace = f->trace_on ? f->trace[3] : nullptr;
   const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(per_sm) * sms, d->sinv_ntasks)));
   dev::selinv_kernel<B><<<grid, 128, dev::SelinvCfg<B>::SMEM, st>>>(a);
   CUDA_TRY(cudaGetLastError());
@@ -1134,13 +1151,15 @@ stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
     if (!d->sinv_ready) {
       cudaError_t e = upload(&d->sinv_tasks, pm->selinv.tasks);
       if (e == cudaSuccess) e = upload(&d->sinv_pairs, pm->selinv.pairs);
+      if (e == cudaSuccess) e = upload(&d->sinv_loads, pm->selinv.loads);
+      if (e == cudaSuccess) e = upload(&d->sinv_posts, pm->selinv.posts);
       if (e == cudaSuccess) e = upload(&d->sinv_ulist, pm->selinv.ulist);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
                     std::string("selected-inverse upload: ") + cudaGetErrorString(e));
       }
-      d->sinv_ntasks = int(pm->selinv.tasks.size() / 4);
+      d->sinv_ntasks = int(pm->selinv.tasks.size() / 8);
       d->sinv_nu = int64_t(pm->selinv.ulist.size() / 2);
       d->sinv_ready = true;
     }
@@ -1151,6 +1170,7 @@ stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
   if (!f->sigmaT) CUDA_TRY(cudaMalloc(&f->sigmaT, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_u) CUDA_TRY(cudaMalloc(&f->sinv_u, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_w) CUDA_TRY(cudaMalloc(&f->sinv_w, size_t(p->nsub) * tile * sizeof(double)));
+  if (!f->sinv_x) CUDA_TRY(cudaMalloc(&f->sinv_x, size_t(p->nsub) * tile * sizeof(double)));
   if (!f->sinv_flags) CUDA_TRY(cudaMalloc(&f->sinv_flags, size_t(p->nsub) * sizeof(int)));
   if (!f->sinv_ctl) CUDA_TRY(cudaMalloc(&f->sinv_ctl, sizeof(dev::Ctl)));
   if (f->done) CUDA_TRY(cudaStreamWaitEvent(st, f->done, 0));  // the factorization has finished
@@ -1236,8 +1256,9 @@ stiles_status stiles_factor_timing(const stiles_factor* f, double* ms_call, doub
 stiles_status stiles_factor_set_trace(stiles_factor* f, int32_t enable) {
   if (!f) return fail(STILES_ERR_INVALID, "null factor");
   const stiles_plan* p = f->plan;
-  const size_t n[3] = {p->graph.tasks.size(), p->fwd.tasks.size(), p->bwd.tasks.size()};
-  for (int i = 0; i < 3; ++i) {
+  const size_t n[4] = {p->graph.tasks.size(), p->fwd.tasks.size(), p->bwd.tasks.size(), 0};
+  f->trace_on = enable != 0;
+  for (int i = 0; i < 4; ++i) {
     cudaFree(f->trace[i]);
     f->trace[i] = nullptr;
     if (enable && n[i]) {
@@ -1249,9 +1270,12 @@ stiles_status stiles_factor_set_trace(stiles_factor* f, int32_t enable) {
 }
 
 stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int64_t* out, int64_t* ntasks) {
-  if (!f || which < 0 || which > 2) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!f || which < 0 || which > 3) return fail(STILES_ERR_INVALID, "bad argument");
   const stiles_plan* p = f->plan;
-  const size_t n = which == 0 ? p->graph.tasks.size() : (which == 1 ? p->fwd.tasks.size() : p->bwd.tasks.size());
+  const size_t n = which == 0   ? p->graph.tasks.size()
+                   : which == 1 ? p->fwd.tasks.size()
+                   : which == 2 ? p->bwd.tasks.size()
+                                : (p->selinv_built ? p->selinv.tasks.size() / 8 : 0);
   if (ntasks) *ntasks = int64_t(n);
   if (!out) return STILES_OK;
   if (!f->trace[which]) return fail(STILES_ERR_INVALID, "tracing is not enabled");
@@ -1261,15 +1285,18 @@ stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int
 }
 
 stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
-  if (!p || which < 0 || which > 4) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!p || which < 0 || which > 6) return fail(STILES_ERR_INVALID, "bad argument");
   if (which >= 3) {  // the selected inverse's graph (host only; built on first use)
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     stiles_plan* pm = const_cast<stiles_plan*>(p);
     std::string err;
     stiles_status s = build_selinv(pm, &err);
     if (s != STILES_OK) return fail(s, err);
-    const std::vector<int32_t>& v = which == 3 ? pm->selinv.tasks : pm->selinv.pairs;
-    const size_t width = which == 3 ? 4 : 2;
+    const std::vector<int32_t>& v = which == 3   ? pm->selinv.tasks
+                                    : which == 4 ? pm->selinv.pairs
+                                    : which == 5 ? pm->selinv.loads
+                                                 : pm->selinv.posts;
+    const size_t width = which == 3 ? 8 : which == 6 ? 1 : which == 5 ? 3 : 2;
     if (ntasks) *ntasks = int64_t(v.size() / width);
     if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
     return STILES_OK;

@@ -31,6 +31,15 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Relaxed load: several can be in flight at once (an acquire load orders every
+// later access after it, so a run of them costs one round trip each); a run of
+// relaxed loads followed by fence_acq_rel_gpu() acquires them all together.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ int ld_volatile(const int* p) {
   int v;
   asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -92,6 +101,50 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int want, long long l
     if ((it & 255) == 255 && ld_volatile(&ctl->abort)) return false;
   }
   return false;
+}
+
+// Index of the first flag among ptr(first) .. ptr(n - 1) below its wanted
+// value want(i) (n if none), read with up to 16 relaxed loads in flight (no
+// acquire: the caller fences once it has advanced).  Flags only grow.
+template <class P, class V>
+__device__ __forceinline__ int count_set_flags(P ptr, V want, int first, int n) {
+  constexpr int W = 16;
+  while (first < n) {
+    bool ok[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) ok[j] = (first + j < n) ? ld_relaxed(ptr(first + j)) >= want(first + j) : true;
+    int adv = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (adv == j && ok[j]) ++adv;
+    first = min(first + adv, n);
+    if (adv < W) break;
+  }
+  return first;
+}
+template <class P>
+__device__ __forceinline__ int count_set_flags(P ptr, int first, int n) {
+  return count_set_flags(ptr, [](int) { return 1; }, first, n);
+}
+
+// Waits until every flag ptr(i), i < n, has reached want(i), polling them in
+// batches; the final fence acquires every one of them.  Bounded like wait_flag.
+template <class P, class V>
+__device__ __forceinline__ bool wait_flags(P ptr, V want, int n, long long limit, Ctl* ctl) {
+  int first = 0;
+  for (long long it = 0;; ++it) {
+    first = count_set_flags(ptr, want, first, n);
+    if (first >= n) break;
+    if (it >= limit) return false;
+    if (it >= 2048) __nanosleep(256);
+    if ((it & 255) == 255 && ld_volatile(&ctl->abort)) return false;
+  }
+  fence_acq_rel_gpu();
+  return true;
+}
+template <class P>
+__device__ __forceinline__ bool wait_flags(P ptr, int n, long long limit, Ctl* ctl) {
+  return wait_flags(ptr, [](int) { return 1; }, n, limit, ctl);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {

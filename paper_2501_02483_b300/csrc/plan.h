@@ -72,9 +72,13 @@ struct SolveGraph {
 // sub-tile with bit 30 set when it is read transposed, U sub-tile); per
 // off-diagonal sub-tile 2 int32 (sub-tile, sub-column) for U = L_jk L_kk^{-1}.
 struct SelinvGraph {
-  std::vector<int32_t> tasks;
-  std::vector<int32_t> pairs;
-  std::vector<int32_t> ulist;
+  std::vector<int32_t> tasks;  // 8 per task: output, column of a diagonal task or -1, products,
+                               // loads, X products (each a [begin, end) range)
+  std::vector<int32_t> pairs;  // 2 per product: Sigma sub-tile (bit 30: transposed), U sub-tile
+  std::vector<int32_t> loads;  // 3 per finished term: flag sub-tile, value it waits for, term
+                               // sub-tile (bit 30: in W, else in X)
+  std::vector<int32_t> posts;  // 1 per X product: sub-tile (m, c) of U and of X
+  std::vector<int32_t> ulist;  // 2 per U product: sub-tile, sub-column
 };
 
 struct DevPlan;  // device copies, defined in capi.cu

@@ -180,14 +180,18 @@ def _selinv_graph_case(T, B, order):
 
 
 @pytest.mark.parametrize("T,B,order", [(16, 16, st.ORDER_ND), (32, 16, st.ORDER_ND), (32, 32, st.ORDER_RCM),
-                                       (16, 16, st.ORDER_NONE)])
+                                       (16, 16, st.ORDER_NONE), (64, 16, st.ORDER_ND)])
 def test_selected_inverse_graph_executes_to_the_dense_inverse(T, B, order):
     """Runs the selected inverse's host-built task graph in ticket order with
-    numpy (the semantics the persistent kernel implements: off-diagonal tasks
-    Sigma_mk = -sum S U and W = Sigma_mk^T U_mk, diagonal tasks
-    L_kk^{-T} L_kk^{-1} - sum W) and checks every Sigma sub-tile against the
-    dense inverse of P A P^T.  Also checks that each operand is produced by an
-    earlier ticket and that every sub-tile is produced once."""
+    numpy, with the semantics the persistent kernel implements:
+      off-diagonal task (m, k): Sigma_mk = -(sum of its products S U + sum of its
+        loaded X terms), then W(m, k) = Sigma_mk^T U_mk and X(m, c) = Sigma_mk^T U_mc
+        for its X products;
+      diagonal task k: Sigma_kk = L_kk^{-T} L_kk^{-1} - sum of its loaded W terms;
+    and checks every Sigma sub-tile against the dense inverse of P A P^T.  Each
+    operand's and each loaded term's guarding flag must belong to an earlier
+    ticket, each term must be formed before it is loaded, and every sub-tile is
+    produced once."""
     m, plan = _selinv_graph_case(T, B, order)
     n = m["n"]
     A = inputs.dense_from_csc(m)
@@ -209,34 +213,49 @@ def test_selected_inverse_graph_executes_to_the_dense_inverse(T, B, order):
                     if ii >= jj and ii < nsb and jj < nsb:
                         where[e * R * R + q * R + p] = (ii, jj)
     blk = lambda M, ii, jj: M[ii * B:(ii + 1) * B, jj * B:(jj + 1) * B]
-    tasks, pairs = plan.tasks(3), plan.tasks(4)
+    tasks, pairs, loads, posts = plan.tasks(3), plan.tasks(4), plan.tasks(5), plan.tasks(6)[:, 0]
     outs = tasks[:, 0]
     assert len(np.unique(outs)) == len(outs) == len(where)
-    ticket = {int(o): t for t, o in enumerate(outs)}
     mask = (1 << 30) - 1
     linv = {k: np.linalg.inv(blk(Lf, k, k)) for k in range(nsb)}
-    S, W = {}, {}
-    for t, (out, dcol, pb, pe) in enumerate(tasks):
-        ii, k = where[int(out)]
+    U = lambda s: blk(Lf, *where[s]) @ linv[where[s][1]]
+    # executing in ticket order, every operand must already be final and every
+    # loaded term's flag must already hold its wanted value
+    S, W, X = {}, {}, {}
+
+    def loaded(lb, le):
+        acc = np.zeros((B, B))
+        for f, want, x in loads[lb:le]:
+            f, want, x = int(f), int(want), int(x)
+            assert f in S and want == 1
+            acc += (W if (x >> 30) & 1 else X)[x & mask]
+        return acc
+
+    def products(pb, pe):
+        acc = np.zeros((B, B))
         for sg, su in pairs[pb:pe]:
-            assert ticket[int(sg) & mask] < t
-        if dcol >= 0:
-            assert dcol == k == ii
-            assert np.all(pairs[pb:pe, 0] == pairs[pb:pe, 1]) and not np.any(pairs[pb:pe, 0] >> 30)
-            v = linv[k].T @ linv[k]
-            for sg, _ in pairs[pb:pe]:
-                v = v - W[int(sg)]
+            s = S[int(sg) & mask]
+            acc += (s.T if (int(sg) >> 30) & 1 else s) @ U(int(su))
+        return acc
+
+    for t, (out, kind, pb, pe, lb, le, xb, xe) in enumerate(tasks):
+        out = int(out)
+        ii, k = where[out]
+        for sg, su in pairs[pb:pe]:
+            assert where[int(su)][1] == k
+        if kind >= 0:
+            assert kind == k == ii and pe == pb and xe == xb
+            v = linv[k].T @ linv[k] - loaded(lb, le)
         else:
-            acc = np.zeros((B, B))
-            for sg, su in pairs[pb:pe]:
-                s = S[int(sg) & mask]
-                j, kk = where[int(su)]
-                assert kk == k
-                acc += (s.T if (int(sg) >> 30) & 1 else s) @ (blk(Lf, j, k) @ linv[k])
-            v = -acc
-            W[int(out)] = v.T @ (blk(Lf, ii, k) @ linv[k])
-        S[int(out)] = v
+            assert kind == -1
+            v = -(loaded(lb, le) + products(pb, pe))
+            W[out] = v.T @ U(out)
+            for x in posts[xb:xe]:
+                assert where[int(x)][0] == ii
+                X[int(x)] = v.T @ U(int(x))
+        S[out] = v
         assert np.allclose(v, blk(Sig, ii, k), rtol=1e-9, atol=1e-12 * np.abs(Sig).max())
+    assert len(S) == len(where)
 
 
 def test_selected_inverse_graph_interleaves_nd_halves():
