@@ -199,10 +199,10 @@ __device__ __forceinline__ void init_df_elements(uint16_t* sElem, int tid, int n
 // first bad one (not a positive normal number below 2^1022).  Returns that
 // pivot (the tile is then NaN) or -1; sInv receives 1/L_jj.  Shared scratch:
 // sC (B x B), sPiv, sRs, sInv (B each), sK (B ints), sElem.
-template <int B>
+template <int B, class Sync>
 __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv,
                                              double* sInv, double* sRs, int* sK, const uint16_t* sElem, int row,
-                                             int q, int tid) {
+                                             int q, int tid, Sync sync) {
   static_assert(B <= 32, "one warp scans the pivots");
   constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
   constexpr int NE = PotrfDf<B>::NE, NLIVE = PotrfDf<B>::NLIVE;
@@ -213,12 +213,12 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
   };
 #pragma unroll
   for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
-  __syncthreads();
+  sync();
   if (tid < B) {  // equilibration exponents
     const double v = sC[tid * (B + 1)];
     sK[tid] = pivot_ok(v) ? ((int(__double_as_longlong(v) >> 52) - 1023) >> 1) : 0;
   }
-  __syncthreads();
+  sync();
   double a[NE];
   int ei[NE], ec[NE];
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
     sC[tid] = v;
     if (tid == 0) sPiv[0] = v;
   }
-  __syncthreads();
+  sync();
 
   int bad = -1;
   for (int j = 0; j + 1 < B; ++j) {
@@ -266,7 +266,7 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
         }
       }
     }
-    __syncthreads();
+    sync();
   }
   if (bad < 0 && !pivot_ok(sPiv[B - 1])) bad = B - 1;
 
@@ -295,7 +295,7 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
         sPiv[tid] = pv * r * pow2(k);   // L_cc
       }
     }
-    __syncthreads();
+    sync();
     const double sr = pow2(sK[row]);
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
@@ -303,7 +303,7 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
       acc[m] = (c < row) ? sC[row + c * B] * sRs[c] * sr : ((c == row) ? sPiv[c] : 0.0);
     }
   }
-  __syncthreads();
+  sync();
   return bad;
 }
 
@@ -314,226 +314,9 @@ __device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], doubl
                                          double* sRs, int* sK, const uint16_t* sElem, int row, int q,
                                          int tid) {
   if constexpr (B <= 32)
-    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
+    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid, []() { __syncthreads(); });
   else
     return potrf_tile<B>(acc, sC, sPiv, sInv, sRs, row, q, tid);
-}
-
-// The lower triangle of a B x B tile numbered column by column: entry e of
-// sIC is (c << 8) | i for the e-th element (i >= c).  Filled once per CTA.
-template <int B>
-__device__ __forceinline__ void init_lower_index(uint16_t* sIC, int tid, int nthreads) {
-  constexpr int NE = B * (B + 1) / 2;
-  for (int e = tid; e < NE; e += nthreads) {
-    int c = 0, off = 0;
-    while (off + (B - c) <= e) {
-      off += B - c;
-      ++c;
-    }
-    sIC[e] = uint16_t((c << 8) | (c + e - off));
-  }
-}
-
-// Shared-memory flag words of potrf_tile_ws: column-ready flags, per-step
-// counters of the trailing-update warps, the status word.
-template <int B>
-struct PotrfFlags {
-  static constexpr int COL = 0, CNT = B, STATUS = 2 * B, WORDS = 2 * B + 1;
-};
-
-__device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-
-// POTRF of a B x B FP64 tile held column-major in shared memory (lower
-// triangle), 128 threads, right-looking, warp-specialized:
-//
-//   warp 3 (the pivot chain) finishes the columns in order: column c takes
-//     step c-1 (a_ic -= L_i,c-1 L_c,c-1), then s = 1/sqrt(d_c), L_cc = d_c s,
-//     L_ic = a_ic s, and is published with a column-ready flag;
-//   warps 0-2 apply step j (a_ic -= L_ij L_cj) to the columns c >= j+2 as
-//     soon as column j is ready; the elements of column j+2 first, then a
-//     per-step counter tells the chain that column j+2 may take step j+1.
-//
-// The chain therefore runs one column ahead of the bulk of the trailing
-// update instead of waiting for all of it at every step.  The lower-triangle
-// elements (sIC numbering) are owned in chunks of 32 by the three update
-// warps, chunk k by warp k % 3, so every element sees its steps in order and
-// nearly every lane of every FP64 instruction does useful work (an FP64 warp
-// instruction costs the same pipe time however many lanes are active).
-// Flags live in shared memory (PotrfFlags words); waits are bounded by
-// `limit` polls.  `tid` counts the 128 participating threads from 0 and
-// `sync` is their barrier (the CTA's, or a named barrier of a task slot).  Returns -1, the first bad pivot (<= 0 or NaN; the tile is
-// then filled with NaN), or -2 when a wait gave up.  sInv receives 1/L_jj;
-// the strict upper triangle is zeroed.
-template <int B, class Sync>
-__device__ int potrf_tile_ws(double* sD, double* sInv, const uint16_t* sIC, int* sF, int tid, long long limit,
-                              Sync sync) {
-  using F = PotrfFlags<B>;
-  constexpr int NE = B * (B + 1) / 2;
-  constexpr int NK = (NE + 31) / 32;
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int w = tid; w < F::WORDS; w += 128) sF[w] = (w == F::STATUS) ? -1 : 0;
-  sync();
-  auto pivot_ok = [](double d) {
-    const long long bits = __double_as_longlong(d);
-    return bits > 0 && bits <= 0x7ff0000000000000LL;  // positive, at most +inf
-  };
-  if (warp == 3) {
-    // ---- the pivot chain ----
-    // One column per step; lanes hold rows c + lane (and c + lane + 32 while the
-    // column is longer than 32).  The two cases are separate loops: an FP64
-    // instruction whose predicate is off for every lane still takes its pipe slot.
-    bool stop = false;
-    auto finish_column = [&](int c, auto two_rows) {
-      constexpr bool TWO = decltype(two_rows)::value;
-      if (c >= 2) {
-        long long spins = 0;
-        while (ld_volatile_shared(sF + F::CNT + (c - 2)) < 3) {
-          if (++spins > limit) break;
-        }
-        if (spins > limit) {
-          if (lane == 0) sF[F::STATUS] = -2;
-          stop = true;
-          return;
-        }
-        __threadfence_block();
-      }
-      const int i0 = c + lane, i1 = c + lane + 32;
-      double v0 = 0.0, v1 = 0.0;
-      if (c == 0) {
-        if (i0 < B) v0 = sD[i0];
-        if (TWO && i1 < B) v1 = sD[i1];
-      } else {
-        const double* lp = sD + (c - 1) * B;
-        const double lc = lp[c];
-        if (i0 < B) v0 = fma(-lp[i0], lc, sD[c * B + i0]);
-        if (TWO && i1 < B) v1 = fma(-lp[i1], lc, sD[c * B + i1]);
-      }
-      const double d = __shfl_sync(0xffffffffu, v0, 0);
-      const bool ok = pivot_ok(d);
-      if (ok) {
-        const double sc = rsqrt(d);
-        if (i0 < B) sD[c * B + i0] = v0 * sc;
-        if (TWO && i1 < B) sD[c * B + i1] = v1 * sc;
-        if (lane == 0) sInv[c] = sc;
-      }
-      __threadfence_block();
-      __syncwarp();
-      if (lane == 0) {
-        if (!ok) sF[F::STATUS] = c;
-        __threadfence_block();
-        sF[F::COL + c] = 1;
-      }
-      if (!ok) {
-        // release the update warps waiting on later columns
-        for (int q = c + 1 + lane; q < B; q += 32) sF[F::COL + q] = 1;
-        stop = true;
-      }
-    };
-    int c = 0;
-    for (; c + 32 < B && !stop; ++c) finish_column(c, std::true_type());
-    for (; c < B && !stop; ++c) finish_column(c, std::false_type());
-  } else {
-    // ---- the trailing update: step j on columns >= j+2 ----
-    // This warp owns chunks k = warp + 3m; slot m holds its lane's element in a
-    // register for the whole factorization (packed (c << 8) | i, or -1 past the end).
-    constexpr int NSLOT = (NK + 2) / 3;
-    static_assert(NSLOT <= 24, "the group switch covers 24 slots");
-    double a[NSLOT];
-    int ic[NSLOT];
-#pragma unroll
-    for (int m = 0; m < NSLOT; ++m) {
-      const int e = (warp + 3 * m) * 32 + lane;
-      ic[m] = -1;
-      a[m] = 0.0;
-      if (warp + 3 * m < NK && e < NE) {
-        ic[m] = sIC[e];
-        a[m] = sD[(ic[m] >> 8) * B + (ic[m] & 255)];
-      }
-    }
-    for (int j = 0; j + 2 < B; ++j) {
-      {
-        long long spins = 0;
-        while (ld_volatile_shared(sF + F::COL + j) == 0) {
-          if (++spins > limit) break;
-        }
-        if (spins > limit) {
-          if (lane == 0) sF[F::STATUS] = -2;
-          break;
-        }
-      }
-      __threadfence_block();
-      if (ld_volatile_shared(sF + F::STATUS) != -1) break;
-      const double* lj = sD + j * B;
-      const int e2 = (j + 2) * B - ((j + 2) * (j + 1)) / 2;  // first element of column j+2
-      const int e3 = e2 + (B - j - 2);                         // first element of column j+3
-      const int kfirst = e2 >> 5, kcol_end = (e3 - 1) >> 5;    // chunks holding column j+2
-      // first live slot (chunks of finished columns are not visited); if it holds
-      // elements of column j+2 they are stored for the chain and the counter is
-      // bumped right after it, otherwise before any slot
-      const int m_lo = (kfirst > warp) ? (kfirst - warp + 2) / 3 : 0;
-      const bool first_has_col = m_lo < NSLOT && warp + 3 * m_lo <= kcol_end && warp + 3 * m_lo < NK;
-      auto signal = [&]() {
-        __threadfence_block();
-        __syncwarp();
-        if (lane == 0) atomicAdd(sF + F::CNT + j, 1);
-      };
-      if (!first_has_col) signal();
-      // Slots are visited in groups of four, entered at the group holding m_lo
-      // and falling through to the last group: only live groups issue FP64
-      // instructions, and inside a group every load comes before the FMAs.
-      const int g_lo = m_lo / 4;
-      auto group = [&](auto gc) {
-        constexpr int G = decltype(gc)::value;
-        double xv[4], yv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int m = min(4 * G + u, NSLOT - 1);  // clamped: slots past NSLOT are never used
-          xv[u] = 0.0;
-          yv[u] = 0.0;
-          if (4 * G + u < NSLOT && ic[m] >= 0) {
-            xv[u] = lj[ic[m] & 255];
-            yv[u] = lj[ic[m] >> 8];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int m = min(4 * G + u, NSLOT - 1);
-          if (4 * G + u < NSLOT && ic[m] >= 0 && (ic[m] >> 8) >= j + 2) a[m] = fma(-xv[u], yv[u], a[m]);
-        }
-        if (G == g_lo && first_has_col) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int m = min(4 * G + u, NSLOT - 1);
-            if (4 * G + u == m_lo && ic[m] >= 0 && (ic[m] >> 8) == j + 2)
-              sD[(ic[m] >> 8) * B + (ic[m] & 255)] = a[m];  // column j+2 is final for the chain
-          }
-          signal();
-        }
-      };
-      using std::integral_constant;
-      switch (g_lo) {
-        case 0: if constexpr (0 < NSLOT) group(integral_constant<int, 0>()); [[fallthrough]];
-        case 1: if constexpr (4 < NSLOT) group(integral_constant<int, 1>()); [[fallthrough]];
-        case 2: if constexpr (8 < NSLOT) group(integral_constant<int, 2>()); [[fallthrough]];
-        case 3: if constexpr (12 < NSLOT) group(integral_constant<int, 3>()); [[fallthrough]];
-        case 4: if constexpr (16 < NSLOT) group(integral_constant<int, 4>()); [[fallthrough]];
-        case 5: if constexpr (20 < NSLOT) group(integral_constant<int, 5>()); [[fallthrough]];
-        default: break;
-      }
-    }
-  }
-  sync();
-  const int bad = sF[F::STATUS];
-  if (bad != -1) {
-    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-    for (int e = tid; e < B * B; e += 128) sD[e] = nanv;
-    if (tid < B) sInv[tid] = nanv;
-  } else {
-    for (int e = tid; e < B * B; e += 128)
-      if ((e % B) < (e / B)) sD[e] = 0.0;  // strict upper triangle (row < column)
-  }
-  sync();
-  return bad;
 }
 
 // X L^T = acc, column by column, with L's columns pre-scaled by 1/L_jj (sLs:

@@ -36,9 +36,8 @@ constexpr uint32_t LP_TMEM_COLS = 128;              // two 64-column FP32 accumu
 constexpr int LP_SLOTS = 2;                         // task slots per CTA
 constexpr int LP_THREADS = 128 * LP_SLOTS;
 
-// shared memory: stages | sD (FP64 64x64) | sL (FP32 64x64) | sInv/sPiv/sRs (FP64 x 64 each; sPiv and sRs
-// hold the POTRF's flag words) | barriers
-static_assert(PotrfFlags<64>::WORDS * sizeof(int) <= 2 * 64 * sizeof(double), "POTRF flags fit in sPiv/sRs");
+// shared memory: stages (also the POTRF's scratch) | sD (FP64 64x64) | sL (FP32 64x64) | sInv/sPiv/sRs
+// (FP64 x 64 each) | barriers
 constexpr size_t LP_SMEM = size_t(LP_NSTAGE) * LP_STAGE_BYTES + LP_TILE * 8 + LP_TILE * 4 + 3 * LP_B * 8 +
                            (LP_NSTAGE * 2 + 2) * 8 + 64;
 constexpr size_t LP_SLOT_BYTES = (LP_SMEM + 1023) / 1024 * 1024;  // one slot's dynamic shared memory
@@ -137,17 +136,83 @@ __device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int s
   }
 }
 
+// FP64 POTRF of the 64 x 64 tile in sD (column-major, both triangles of the
+// symmetric input) by 32 x 32 blocks: L11 = chol(A11) (division-free form),
+// L21 = A21 L11^{-T} (rows against L11 with its columns pre-scaled by 1/L_jj),
+// A22 -= L21 L21^T, L22 = chol(A22).  The 32-wide steps keep every thread of
+// the slot busy (a block row per four threads) where the 64-wide elimination
+// runs 64 dependent steps.  sD receives L (zero upper triangle) and sInv the 64
+// values 1/L_jj; scratch holds 32 x 32 + 4 x 32 doubles.  Returns the first bad
+// pivot (the tile is then NaN) or -1.
+__shared__ uint16_t lp_sElem32[PotrfDf<32>::NLIVE];  // element numbering of the 32-wide POTRF
+
+template <class Sync>
+__device__ __forceinline__ int lp_potrf64_blocked(double* sD, double* sInv, double* scratch, int tid, Sync sync) {
+  using C32 = FactorCfg<32>;
+  constexpr int RPT = C32::RPT, CPT = C32::CPT, H = 32;
+  double* sC = scratch;  // 32 x 32: POTRF scratch, then L11 pre-scaled for the TRSM
+  double* sPiv = sC + H * H;
+  double* sInv32 = sPiv + H;
+  double* sRs = sInv32 + H;
+  int* sK = reinterpret_cast<int*>(sRs + H);
+  const int row = tid / RPT, q = tid % RPT;
+  double acc[CPT];
+  // L11
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + row];
+  const int bad1 = potrf_tile_df<32>(acc, sC, sPiv, sInv32, sRs, sK, lp_sElem32, row, q, tid, sync);
+  double inv[CPT];
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int c = q + RPT * m;
+    inv[m] = sInv32[c];
+    sD[c * LP_B + row] = acc[m];                               // L11
+    sD[(H + c) * LP_B + row] = 0.0;                             // upper right block
+    if (row > c) sC[row + c * H] = acc[m] * inv[m];             // L11(row, c) / L11(c, c)
+  }
+  if (tid < H) sInv[tid] = sInv32[tid];
+  sync();
+  // L21 = A21 L11^{-T}
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + H + row];
+  trsm_rows<32>(acc, inv, sC, q, (tid & 31) - q);
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) sD[(q + RPT * m) * LP_B + H + row] = acc[m];
+  sync();
+  // A22 - L21 L21^T (lower triangle; potrf_tile_df reads no other element)
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int c = q + RPT * m;
+    double v = 0.0;
+    if (c <= row) {
+      v = sD[(H + c) * LP_B + H + row];
+      double v2 = 0.0;
+#pragma unroll 8
+      for (int p = 0; p < H; p += 2) {
+        v = fma(-sD[p * LP_B + H + row], sD[p * LP_B + H + c], v);
+        v2 = fma(-sD[(p + 1) * LP_B + H + row], sD[(p + 1) * LP_B + H + c], v2);
+      }
+      v += v2;
+    }
+    acc[m] = v;
+  }
+  const int bad2 = potrf_tile_df<32>(acc, sC, sPiv, sInv32, sRs, sK, lp_sElem32, row, q, tid, sync);
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) sD[(H + q + RPT * m) * LP_B + H + row] = acc[m];
+  if (tid < H) sInv[H + tid] = sInv32[tid];
+  sync();
+  return bad1 >= 0 ? bad1 : (bad2 >= 0 ? H + bad2 : -1);
+}
+
 // One task slot: 128 threads (4 warps) running the persistent task loop on
 // their own shared-memory area, mbarriers, TMEM columns and ticket, with a
 // named barrier for the slot's own synchronisation.
-__shared__ uint16_t lp_sIC[LP_B * (LP_B + 1) / 2];  // lower-triangle numbering of the POTRF
 
 template <int SLOT>
 __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid) {
   extern __shared__ __align__(1024) unsigned char lp_dyn[];
   __shared__ int sTicket, sAbort;  // one pair per instantiation, i.e. per slot
   unsigned char* smem_raw = lp_dyn + SLOT * LP_SLOT_BYTES;
-  const uint16_t* sIC = lp_sIC;
   __builtin_assume(tid >= 0 && tid < 128);
   auto sync = []() { asm volatile("bar.sync %0, 128;" ::"n"(1 + SLOT) : "memory"); };
   auto publish = [&](int* flag) {
@@ -429,13 +494,8 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
     }
     sync();
     {
-      // sPiv/sRs (2 x 64 doubles) hold the POTRF's flag words
-      const int bad = potrf_tile_ws<LP_B>(sD, sInv, sIC, reinterpret_cast<int*>(sPiv), tid, limit, sync);
-      if (bad == -2) {
-        if (tid == 0) raise_timeout(a.ctl, t);
-        aborted = true;
-        break;
-      }
+      // the stage area (every MMA of the task has completed) holds the POTRF's scratch
+      const int bad = lp_potrf64_blocked(sD, sInv, reinterpret_cast<double*>(sStage), tid, sync);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)col * LP_B + bad + 1);
     }
     if (warp < 2) {
@@ -462,7 +522,7 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
 __global__ void __launch_bounds__(LP_THREADS) factor_lp_kernel(LPArgs a) {
   __shared__ uint32_t sTmem;
   const int slot = threadIdx.x >> 7, tid = threadIdx.x & 127;
-  init_lower_index<LP_B>(lp_sIC, threadIdx.x, LP_THREADS);
+  init_df_elements<32>(lp_sElem32, threadIdx.x, LP_THREADS);
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sTmem)),
                  "r"(LP_SLOTS * LP_TMEM_COLS));
