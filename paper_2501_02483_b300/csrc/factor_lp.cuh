@@ -139,7 +139,7 @@ __device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int s
 // FP64 POTRF of the 64 x 64 tile in sD (column-major, both triangles of the
 // symmetric input) by 32 x 32 blocks: L11 = chol(A11) (division-free form),
 // L21 = A21 L11^{-T} (rows against L11 with its columns pre-scaled by 1/L_jj),
-// A22 -= L21 L21^T, L22 = chol(A22).  The 32-wide steps keep every thread of
+// A22 -= L21 L21^T (FP64 tensor path), L22 = chol(A22).  The 32-wide steps keep every thread of
 // the slot busy (a block row per four threads) where the 64-wide elimination
 // runs 64 dependent steps.  sD receives L (zero upper triangle) and sInv the 64
 // values 1/L_jj; scratch holds 32 x 32 + 4 x 32 doubles.  Returns the first bad
@@ -179,23 +179,37 @@ __device__ __forceinline__ int lp_potrf64_blocked(double* sD, double* sInv, doub
 #pragma unroll
   for (int m = 0; m < CPT; ++m) sD[(q + RPT * m) * LP_B + H + row] = acc[m];
   sync();
-  // A22 - L21 L21^T (lower triangle; potrf_tile_df reads no other element)
+  // A22 - L21 L21^T (lower triangle; potrf_tile_df reads no other element):
+  // the ten lower 8 x 8 blocks of L21 L21^T on the FP64 tensor path
+  // (mma.sync m8n8k4, 256 FMAs per warp instruction), blocks w, w + 4, w + 8 to
+  // warp w, into sC (the pre-scaled L11 is no longer needed)
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
+    for (int bk = warp; bk < 10; bk += 4) {
+      int bi = 0;
+      while ((bi + 1) * (bi + 2) / 2 <= bk) ++bi;
+      const int bj = bk - bi * (bi + 1) / 2;  // block (bi, bj), bj <= bi, in 8-row units
+      double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+      for (int ks = 0; ks < H; ks += 4) {
+        const double fa = sD[(ks + tq) * LP_B + H + 8 * bi + g];  // A(g, tq) = L21(8 bi + g, ks + tq)
+        const double fb = sD[(ks + tq) * LP_B + H + 8 * bj + g];  // B(tq, g) = L21(8 bj + g, ks + tq)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(d0), "+d"(d1)
+                     : "d"(fa), "d"(fb));
+      }
+      sC[(8 * bi + g) + (8 * bj + 2 * tq) * H] = d0;
+      sC[(8 * bi + g) + (8 * bj + 2 * tq + 1) * H] = d1;
+    }
+  }
+  sync();
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
     const int c = q + RPT * m;
-    double v = 0.0;
-    if (c <= row) {
-      v = sD[(H + c) * LP_B + H + row];
-      double v2 = 0.0;
-#pragma unroll 8
-      for (int p = 0; p < H; p += 2) {
-        v = fma(-sD[p * LP_B + H + row], sD[p * LP_B + H + c], v);
-        v2 = fma(-sD[(p + 1) * LP_B + H + row], sD[(p + 1) * LP_B + H + c], v2);
-      }
-      v += v2;
-    }
-    acc[m] = v;
+    acc[m] = (c <= row) ? sD[(H + c) * LP_B + H + row] - sC[row + c * H] : 0.0;
   }
+  sync();  // sC is the next POTRF's scratch
   const int bad2 = potrf_tile_df<32>(acc, sC, sPiv, sInv32, sRs, sK, lp_sElem32, row, q, tid, sync);
 #pragma unroll
   for (int m = 0; m < CPT; ++m) sD[(H + q + RPT * m) * LP_B + H + row] = acc[m];
