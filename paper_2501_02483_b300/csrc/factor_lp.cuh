@@ -136,86 +136,100 @@ __device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int s
   }
 }
 
-// FP64 POTRF of the 64 x 64 tile in sD (column-major, both triangles of the
-// symmetric input) by 32 x 32 blocks: L11 = chol(A11) (division-free form),
-// L21 = A21 L11^{-T} (rows against L11 with its columns pre-scaled by 1/L_jj),
-// A22 -= L21 L21^T (FP64 tensor path), L22 = chol(A22).  The 32-wide steps keep every thread of
-// the slot busy (a block row per four threads) where the 64-wide elimination
-// runs 64 dependent steps.  sD receives L (zero upper triangle) and sInv the 64
-// values 1/L_jj; scratch holds 32 x 32 + 4 x 32 doubles.  Returns the first bad
-// pivot (the tile is then NaN) or -1.
-__shared__ uint16_t lp_sElem32[PotrfDf<32>::NLIVE];  // element numbering of the 32-wide POTRF
-
-template <class Sync>
-__device__ __forceinline__ int lp_potrf64_blocked(double* sD, double* sInv, double* scratch, int tid, Sync sync) {
-  using C32 = FactorCfg<32>;
-  constexpr int RPT = C32::RPT, CPT = C32::CPT, H = 32;
-  double* sC = scratch;  // 32 x 32: POTRF scratch, then L11 pre-scaled for the TRSM
-  double* sPiv = sC + H * H;
-  double* sInv32 = sPiv + H;
-  double* sRs = sInv32 + H;
-  int* sK = reinterpret_cast<int*>(sRs + H);
-  const int row = tid / RPT, q = tid % RPT;
-  double acc[CPT];
-  // L11
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + row];
-  const int bad1 = potrf_tile_df<32>(acc, sC, sPiv, sInv32, sRs, sK, lp_sElem32, row, q, tid, sync);
-  double inv[CPT];
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) {
-    const int c = q + RPT * m;
-    inv[m] = sInv32[c];
-    sD[c * LP_B + row] = acc[m];                               // L11
-    sD[(H + c) * LP_B + row] = 0.0;                             // upper right block
-    if (row > c) sC[row + c * H] = acc[m] * inv[m];             // L11(row, c) / L11(c, c)
-  }
-  if (tid < H) sInv[tid] = sInv32[tid];
-  sync();
-  // L21 = A21 L11^{-T}
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) acc[m] = sD[(q + RPT * m) * LP_B + H + row];
-  trsm_rows<32>(acc, inv, sC, q, (tid & 31) - q);
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) sD[(q + RPT * m) * LP_B + H + row] = acc[m];
-  sync();
-  // A22 - L21 L21^T (lower triangle; potrf_tile_df reads no other element):
-  // the ten lower 8 x 8 blocks of L21 L21^T on the FP64 tensor path
-  // (mma.sync m8n8k4, 256 FMAs per warp instruction), blocks w, w + 4, w + 8 to
-  // warp w, into sC (the pre-scaled L11 is no longer needed)
-  {
-    const int warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
-    for (int bk = warp; bk < 10; bk += 4) {
-      int bi = 0;
-      while ((bi + 1) * (bi + 2) / 2 <= bk) ++bi;
-      const int bj = bk - bi * (bi + 1) / 2;  // block (bi, bj), bj <= bi, in 8-row units
-      double d0 = 0.0, d1 = 0.0;
-#pragma unroll
-      for (int ks = 0; ks < H; ks += 4) {
-        const double fa = sD[(ks + tq) * LP_B + H + 8 * bi + g];  // A(g, tq) = L21(8 bi + g, ks + tq)
-        const double fb = sD[(ks + tq) * LP_B + H + 8 * bj + g];  // B(tq, g) = L21(8 bj + g, ks + tq)
-        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                     : "+d"(d0), "+d"(d1)
-                     : "d"(fa), "d"(fb));
-      }
-      sC[(8 * bi + g) + (8 * bj + 2 * tq) * H] = d0;
-      sC[(8 * bi + g) + (8 * bj + 2 * tq + 1) * H] = d1;
+// Lower 8 x 8 blocks of X X^T (X: n rows of a column-major array with leading
+// dimension ld, k columns) on the FP64 tensor path (mma.sync m8n8k4, 256 FMAs
+// per warp instruction), block b to warp b % 4, into out (n x n, column-major;
+// the upper blocks untouched); n a multiple of 8, k of 4.
+__device__ __forceinline__ void lp_syrk_mma(const double* X, int ld, int n, int k, double* out, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
+  const int nb = n / 8;
+  for (int bk = warp; bk < nb * (nb + 1) / 2; bk += 4) {
+    int bi = 0;
+    while ((bi + 1) * (bi + 2) / 2 <= bk) ++bi;
+    const int bj = bk - bi * (bi + 1) / 2;  // block (bi, bj), bj <= bi, in 8-row units
+    double d0 = 0.0, d1 = 0.0;
+    for (int ks = 0; ks < k; ks += 4) {
+      const double fa = X[(ks + tq) * ld + 8 * bi + g];  // A(g, tq) = X(8 bi + g, ks + tq)
+      const double fb = X[(ks + tq) * ld + 8 * bj + g];  // B(tq, g) = X(8 bj + g, ks + tq)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(d0), "+d"(d1)
+                   : "d"(fa), "d"(fb));
     }
+    out[(8 * bi + g) + (8 * bj + 2 * tq) * n] = d0;
+    out[(8 * bi + g) + (8 * bj + 2 * tq + 1) * n] = d1;
   }
-  sync();
+}
+
+__shared__ uint16_t lp_sElem16[PotrfDf<16>::NLIVE];  // element numbering of the 16-wide POTRF
+
+// FP64 POTRF of the H x H block at S (column-major, leading dimension ld, lower
+// triangle of the input read; H = 16, 32 or 64) in place.  H = 16: the
+// division-free POTRF.  Larger H by H/2 x H/2 blocks:
+//   L11 = chol(A11), L21 = A21 L11^{-T} (rows against L11 with its columns
+//   pre-scaled by 1/L_jj), A22 -= L21 L21^T (FP64 tensor path), L22 = chol(A22),
+// so every step keeps all 128 threads of the slot busy (a block row per
+// 256 / H threads) where an H-wide elimination runs H dependent steps.  S
+// receives L (zero strict upper triangle), inv the H values 1/L_jj.  Returns
+// the first bad pivot (the block is then NaN) or -1.  Scratch: 1 KB + H^2 / 4
+// doubles per level.
+template <int H, class Sync>
+__device__ int lp_potrf_blocked(double* S, int ld, double* inv, double* scratch, int tid, Sync sync) {
+  if constexpr (H == 16) {
+    using C = FactorCfg<16>;
+    constexpr int RPT = C::RPT, CPT = C::CPT;
+    const int row = tid / RPT, q = tid % RPT;
+    double* sW = scratch;  // 16 x 16
+    double* sPiv = sW + H * H;
+    double* sInv = sPiv + H;
+    double* sRs = sInv + H;
+    int* sK = reinterpret_cast<int*>(sRs + H);
+    double acc[CPT];
 #pragma unroll
-  for (int m = 0; m < CPT; ++m) {
-    const int c = q + RPT * m;
-    acc[m] = (c <= row) ? sD[(H + c) * LP_B + H + row] - sC[row + c * H] : 0.0;
+    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + row];
+    const int bad = potrf_tile_df<16>(acc, sW, sPiv, sInv, sRs, sK, lp_sElem16, row, q, tid, sync);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + row] = acc[m];
+    if (tid < H) inv[tid] = sInv[tid];
+    sync();
+    return bad;
+  } else {
+    constexpr int G = H / 2;
+    using C = FactorCfg<G>;
+    constexpr int RPT = C::RPT, CPT = C::CPT;
+    const int row = tid / RPT, q = tid % RPT;
+    double* sC = scratch;          // G x G: pre-scaled L11, then the A22 update
+    double* sub = scratch + G * G;  // the half-size calls' scratch
+    const int bad1 = lp_potrf_blocked<G>(S, ld, inv, sub, tid, sync);
+    double iv[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      iv[m] = inv[c];
+      S[(G + c) * ld + row] = 0.0;                             // upper right block
+      if (row > c) sC[row + c * G] = S[c * ld + row] * iv[m];  // L11(row, c) / L11(c, c)
+    }
+    sync();
+    // L21 = A21 L11^{-T}
+    double acc[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + G + row];
+    trsm_rows<G>(acc, iv, sC, q, (tid & 31) - q);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + G + row] = acc[m];
+    sync();
+    // A22 - L21 L21^T (lower triangle)
+    lp_syrk_mma(S + G, ld, G, G, sC, tid);
+    sync();
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      if (c <= row) S[(G + c) * ld + G + row] -= sC[row + c * G];
+    }
+    sync();
+    const int bad2 = lp_potrf_blocked<G>(S + G * ld + G, ld, inv + G, sub, tid, sync);
+    return bad1 >= 0 ? bad1 : (bad2 >= 0 ? G + bad2 : -1);
   }
-  sync();  // sC is the next POTRF's scratch
-  const int bad2 = potrf_tile_df<32>(acc, sC, sPiv, sInv32, sRs, sK, lp_sElem32, row, q, tid, sync);
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) sD[(H + q + RPT * m) * LP_B + H + row] = acc[m];
-  if (tid < H) sInv[H + tid] = sInv32[tid];
-  sync();
-  return bad1 >= 0 ? bad1 : (bad2 >= 0 ? H + bad2 : -1);
 }
 
 // One task slot: 128 threads (4 warps) running the persistent task loop on
@@ -509,7 +523,7 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
     sync();
     {
       // the stage area (every MMA of the task has completed) holds the POTRF's scratch
-      const int bad = lp_potrf64_blocked(sD, sInv, reinterpret_cast<double*>(sStage), tid, sync);
+      const int bad = lp_potrf_blocked<LP_B>(sD, LP_B, sInv, reinterpret_cast<double*>(sStage), tid, sync);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)col * LP_B + bad + 1);
     }
     if (warp < 2) {
@@ -536,7 +550,7 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
 __global__ void __launch_bounds__(LP_THREADS) factor_lp_kernel(LPArgs a) {
   __shared__ uint32_t sTmem;
   const int slot = threadIdx.x >> 7, tid = threadIdx.x & 127;
-  init_df_elements<32>(lp_sElem32, threadIdx.x, LP_THREADS);
+  init_df_elements<16>(lp_sElem16, threadIdx.x, LP_THREADS);
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sTmem)),
                  "r"(LP_SLOTS * LP_TMEM_COLS));
