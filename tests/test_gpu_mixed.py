@@ -154,3 +154,58 @@ def test_in_place_device_solve_keeps_b_for_residuals():
     x, rr = f.solve(b, x=b, relres=True)
     assert rr <= 1e-10
     assert torch.allclose(x, ref, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("pos", [1, 17, 40, 63])
+def test_not_spd_mixed_position_in_tile(pos):
+    """The first bad pivot is reported at every depth of the 64 x 64 diagonal
+    tile's blocked POTRF (16-wide leaves, 32- and 64-wide levels)."""
+    d = np.ones(320)
+    col = 128 + pos
+    d[col] = -2.0
+    d[col + 5] = -1.0  # a later bad pivot (same leaf, or the next tile) must not win
+    m = inputs.diagonal_matrix(d)
+    plan = st.Plan.from_matrix(m, tile=64, ordering=st.ORDER_NONE, precision=st.PREC_F16)
+    with pytest.raises(st.StilesError) as e:
+        st.Factor(plan).factorize(m["values"])
+    assert e.value.name == "NOT_SPD" and e.value.info == col + 1
+
+
+def test_mixed_diagonal_tiles_are_fp64_cholesky():
+    """A block-diagonal matrix of dense 64 x 64 SPD blocks has no off-diagonal
+    tiles, so its mixed-precision factor is the FP64 POTRF of each diagonal tile
+    on the FP32-rounded input the mixed path stores: it must match numpy's FP64
+    Cholesky of the same rounded blocks to FP64 accuracy (the 16-bit operand
+    tolerance of the other mixed tests would hide an error here)."""
+    rng = np.random.default_rng(7)
+    nb = 5
+    n = 64 * nb
+    rows, cols, vals, blocks = [], [], [], []
+    for b in range(nb):
+        G = rng.standard_normal((64, 64))
+        A = (G @ G.T / 64 + (0.05 + 0.5 * b) * np.eye(64)) * 10.0 ** (3 * (b - 2))
+        blocks.append(A)
+        i, j = np.tril_indices(64)
+        rows.append(i + 64 * b)
+        cols.append(j + 64 * b)
+        vals.append(A[i, j])
+    colptr, rowidx, values = inputs.coo_to_csc_lower(n, np.concatenate(rows), np.concatenate(cols),
+                                                     np.concatenate(vals))
+    m = {"n": n, "n_arrow": 0, "colptr": colptr, "rowidx": rowidx, "values": values, "rhs": None,
+         "name": "blockdiag64"}
+    plan = st.Plan.from_matrix(m, tile=64, ordering=st.ORDER_NONE, precision=st.PREC_F16)
+    f = st.Factor(plan)
+    f.factorize(values)
+    tiles = f.tiles()
+    tc, tr = plan.tilemap()
+    assert np.array_equal(np.diff(tc), np.ones(nb, dtype=tc.dtype))  # diagonal tiles only
+    for b in range(nb):
+        L = tiles[tc[b]].T
+        Lref = np.linalg.cholesky(blocks[b].astype(np.float32).astype(np.float64))
+        # L is stored in FP32: compare within FP32 rounding of an FP64-accurate factor
+        assert np.max(np.abs(L - Lref)) <= 2.0 ** -23 * np.max(np.abs(Lref))
+        assert np.all(np.triu(L, 1) == 0.0)
+    ld = f.logdet()
+    ld_ref = sum(2.0 * np.log(np.diag(np.linalg.cholesky(A.astype(np.float32).astype(np.float64)))).sum()
+                 for A in blocks)
+    assert abs(ld - ld_ref) <= 1e-12 * abs(ld_ref)
