@@ -86,79 +86,6 @@ __device__ __forceinline__ void publish(int* flag) {
   if (threadIdx.x == 0) st_release(flag, 1);
 }
 
-// POTRF of the tile held in `acc` (row-quad layout), in place, using sC as the
-// shared copy of the unscaled columns.  Right-looking: step j subtracts
-// a_ij a_cj / d_j from every (i, c) with j < c <= i; the owner of the next
-// pivot publishes it and its reciprocal, so each step costs one barrier.
-// The reciprocal square roots of the pivots (for the final scaling) are taken
-// by a warp other than the next pivot's owner, off the dependency chain.
-// Returns the first bad pivot (<= 0 or NaN) or -1; sInv receives 1/L_jj.
-template <int B>
-__device__ __forceinline__ int potrf_tile(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
-                                          double* sRs, int row, int q, int tid) {
-  constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
-  constexpr int RPW = 32 / RPT;  // tile rows per warp
-  const int warp = tid >> 5, lane = tid & 31;
-#pragma unroll
-  for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
-  __syncthreads();
-  if (tid == 0) {
-    const double d = sC[0];
-    sPiv[0] = d;
-    sInv[0] = 1.0 / d;
-  }
-  __syncthreads();
-  int bad = -1;
-#pragma unroll
-  for (int j = 0; j < B; ++j) {
-    const double d = sPiv[j];
-    // d > 0 and not NaN, tested on the bit pattern (an FP64 compare would occupy
-    // the FP64 pipe on the dependency chain): positive, at most +inf
-    const long long bits = __double_as_longlong(d);
-    if (!(bits > 0 && bits <= 0x7ff0000000000000LL)) { bad = j; break; }
-    if (lane == 0 && warp == (((j + 1) / RPW) + 2) % 4) sRs[j] = rsqrt(d);
-    const double tr = sC[row + j * B] * sInv[j];
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) {
-      const int c = q + RPT * m;
-      if (c > j && c <= row) acc[m] = fma(-tr, sC[c + j * B], acc[m]);
-    }
-    if (j + 1 < B) {
-      const int cn = j + 1;
-      if (q == cn % RPT && row >= cn) {
-        const double v = acc[cn / RPT];
-        sC[row + cn * B] = v;
-        if (row == cn) {
-          sPiv[cn] = v;
-          sInv[cn] = 1.0 / v;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (bad >= 0) {
-    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) acc[m] = nanv;
-    if (tid < B) sInv[tid] = nanv;
-  } else {
-    // L_ic = a_ic * rsqrt(d_c) below the diagonal, L_cc = d_c * rsqrt(d_c)
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) {
-      const int c = q + RPT * m;
-      acc[m] = (c <= row) ? acc[m] * sRs[c] : 0.0;
-    }
-    if (tid < B) sInv[tid] = sRs[tid];
-  }
-  __syncthreads();
-  return bad;
-}
-
-// The elements of a B x B tile that a POTRF updates (columns 1..B-1, on and
-// below the diagonal), numbered column by column: entry t of the table is
-// (i << 8) | c, held by thread t % 128 in register slot t / 128.  Column-major
-// numbering makes the live elements of step j (c > j) a suffix, so finished
-// warps skip whole steps.  Filled once per CTA.
 template <int B>
 struct PotrfDf {
   static constexpr int NLIVE = B * (B - 1) / 2;
@@ -307,18 +234,6 @@ __device__ __forceinline__ int potrf_tile_df(double (&acc)[FactorCfg<B>::CPT], d
   return bad;
 }
 
-// The tile POTRF of the FP64 kernel: the division-free form up to B = 32, the
-// all-warps reciprocal form for B = 64.
-template <int B>
-__device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
-                                         double* sRs, int* sK, const uint16_t* sElem, int row, int q,
-                                         int tid) {
-  if constexpr (B <= 32)
-    return potrf_tile_df<B>(acc, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid, []() { __syncthreads(); });
-  else
-    return potrf_tile<B>(acc, sC, sPiv, sInv, sRs, row, q, tid);
-}
-
 // X L^T = acc, column by column, with L's columns pre-scaled by 1/L_jj (sLs:
 // L_cj / L_jj below the diagonal) so that the dependency chain of a column is
 // a shuffle and one FMA: the unscaled y_j = x_j L_jj is broadcast to the row's
@@ -342,6 +257,125 @@ __device__ __forceinline__ void trsm_rows(double (&acc)[FactorCfg<B>::CPT], cons
   for (int m = 0; m < CPT; ++m) acc[m] *= inv[m];
 }
 
+// Lower 8 x 8 blocks of X X^T (X: n rows of a column-major array with leading
+// dimension ld, k columns) on the FP64 tensor path (mma.sync m8n8k4, 256 FMAs
+// per warp instruction), block b to warp b % 4, into out (n x n, column-major;
+// the upper blocks untouched); n a multiple of 8, k of 4.
+__device__ __forceinline__ void syrk_mma(const double* X, int ld, int n, int k, double* out, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
+  const int nb = n / 8;
+  for (int bk = warp; bk < nb * (nb + 1) / 2; bk += 4) {
+    int bi = 0;
+    while ((bi + 1) * (bi + 2) / 2 <= bk) ++bi;
+    const int bj = bk - bi * (bi + 1) / 2;  // block (bi, bj), bj <= bi, in 8-row units
+    double d0 = 0.0, d1 = 0.0;
+    for (int ks = 0; ks < k; ks += 4) {
+      const double fa = X[(ks + tq) * ld + 8 * bi + g];  // A(g, tq) = X(8 bi + g, ks + tq)
+      const double fb = X[(ks + tq) * ld + 8 * bj + g];  // B(tq, g) = X(8 bj + g, ks + tq)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(d0), "+d"(d1)
+                   : "d"(fa), "d"(fb));
+    }
+    out[(8 * bi + g) + (8 * bj + 2 * tq) * n] = d0;
+    out[(8 * bi + g) + (8 * bj + 2 * tq + 1) * n] = d1;
+  }
+}
+
+// FP64 POTRF of the H x H block at S (column-major, leading dimension ld, lower
+// triangle of the input read; H = 16, 32 or 64) in place.  H = 16: the
+// division-free POTRF.  Larger H by H/2 x H/2 blocks:
+//   L11 = chol(A11), L21 = A21 L11^{-T} (rows against L11 with its columns
+//   pre-scaled by 1/L_jj), A22 -= L21 L21^T (FP64 tensor path), L22 = chol(A22),
+// so every step keeps all 128 threads busy (a block row per 256 / H threads)
+// where an H-wide elimination runs H dependent steps.  S receives L (zero
+// strict upper triangle), inv the H values 1/L_jj.  Returns the first bad
+// pivot (the block is then NaN) or -1.  sElem16: the 16-wide POTRF's element
+// numbering (init_df_elements<16>).  Scratch: 1 KB + H^2 / 4 doubles per level.
+// `tid` counts the 128 threads from 0; `sync` is their barrier.
+template <int H, class Sync>
+__device__ int potrf_blocked(double* S, int ld, double* inv, double* scratch, const uint16_t* sElem16, int tid,
+                             Sync sync) {
+  if constexpr (H == 16) {
+    using C = FactorCfg<16>;
+    constexpr int RPT = C::RPT, CPT = C::CPT;
+    const int row = tid / RPT, q = tid % RPT;
+    double* sW = scratch;  // 16 x 16
+    double* sPiv = sW + H * H;
+    double* sInv = sPiv + H;
+    double* sRs = sInv + H;
+    int* sK = reinterpret_cast<int*>(sRs + H);
+    double acc[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + row];
+    const int bad = potrf_tile_df<16>(acc, sW, sPiv, sInv, sRs, sK, sElem16, row, q, tid, sync);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + row] = acc[m];
+    if (tid < H) inv[tid] = sInv[tid];
+    sync();
+    return bad;
+  } else {
+    constexpr int G = H / 2;
+    using C = FactorCfg<G>;
+    constexpr int RPT = C::RPT, CPT = C::CPT;
+    const int row = tid / RPT, q = tid % RPT;
+    double* sC = scratch;          // G x G: pre-scaled L11, then the A22 update
+    double* sub = scratch + G * G;  // the half-size calls' scratch
+    const int bad1 = potrf_blocked<G>(S, ld, inv, sub, sElem16, tid, sync);
+    double iv[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      iv[m] = inv[c];
+      S[(G + c) * ld + row] = 0.0;                             // upper right block
+      if (row > c) sC[row + c * G] = S[c * ld + row] * iv[m];  // L11(row, c) / L11(c, c)
+    }
+    sync();
+    // L21 = A21 L11^{-T}
+    double acc[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + G + row];
+    trsm_rows<G>(acc, iv, sC, q, (tid & 31) - q);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + G + row] = acc[m];
+    sync();
+    // A22 - L21 L21^T (lower triangle)
+    syrk_mma(S + G, ld, G, G, sC, tid);
+    sync();
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int c = q + RPT * m;
+      if (c <= row) S[(G + c) * ld + G + row] -= sC[row + c * G];
+    }
+    sync();
+    const int bad2 = potrf_blocked<G>(S + G * ld + G, ld, inv + G, sub, sElem16, tid, sync);
+    return bad1 >= 0 ? bad1 : (bad2 >= 0 ? G + bad2 : -1);
+  }
+}
+
+// The tile POTRF of the FP64 kernel: the division-free form at B = 16; at
+// B = 32 and 64 by halves down to 16 x 16 leaves (potrf_blocked), on the tile
+// written to sC, with `scratch` (free shared memory) for the blocked steps.
+template <int B>
+__device__ __forceinline__ int potrf_any(double (&acc)[FactorCfg<B>::CPT], double* sC, double* sPiv, double* sInv,
+                                         double* sRs, int* sK, const uint16_t* sElem16, double* scratch, int row,
+                                         int q, int tid) {
+  auto sync = []() { __syncthreads(); };
+  if constexpr (B == 16) {
+    return potrf_tile_df<16>(acc, sC, sPiv, sInv, sRs, sK, sElem16, row, q, tid, sync);
+  } else {
+    constexpr int RPT = FactorCfg<B>::RPT, CPT = FactorCfg<B>::CPT;
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) sC[(q + RPT * m) * B + row] = acc[m];
+    sync();
+    const int bad = potrf_blocked<B>(sC, B, sInv, scratch, sElem16, tid, sync);
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) acc[m] = sC[(q + RPT * m) * B + row];
+    sync();
+    return bad;
+  }
+}
+
 template <int B>
 __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   using Cfg = FactorCfg<B>;
@@ -357,15 +391,14 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
   double* sInvL = sRs + 2 * B;                 // 1/L_jj of the diagonal tile a TRSM applies (16-byte aligned)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sInvL + B);
   __shared__ int sTicket, sAbort;
-  constexpr bool PW = B <= 32;  // division-free POTRF
-  __shared__ uint16_t sElem[PW ? PotrfDf<B>::NLIVE : 1];
+  __shared__ uint16_t sElem[PotrfDf<16>::NLIVE];  // the 16-wide division-free POTRF's elements
 
   const int tid = threadIdx.x;
   const int row = tid / RPT;
   const int q = tid % RPT;
   const int lane = tid & 31;
   const int row_lane0 = lane - (lane % RPT);  // first lane of this row inside the warp
-  if constexpr (PW) init_df_elements<B>(sElem, tid, 128);
+  init_df_elements<16>(sElem, tid, 128);
 
   if (tid == 0) {
     for (int s = 0; s <= NSTAGE; ++s) mbar_init(&bars[s], 1);
@@ -564,7 +597,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
     }
 
     if (tk.type == TASK_DIAG) {
-      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
+      const int bad = potrf_any<B>(acc1, sC, sPiv, sInv, sRs, sK, sElem, sStage, row, q, tid);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col * B + bad + 1);
       double* dst = mc.tiles + size_t(tk.out) * TILE;
 #pragma unroll
@@ -659,7 +692,7 @@ __global__ void __launch_bounds__(128) factor_f64_kernel(FactorArgs a) {
         for (int m = 0; m < CPT; ++m) acc2[m] = fma(-av, sL[q + RPT * m + p * B], acc2[m]);
       }
     }
-    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sElem, row, q, tid);
+    const int bad = potrf_any<B>(acc2, sC, sPiv, sInv, sRs, sK, sElem, sStage, row, q, tid);
     if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)tk.col2 * B + bad + 1);
     {
       double* dst = mc.tiles + size_t(tk.out2) * TILE;

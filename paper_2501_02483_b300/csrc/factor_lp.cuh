@@ -136,101 +136,7 @@ __device__ __forceinline__ void lp_store_row(const LPMatCtx& mc, int fp16, int s
   }
 }
 
-// Lower 8 x 8 blocks of X X^T (X: n rows of a column-major array with leading
-// dimension ld, k columns) on the FP64 tensor path (mma.sync m8n8k4, 256 FMAs
-// per warp instruction), block b to warp b % 4, into out (n x n, column-major;
-// the upper blocks untouched); n a multiple of 8, k of 4.
-__device__ __forceinline__ void lp_syrk_mma(const double* X, int ld, int n, int k, double* out, int tid) {
-  const int warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, tq = lane & 3;  // fragment row / column group of this lane
-  const int nb = n / 8;
-  for (int bk = warp; bk < nb * (nb + 1) / 2; bk += 4) {
-    int bi = 0;
-    while ((bi + 1) * (bi + 2) / 2 <= bk) ++bi;
-    const int bj = bk - bi * (bi + 1) / 2;  // block (bi, bj), bj <= bi, in 8-row units
-    double d0 = 0.0, d1 = 0.0;
-    for (int ks = 0; ks < k; ks += 4) {
-      const double fa = X[(ks + tq) * ld + 8 * bi + g];  // A(g, tq) = X(8 bi + g, ks + tq)
-      const double fb = X[(ks + tq) * ld + 8 * bj + g];  // B(tq, g) = X(8 bj + g, ks + tq)
-      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                   : "+d"(d0), "+d"(d1)
-                   : "d"(fa), "d"(fb));
-    }
-    out[(8 * bi + g) + (8 * bj + 2 * tq) * n] = d0;
-    out[(8 * bi + g) + (8 * bj + 2 * tq + 1) * n] = d1;
-  }
-}
-
 __shared__ uint16_t lp_sElem16[PotrfDf<16>::NLIVE];  // element numbering of the 16-wide POTRF
-
-// FP64 POTRF of the H x H block at S (column-major, leading dimension ld, lower
-// triangle of the input read; H = 16, 32 or 64) in place.  H = 16: the
-// division-free POTRF.  Larger H by H/2 x H/2 blocks:
-//   L11 = chol(A11), L21 = A21 L11^{-T} (rows against L11 with its columns
-//   pre-scaled by 1/L_jj), A22 -= L21 L21^T (FP64 tensor path), L22 = chol(A22),
-// so every step keeps all 128 threads of the slot busy (a block row per
-// 256 / H threads) where an H-wide elimination runs H dependent steps.  S
-// receives L (zero strict upper triangle), inv the H values 1/L_jj.  Returns
-// the first bad pivot (the block is then NaN) or -1.  Scratch: 1 KB + H^2 / 4
-// doubles per level.
-template <int H, class Sync>
-__device__ int lp_potrf_blocked(double* S, int ld, double* inv, double* scratch, int tid, Sync sync) {
-  if constexpr (H == 16) {
-    using C = FactorCfg<16>;
-    constexpr int RPT = C::RPT, CPT = C::CPT;
-    const int row = tid / RPT, q = tid % RPT;
-    double* sW = scratch;  // 16 x 16
-    double* sPiv = sW + H * H;
-    double* sInv = sPiv + H;
-    double* sRs = sInv + H;
-    int* sK = reinterpret_cast<int*>(sRs + H);
-    double acc[CPT];
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + row];
-    const int bad = potrf_tile_df<16>(acc, sW, sPiv, sInv, sRs, sK, lp_sElem16, row, q, tid, sync);
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + row] = acc[m];
-    if (tid < H) inv[tid] = sInv[tid];
-    sync();
-    return bad;
-  } else {
-    constexpr int G = H / 2;
-    using C = FactorCfg<G>;
-    constexpr int RPT = C::RPT, CPT = C::CPT;
-    const int row = tid / RPT, q = tid % RPT;
-    double* sC = scratch;          // G x G: pre-scaled L11, then the A22 update
-    double* sub = scratch + G * G;  // the half-size calls' scratch
-    const int bad1 = lp_potrf_blocked<G>(S, ld, inv, sub, tid, sync);
-    double iv[CPT];
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) {
-      const int c = q + RPT * m;
-      iv[m] = inv[c];
-      S[(G + c) * ld + row] = 0.0;                             // upper right block
-      if (row > c) sC[row + c * G] = S[c * ld + row] * iv[m];  // L11(row, c) / L11(c, c)
-    }
-    sync();
-    // L21 = A21 L11^{-T}
-    double acc[CPT];
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) acc[m] = S[(q + RPT * m) * ld + G + row];
-    trsm_rows<G>(acc, iv, sC, q, (tid & 31) - q);
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) S[(q + RPT * m) * ld + G + row] = acc[m];
-    sync();
-    // A22 - L21 L21^T (lower triangle)
-    lp_syrk_mma(S + G, ld, G, G, sC, tid);
-    sync();
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) {
-      const int c = q + RPT * m;
-      if (c <= row) S[(G + c) * ld + G + row] -= sC[row + c * G];
-    }
-    sync();
-    const int bad2 = lp_potrf_blocked<G>(S + G * ld + G, ld, inv + G, sub, tid, sync);
-    return bad1 >= 0 ? bad1 : (bad2 >= 0 ? G + bad2 : -1);
-  }
-}
 
 // One task slot: 128 threads (4 warps) running the persistent task loop on
 // their own shared-memory area, mbarriers, TMEM columns and ticket, with a
@@ -523,7 +429,7 @@ __device__ __forceinline__ void lp_slot(const LPArgs& a, uint32_t tmem, int tid)
     sync();
     {
       // the stage area (every MMA of the task has completed) holds the POTRF's scratch
-      const int bad = lp_potrf_blocked<LP_B>(sD, LP_B, sInv, reinterpret_cast<double*>(sStage), tid, sync);
+      const int bad = potrf_blocked<LP_B>(sD, LP_B, sInv, reinterpret_cast<double*>(sStage), lp_sElem16, tid, sync);
       if (bad >= 0 && tid == 0) atomicMin(mc.info, (unsigned long long)col * LP_B + bad + 1);
     }
     if (warp < 2) {
