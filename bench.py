@@ -58,8 +58,8 @@ METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set res
 # DRAM bytes per launch of the factorization kernel, from an ncu capture (see
 # profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
 # changed after the capture.
-TRAFFIC = {("factor_f64_v8", "large", 16, 16): 1.352e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
-KERNEL_TAG = "factor_f64_v8"
+TRAFFIC = {("factor_f64_v9_fwd", "large", 16, 16): 1.415e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
+KERNEL_TAG = "factor_f64_v9_fwd"
 
 
 def parse():
@@ -111,7 +111,9 @@ def workload_config(args, info=None):
                "n": args.rows + 100, "n_arrow": 100, "nrhs": 4, "tile": args.tile, "ordering": args.ordering,
                "l2": "inputs larger than L2 (values 0.26 GB, factor tiles > 0.7 GB vs 126 MB L2); no flush"}
     cfg.update({
-           "step": "factorize + logdet + solve (analysis once per pattern, timed separately)",
+           "step": ("factorize + logdet + solve (analysis once per pattern, timed separately); FP64: the "
+                    "forward sweep inside the factorization launch (stiles_factorize_solve), then the "
+                    "backward sweep"),
            "flops": "tile-level task flops of Algorithm 1 at tile T (POTRF b(b+1)(2b+1)/6, SYRK kb(b+1), "
                     "GEMM 2mnk, TRSM mb^2)"})
     if info:
@@ -278,8 +280,16 @@ def run_ours(args):
 
     f = st.Factor(plan)
     stream = torch.cuda.current_stream(dev)
+    # FP64: the forward sweep runs inside the factorization launch
+    # (stiles_factorize_solve); mixed precision: factorize, then the refined solve
+    fused = prec == st.PREC_F64 and nrhs <= min(info["block"], 16)
+    x_d = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev).t()  # n x nrhs, column-major
 
     def step_device():
+        if fused:
+            x = f.factorize_solve(vals_d, b_d, x=x_d, stream=stream)
+            ld = f.logdet()
+            return ld, x
         f.factorize(vals_d, stream=stream)
         ld = f.logdet()
         x = f.solve(b_d, stream=stream)
@@ -313,17 +323,29 @@ def run_ours(args):
     value = world * flops / (ms * 1e-3) / 1e12
 
     # end to end through host buffers (pinned): H2D values + RHS, D2H x + logdet
-    for _ in range(1):
-        f.factorize(vals_host)
-        f.solve(b_host, x=x_host)
+    vals_pin = torch.from_numpy(vals_host)
+    vals_stage = torch.empty_like(vals_d)
+    b_stage = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev)
+
+    def step_e2e():
+        if fused:  # explicit copies: the folded call takes device arrays
+            vals_stage.copy_(vals_pin, non_blocking=True)
+            b_stage.copy_(bt, non_blocking=True)
+            f.factorize_solve(vals_stage, b_stage.t(), x=x_d, stream=stream)
+            f.logdet()
+            xt.copy_(x_d.t())
+        else:
+            f.factorize(vals_host)
+            f.logdet()
+            f.solve(b_host, x=x_host)
+
+    step_e2e()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f.factorize(vals_host)
-        f.logdet()
-        f.solve(b_host, x=x_host)
+        step_e2e()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     if dist:
@@ -378,7 +400,9 @@ def run_ours(args):
     if prec == st.PREC_F64:
         traffic = TRAFFIC.get((KERNEL_TAG, args.workload, args.tile, info["block"]))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"factor_f64_kernel<{info['block']}>", "kernel_ms": kms,
+                "traffic": traffic, "kernel_ms": kms,
+                "kernel": f"factor_f64_kernel<{info['block']}>" + (" (forward sweep folded in; achieved counts the "
+                                                                    "factorization's flops only)" if fused else ""),
                 "peak_source": "FP64 DFMA probe of libstiles.so measured in this run (MEASURED_PEAKS.json "
                                "has no FP64 entry)"}
     else:

@@ -140,6 +140,20 @@ stiles_status stiles_factor_wait(stiles_factor* factor, int64_t* info);
 /* log det A = 2 sum_i log L_ii, reduced on the device in a fixed order; *out on the host. */
 stiles_status stiles_logdet(const stiles_factor* factor, double* out);
 
+/* Factorize and solve in one pass (FP64 plans): the forward sweep L Y = P B runs inside the
+ * factorization's persistent launch (Algorithm 1's task graph plus one task per B-row block of
+ * the right-hand sides, which are held transposed as tiles after the factor's; each block is
+ * the same update-and-TRSM step as an off-diagonal tile), so the forward chain follows the
+ * factorization instead of running after it; then the backward sweep L^T P X = Y.  The factor
+ * is left as stiles_factorize leaves it (stiles_logdet, stiles_solve, ... apply).
+ *   values : as stiles_factorize;  b, x : n x nrhs device arrays, column-major, leading
+ *            dimension ld >= n; 1 <= nrhs <= min(B, 16); x may equal b.
+ *   inout, info : as stiles_factorize.
+ * Errors: STILES_ERR_INVALID (null, sizes, host arrays), STILES_ERR_UNSUPPORTED (mixed-precision
+ * plan), STILES_ERR_NOT_SPD, STILES_ERR_TIMEOUT, STILES_ERR_NOMEM, STILES_ERR_CUDA. */
+stiles_status stiles_factorize_solve(const stiles_plan* plan, const double* values, const double* b, double* x,
+                                     int32_t nrhs, int64_t ld, void* stream, stiles_factor** inout, int64_t* info);
+
 /* Solve A X = B for nrhs right-hand sides: X = P^T L^{-T} L^{-1} P B.
  * For a BF16/FP16 factor the solve refines in FP64: x <- x + solve(b - A x) with the residual
  * from the original FP64 values, until ||b - A x||_2 / ||b||_2 <= opts.refine_tol for every
@@ -201,8 +215,10 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
  * set when read transposed; U sub-tile); 5 = loads of finished terms, 3 int32 each (the Sigma
  * sub-tile whose flag guards the term; the flag value it waits for (1); term sub-tile, bit 30
  * set when the term is in W (a diagonal task's terms), else in X);
- * 6 = X products, 1 int32 each (sub-tile of U and X).  *ntasks receives the number of
- * entries.  out may be NULL to query ntasks. */
+ * 6 = X products, 1 int32 each (sub-tile of U and X).  which = 7: the tasks of the
+ * factorization with the forward sweep folded in (stiles_factorize_solve; 16 int32 each as for
+ * which = 0; a forward block k is an OFF task with output nsub + k).  *ntasks receives the
+ * number of entries.  out may be NULL to query ntasks. */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */

@@ -939,6 +939,120 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   return STILES_OK;
 }
 
+// The factorization with the forward sweep folded in.  With block k's
+// right-hand sides stored transposed as a tile (Y_k^T, a row per right-hand
+// side), the forward step Y_k^T = (b_k^T - sum_j Y_j^T L_kj^T) L_kk^{-T} is an
+// OFF task of the factor kernel: its pair loop forms acc -= A B^T with
+// A = Y_j^T (tile nsub + j) and B = L_kj, and its row TRSM applies L_kk.  The
+// forward solve graph's tasks are mapped one to one (tree partials to
+// PARTIAL/COMBINE tasks on scratch tiles after the factor's) and each is
+// placed right after the last producer of its inputs, so the forward chain
+// follows the factorization instead of running after it.
+stiles_status build_fused(stiles_plan* p, std::string* err) {
+  if (p->fused_built) return STILES_OK;
+  if (!p->executable) { *err = "the plan has no sub-tile executor"; return STILES_ERR_UNSUPPORTED; }
+  const TaskGraph& fg = p->graph;
+  const SolveGraph& sg = p->fwd;
+  const int64_t nsub = p->nsub, nsb = p->nsb, nf = int64_t(fg.tasks.size());
+  // ticket of the factor task that produces each sub-tile
+  std::vector<int64_t> tout(size_t(nsub), -1);
+  for (int64_t t = 0; t < nf; ++t) {
+    const DevTask& tk = fg.tasks[size_t(t)];
+    if (tk.type == TASK_PARTIAL || tk.type == TASK_COMBINE) continue;
+    tout[size_t(tk.out)] = t;
+    if (tk.out2 >= 0) tout[size_t(tk.out2)] = t;
+  }
+  // forward tasks: mapped task and the factor ticket it must follow
+  const int64_t ns = int64_t(sg.tasks.size());
+  std::vector<int64_t> key(size_t(ns), -1), kblk(size_t(nsb), -1), kscr(size_t(std::max<int64_t>(sg.nscratch, 1)), -1);
+  TaskGraph out;
+  std::vector<DevTask> ftask(static_cast<size_t>(ns));
+  std::vector<int32_t> fpairs, fparts;
+  for (int64_t t = 0; t < ns; ++t) {
+    const SolveTask& st = sg.tasks[size_t(t)];
+    int64_t k = -1;
+    DevTask d{};
+    d.out2 = -1;
+    d.col2 = -1;
+    d.diag = -1;
+    d.pb2 = d.pe2 = d.qb2 = d.qe2 = 0;
+    d.pad0 = d.pad1 = 0;
+    const int64_t pb = int64_t(fpairs.size()) / 2;
+    for (int32_t q = st.pb; q < st.pe; ++q) {
+      const int32_t ls = sg.pairs[2 * size_t(q)], bk = sg.pairs[2 * size_t(q) + 1];
+      if (ls < 0 || ls >= nsub || bk < 0 || bk >= nsb || tout[size_t(ls)] < 0 || kblk[size_t(bk)] < 0) {
+        *err = "internal: forward operand without a producer";
+        return STILES_ERR_INVALID;
+      }
+      fpairs.push_back(int32_t(nsub + bk));
+      fpairs.push_back(ls);
+      k = std::max({k, tout[size_t(ls)], kblk[size_t(bk)]});
+    }
+    const int64_t qb = int64_t(fparts.size());
+    for (int32_t q = st.qb; q < st.qe; ++q) {
+      const int32_t sc = sg.parts[size_t(q)];
+      if (sc < 0 || sc >= sg.nscratch || kscr[size_t(sc)] < 0) { *err = "internal: forward partial order"; return STILES_ERR_INVALID; }
+      fparts.push_back(int32_t(fg.nscratch + sc));
+      k = std::max(k, kscr[size_t(sc)]);
+    }
+    d.pb = int32_t(pb);
+    d.pe = int32_t(fpairs.size() / 2);
+    d.qb = int32_t(qb);
+    d.qe = int32_t(fparts.size());
+    if (st.type == SOLVE_FINAL) {
+      if (st.diag < 0 || st.diag >= nsub || tout[size_t(st.diag)] < 0) { *err = "internal: forward diagonal"; return STILES_ERR_INVALID; }
+      d.type = TASK_OFF;
+      d.out = int32_t(nsub + st.out);
+      d.diag = st.diag;
+      d.col = st.out;
+      k = std::max(k, tout[size_t(st.diag)]);
+      kblk[size_t(st.out)] = k;
+    } else {
+      d.type = (st.type == SOLVE_PARTIAL) ? TASK_PARTIAL : TASK_COMBINE;
+      d.out = int32_t(fg.nscratch + st.out);
+      d.col = -1;
+      kscr[size_t(st.out)] = k;
+    }
+    if (k < 0) { *err = "internal: forward task without inputs"; return STILES_ERR_INVALID; }
+    key[size_t(t)] = k;
+    ftask[size_t(t)] = d;
+  }
+  // merged ticket order: factor task i, then the forward tasks keyed to i (solve order)
+  std::vector<std::vector<int32_t>> after(static_cast<size_t>(nf));
+  for (int64_t t = 0; t < ns; ++t) after[size_t(key[size_t(t)])].push_back(int32_t(t));
+  out.pairs = fg.pairs;
+  out.parts = fg.parts;
+  const int64_t pshift = int64_t(out.pairs.size()) / 2, qshift = int64_t(out.parts.size());
+  out.pairs.insert(out.pairs.end(), fpairs.begin(), fpairs.end());
+  out.parts.insert(out.parts.end(), fparts.begin(), fparts.end());
+  out.nscratch = fg.nscratch + sg.nscratch;
+  out.tasks.reserve(size_t(nf + ns));
+  for (int64_t i = 0; i < nf; ++i) {
+    out.tasks.push_back(fg.tasks[size_t(i)]);
+    for (int32_t t : after[size_t(i)]) {
+      DevTask d = ftask[size_t(t)];
+      d.pb += int32_t(pshift);
+      d.pe += int32_t(pshift);
+      d.qb += int32_t(qshift);
+      d.qe += int32_t(qshift);
+      out.tasks.push_back(d);
+    }
+  }
+  if (!check_order(out.tasks, out.pairs, out.parts, nsub + nsb, std::max<int64_t>(out.nscratch, 1), TASK_PARTIAL,
+                   TASK_COMBINE, false, err))
+    return STILES_ERR_INVALID;
+  p->fused_chain.clear();
+  p->fused_bulk.clear();
+  for (size_t t = 0; t < out.tasks.size(); ++t) {
+    const int32_t ty = out.tasks[t].type;
+    const bool fwd = out.tasks[t].out >= nsub && ty != TASK_PARTIAL && ty != TASK_COMBINE;
+    ((ty == TASK_DIAG || ty == TASK_CHAIN) && !fwd ? p->fused_chain : p->fused_bulk).push_back(int32_t(t));
+  }
+  p->fused = std::move(out);
+  p->fused_built = true;
+  return STILES_OK;
+}
+
 // Task graph of the selected inverse (Sigma L = L^{-T}, every column block
 // after its ancestors).  For sub-column k with sub-rows S_k (p = min S_k, its
 // parent in the sub-column elimination tree) and U_jk = L_jk L_kk^{-1}:

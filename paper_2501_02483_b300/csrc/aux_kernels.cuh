@@ -134,6 +134,36 @@ __global__ void permute_in_kernel(TY* __restrict__ Y, const double* __restrict__
   }
 }
 
+// Block k of the permuted right-hand sides, transposed, into tile nsub + k of
+// the factor's tile array (element (r, i) at i B + r for r < nr; the other rows
+// stay zero): the forward sweep folded into the factorization reads them there.
+__global__ void rhs_to_tiles_kernel(double* __restrict__ tiles, const double* __restrict__ b,
+                                    const int64_t* __restrict__ perm, int64_t n, int64_t ld, int nr, int B,
+                                    int64_t nsb, int64_t nsub) {
+  const int64_t total = nsb * B * nr;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t k = e / (int64_t(B) * nr);
+    const int64_t rem = e % (int64_t(B) * nr);
+    const int r = int(rem / B), i = int(rem % B);
+    const int64_t g = k * B + i;
+    tiles[(nsub + k) * B * B + int64_t(i) * B + r] = (g < n) ? b[perm[g] + r * ld] : 0.0;
+  }
+}
+
+// The forward result tiles, transposed back into the sweeps' block layout.
+__global__ void tiles_to_blocks_kernel(double* __restrict__ Y, const double* __restrict__ tiles, int nr, int B,
+                                       int64_t nsb, int64_t nsub) {
+  const int64_t total = nsb * B * nr;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t k = e / (int64_t(B) * nr);
+    const int64_t rem = e % (int64_t(B) * nr);
+    const int r = int(rem / B), i = int(rem % B);
+    Y[e] = tiles[(nsub + k) * B * B + int64_t(i) * B + r];
+  }
+}
+
 template <typename TY>
 __global__ void permute_out_kernel(double* __restrict__ x, const TY* __restrict__ Y, const int64_t* __restrict__ perm,
                                    int64_t n, int64_t ld, int r0, int nr, int B) {

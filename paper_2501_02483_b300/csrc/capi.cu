@@ -91,6 +91,8 @@ struct DevPlan {
   int32_t* rcol = nullptr;
   int64_t* rval = nullptr;
   DevGraph fac, fwd, bwd;
+  DevGraph fus;          // factorization with the forward sweep folded in (built on first use)
+  bool fus_ready = false;
   int grid_factor = 0, grid_solve = 0;
   // selected inverse (uploaded on first use)
   int32_t* sinv_tasks = nullptr;
@@ -125,7 +127,7 @@ struct stiles_factor {
   double* cgs = nullptr;      // CG scalars: dot products and step lengths, 2 * SOLVE_MAXR
   int last_refine_iters = 0;
   int last_cg_iters = 0;      // of those, conjugate-gradient iterations (refinement stalled)
-  int* flags = nullptr;       // nsub + nscratch
+  int* flags = nullptr;       // nsub + nsb (sub-tiles, forward blocks) + scratch
   int* claim = nullptr;       // reserved-SM claims of a split factor launch
   stiles::dev::Ctl* ctl = nullptr;  // [0] factor, [1] forward, [2] backward
   double* logdet_part = nullptr;    // LOGDET_BLOCKS + 1
@@ -188,6 +190,7 @@ void free_dev_plan(stiles_plan* p) {
   free_graph(d->fac);
   free_graph(d->fwd);
   free_graph(d->bwd);
+  free_graph(d->fus);
   cudaFree(d->sinv_tasks);
   cudaFree(d->sinv_pairs);
   cudaFree(d->sinv_loads);
@@ -352,11 +355,13 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
   f->plan = p;
   cudaGetDevice(&f->device);
   const size_t tile = size_t(p->B) * p->B;
-  const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
+  // scratch and flags also cover the factorization with the forward sweep
+  // folded in: nsb more tiles (the right-hand-side blocks) and its partials
+  const int64_t nscr = std::max<int64_t>(p->graph.nscratch + p->fwd.nscratch, 1);
   f->lp = p->opts.precision != STILES_PREC_F64;
   cudaError_t e = cudaMalloc(&f->values, size_t(p->nnz) * sizeof(double));
   if (!f->lp) {
-    if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub) * tile * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub + p->nsb) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->linv, 5 * size_t(p->nsb) * tile * sizeof(double));
@@ -368,7 +373,7 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     if (e == cudaSuccess) e = cudaMalloc(&f->ldiag, size_t(p->nsb) * p->B * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->linv32, size_t(p->nsb) * tile * sizeof(float));
   }
-  if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + nscr) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&f->flags, size_t(p->nsub + p->nsb + nscr) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->ctl, 3 * sizeof(dev::Ctl));
   if (e == cudaSuccess) e = cudaMalloc(&f->claim, kChainSms * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&f->logdet_part, (dev::LOGDET_BLOCKS + 1) * sizeof(double));
@@ -386,16 +391,17 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
   return STILES_OK;
 }
 
-dev::MatCtx mat_ctx(const stiles_plan* p, stiles_factor* f) {
+dev::MatCtx mat_ctx(const stiles_plan* p, stiles_factor* f, bool fused = false) {
   dev::MatCtx c;
+  const DevGraph& g = fused ? p->dev->fus : p->dev->fac;
   c.tiles = f->tiles;
   c.scratch = f->scratch;
   c.invdiag = f->invdiag;
-  c.tasks = p->dev->fac.tasks;
-  c.pairs = p->dev->fac.pairs;
-  c.parts = p->dev->fac.parts;
+  c.tasks = g.tasks;
+  c.pairs = g.pairs;
+  c.parts = g.parts;
   c.flags = f->flags;
-  c.sflags = f->flags + p->nsub;
+  c.sflags = f->flags + p->nsub + p->nsb;
   c.info = f->info;
   c.trace = f->trace[0];
   return c;
@@ -412,25 +418,27 @@ dev::LPMatCtx lp_mat_ctx(const stiles_plan* p, stiles_factor* f) {
   c.pairs = p->dev->fac.pairs;
   c.parts = p->dev->fac.parts;
   c.flags = f->flags;
-  c.sflags = f->flags + p->nsub;
+  c.sflags = f->flags + p->nsub + p->nsb;
   c.info = f->info;
   c.trace = f->trace[0];
   return c;
 }
 
 template <int B>
-cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
+cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s, bool fused = false) {
   dev::FactorArgs a{};
-  a.single = mat_ctx(p, f);
+  const DevGraph& g = fused ? p->dev->fus : p->dev->fac;
+  a.single = mat_ctx(p, f, fused);
+  if (fused) a.single.trace = nullptr;  // the trace array is sized for the plain factorization
   a.mats = nullptr;
   a.tickets = nullptr;
-  a.ntasks = p->dev->fac.ntasks;
+  a.ntasks = g.ntasks;
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
-  a.chain = p->dev->fac.chain;
-  a.bulk = p->dev->fac.bulk;
-  a.nchain = int(p->chain_order.size());
-  a.nbulk = int(p->bulk_order.size());
+  a.chain = g.chain;
+  a.bulk = g.bulk;
+  a.nchain = int(fused ? p->fused_chain.size() : p->chain_order.size());
+  a.nbulk = int(fused ? p->fused_bulk.size() : p->bulk_order.size());
   a.sm_claim = f->claim;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
@@ -562,6 +570,20 @@ cudaError_t launch_solve(const stiles_plan* p, stiles_factor* f, cudaStream_t s,
   return cudaGetLastError();
 }
 
+// The backward sweep alone (the forward one having run inside the factorization).
+template <int B>
+cudaError_t launch_backward(const stiles_plan* p, stiles_factor* f, cudaStream_t s, int nr) {
+  dev::SolveArgs<double> a;
+  a.mats = nullptr;
+  a.tickets = nullptr;
+  a.spin_limit = p->opts.spin_limit;
+  a.single = solve_ctx<double>(p, f, true, nr, f->tiles, f->invdiag, f->linv, f->Y, f->sscratch, f->sflags);
+  a.ntasks = p->dev->bwd.ntasks;
+  a.ctl = f->ctl + 2;
+  dev::solve_kernel<B, true, double><<<p->dev->grid_solve, 128, dev::SolveCfg<B, double>::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
 stiles_status read_ctl(stiles_factor* f, int idx, int64_t* info) {
   dev::Ctl c;
   CUDA_TRY(cudaMemcpy(&c, f->ctl + idx, sizeof(c), cudaMemcpyDeviceToHost));
@@ -688,7 +710,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   f->stream = st;
   const size_t tile = size_t(p->B) * p->B;
-  const int64_t nscr = std::max<int64_t>(p->graph.nscratch, 1);
+  const int64_t nscr = std::max<int64_t>(p->graph.nscratch + p->fwd.nscratch, 1);
   CUDA_TRY(cudaEventRecord(f->ev[0], st));
   CUDA_TRY(cudaMemcpyAsync(f->values, values, size_t(p->nnz) * sizeof(double), cudaMemcpyDefault, st));
   if (!f->lp) {
@@ -708,7 +730,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
       CUDA_TRY(cudaGetLastError());
     }
   }
-  CUDA_TRY(cudaMemsetAsync(f->flags, 0, size_t(p->nsub + nscr) * sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(f->flags, 0, size_t(p->nsub + p->nsb + nscr) * sizeof(int), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl, 1);
   CUDA_TRY(cudaGetLastError());
   count_launch(p->pad.empty() ? 2 : 3);
@@ -748,6 +770,120 @@ stiles_status stiles_factorize(const stiles_plan* p, const double* values, void*
   stiles_status s = stiles_factorize_async(p, values, stream, inout);
   if (s != STILES_OK) return s;
   return stiles_factor_wait(*inout, info);
+}
+
+stiles_status stiles_factorize_solve(const stiles_plan* p, const double* values, const double* b, double* x,
+                                     int32_t nrhs, int64_t ld, void* stream, stiles_factor** inout, int64_t* info) {
+  if (info) *info = 0;
+  if (!p || !values || !b || !x || !inout) return fail(STILES_ERR_INVALID, "null argument");
+  if (p->opts.precision != STILES_PREC_F64)
+    return fail(STILES_ERR_UNSUPPORTED, "the forward sweep is folded into FP64 factorizations only");
+  if (nrhs < 1 || nrhs > std::min<int64_t>(p->B, dev::SOLVE_MAXR) || ld < p->n)
+    return fail(STILES_ERR_INVALID, "nrhs must be 1 .. min(B, 16) and ld >= n");
+  if (!is_device_ptr(b) || !is_device_ptr(x)) return fail(STILES_ERR_INVALID, "b and x must be device memory");
+  stiles_status s = ensure_dev_plan(p);
+  if (s != STILES_OK) return s;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    stiles_plan* pm = const_cast<stiles_plan*>(p);
+    std::string err;
+    s = build_fused(pm, &err);
+    if (s != STILES_OK) return fail(s, err);
+    DevPlan* d = pm->dev;
+    if (!d->fus_ready) {
+      cudaError_t e = upload(&d->fus.tasks, pm->fused.tasks);
+      if (e == cudaSuccess) e = upload(&d->fus.pairs, pm->fused.pairs);
+      if (e == cudaSuccess) e = upload(&d->fus.parts, pm->fused.parts);
+      if (e == cudaSuccess) e = upload(&d->fus.chain, pm->fused_chain);
+      if (e == cudaSuccess) e = upload(&d->fus.bulk, pm->fused_bulk);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? STILES_ERR_NOMEM : STILES_ERR_CUDA,
+                    std::string("folded graph upload: ") + cudaGetErrorString(e));
+      }
+      d->fus.ntasks = int(pm->fused.tasks.size());
+      d->fus_ready = true;
+    }
+  }
+  stiles_factor* f = *inout;
+  if (f && f->plan != p) return fail(STILES_ERR_INVALID, "factor belongs to another plan");
+  if (f && f->view) return fail(STILES_ERR_INVALID, "a factor of a batch is factorized through its batch");
+  if (!f) {
+    s = alloc_factor(p, &f);
+    if (s != STILES_OK) return s;
+    *inout = f;
+  }
+  const int64_t n = p->n, B = p->B;
+  const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
+  if (f->solve_nr < dev::SOLVE_MAXR) {
+    cudaFree(f->Y);
+    cudaFree(f->sscratch);
+    cudaFree(f->sflags);
+    cudaFree(f->ywork);
+    f->Y = f->sscratch = f->ywork = nullptr;
+    f->sflags = nullptr;
+    f->solve_nr = 0;
+    CUDA_TRY(cudaMalloc(&f->Y, size_t(p->nsb) * B * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&f->sscratch, size_t(nf + nb) * B * dev::SOLVE_MAXR * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&f->sflags, size_t(2 * p->nsb + nf + nb) * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&f->ywork, size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
+    f->solve_nr = dev::SOLVE_MAXR;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  f->stream = st;
+  const size_t tile = size_t(B) * B;
+  const int64_t nscr = std::max<int64_t>(p->graph.nscratch + p->fwd.nscratch, 1);
+  CUDA_TRY(cudaEventRecord(f->ev[0], st));
+  CUDA_TRY(cudaMemcpyAsync(f->values, values, size_t(p->nnz) * sizeof(double), cudaMemcpyDefault, st));
+  CUDA_TRY(cudaMemsetAsync(f->tiles, 0, size_t(p->nsub + p->nsb) * tile * sizeof(double), st));
+  dev::scatter_kernel<<<grid_for(p->nnz, 256), 256, 0, st>>>(f->tiles, f->values, p->dev->scatter, p->nnz);
+  CUDA_TRY(cudaGetLastError());
+  if (!p->pad.empty()) {
+    dev::set_ones_kernel<double><<<1, 128, 0, st>>>(f->tiles, p->dev->pad, int64_t(p->pad.size()));
+    CUDA_TRY(cudaGetLastError());
+  }
+  dev::rhs_to_tiles_kernel<<<grid_for(p->nsb * B * nrhs, 256), 256, 0, st>>>(f->tiles, b, p->dev->perm, n, ld, nrhs,
+                                                                           int(B), p->nsb, p->nsub);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(f->flags, 0, size_t(p->nsub + p->nsb + nscr) * sizeof(int), st));
+  dev::init_ctl_kernel<<<1, 32, 0, st>>>(f->ctl, 3);
+  CUDA_TRY(cudaGetLastError());
+  count_launch(p->pad.empty() ? 3 : 4);
+  CUDA_TRY(cudaEventRecord(f->ev[1], st));
+  cudaError_t e;
+  switch (B) {
+    case 16: e = launch_factor<16>(p, f, st, true); break;
+    case 32: e = launch_factor<32>(p, f, st, true); break;
+    default: e = launch_factor<64>(p, f, st, true); break;
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(e));
+  count_launch();
+  CUDA_TRY(cudaEventRecord(f->ev[2], st));
+  e = launch_diag_inverse(p, f, st);
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("diagonal inverses: ") + cudaGetErrorString(e));
+  count_launch(2);
+  CUDA_TRY(cudaEventRecord(f->done, st));
+  f->sinv_valid = false;
+  // the backward sweep from the forward result tiles
+  dev::tiles_to_blocks_kernel<<<grid_for(p->nsb * B * nrhs, 256), 256, 0, st>>>(f->Y, f->tiles, nrhs, int(B), p->nsb,
+                                                                              p->nsub);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(f->sflags, 0, size_t(2 * p->nsb + nf + nb) * sizeof(int), st));
+  switch (B) {
+    case 16: e = launch_backward<16>(p, f, st, nrhs); break;
+    case 32: e = launch_backward<32>(p, f, st, nrhs); break;
+    default: e = launch_backward<64>(p, f, st, nrhs); break;
+  }
+  if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
+  dev::permute_out_kernel<double><<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, f->Y, p->dev->perm, n, ld, 0, nrhs,
+                                                                          int(B));
+  CUDA_TRY(cudaGetLastError());
+  count_launch(3);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  f->pending = false;
+  s = read_ctl(f, 0, info);
+  if (s != STILES_OK) return s;
+  return read_ctl(f, 2, nullptr);
 }
 
 stiles_status stiles_logdet(const stiles_factor* cf, double* out) {
@@ -1285,7 +1421,17 @@ stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int
 }
 
 stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
-  if (!p || which < 0 || which > 6) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!p || which < 0 || which > 7) return fail(STILES_ERR_INVALID, "bad argument");
+  if (which == 7) {  // the factorization with the forward sweep folded in (host only; built on first use)
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    stiles_plan* pm = const_cast<stiles_plan*>(p);
+    std::string err;
+    stiles_status s = build_fused(pm, &err);
+    if (s != STILES_OK) return fail(s, err);
+    if (ntasks) *ntasks = int64_t(pm->fused.tasks.size());
+    if (out && !pm->fused.tasks.empty()) std::memcpy(out, pm->fused.tasks.data(), pm->fused.tasks.size() * sizeof(DevTask));
+    return STILES_OK;
+  }
   if (which >= 3) {  // the selected inverse's graph (host only; built on first use)
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     stiles_plan* pm = const_cast<stiles_plan*>(p);
@@ -2036,7 +2182,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     b->tile_elems += p->nsub * TB;
     b->scratch_elems += std::max<int64_t>(p->graph.nscratch, 1) * TB;
     b->diag_elems += p->nsb * b->B;
-    b->flag_total += p->nsub + std::max<int64_t>(p->graph.nscratch, 1);
+    b->flag_total += p->nsub + p->nsb + std::max<int64_t>(p->graph.nscratch, 1);  // the factor flag layout
   }
   std::vector<BScatter> scat(count);
   for (int i = 0; i < count; ++i) {

@@ -116,6 +116,13 @@ struct stiles_plan {
   stiles::SolveGraph fwd, bwd;
   stiles::SelinvGraph selinv;        // built on first use (stiles_marginal_variances)
   bool selinv_built = false;
+  // factorization with the forward sweep folded in (built on first use): the
+  // factor tasks plus one OFF-type task per forward block (output nsub + k, the
+  // block's right-hand sides transposed as a tile) and the forward tree
+  // partials (scratch after the factor's), each right after its inputs' producers
+  stiles::TaskGraph fused;
+  std::vector<int32_t> fused_chain, fused_bulk;
+  bool fused_built = false;
   stiles::DevPlan* dev = nullptr;
 };
 
@@ -124,5 +131,6 @@ namespace stiles {
 stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx, int64_t n_arrow,
                          const stiles_opts& opts, stiles_plan* p, std::string* err);
 stiles_status build_selinv(stiles_plan* p, std::string* err);
+stiles_status build_fused(stiles_plan* p, std::string* err);
 void default_opts(stiles_opts* o);
 }  // namespace stiles

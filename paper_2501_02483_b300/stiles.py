@@ -59,6 +59,7 @@ def lib():
         L.stiles_plan_perm.argtypes = [P, P]
         L.stiles_plan_tilemap.argtypes = [P, P, P]
         L.stiles_factorize.argtypes = [P, P, P, POINTER(c_void_p), POINTER(c_int64)]
+        L.stiles_factorize_solve.argtypes = [P, P, P, P, c_int32, c_int64, P, POINTER(c_void_p), POINTER(c_int64)]
         L.stiles_factorize_async.argtypes = [P, P, P, POINTER(c_void_p)]
         L.stiles_factor_wait.argtypes = [P, POINTER(c_int64)]
         L.stiles_logdet.argtypes = [P, POINTER(c_double)]
@@ -94,7 +95,7 @@ def lib():
         L.stiles_kernel_launches.argtypes = []
         L.stiles_kernel_launches.restype = c_int64
         for name in ("stiles_analyze", "stiles_plan_get_info", "stiles_plan_perm", "stiles_plan_tilemap",
-                     "stiles_factorize", "stiles_factorize_async", "stiles_factor_wait", "stiles_logdet",
+                     "stiles_factorize", "stiles_factorize_solve", "stiles_factorize_async", "stiles_factor_wait", "stiles_logdet",
                      "stiles_solve", "stiles_factor_tiles", "stiles_probe_fp64_peak", "stiles_factor_timing",
                      "stiles_factor_set_trace", "stiles_factor_get_trace", "stiles_plan_tasks",
                      "stiles_batch_create", "stiles_batch_factorize", "stiles_batch_factor", "stiles_batch_logdet",
@@ -201,7 +202,7 @@ class Plan:
         (which 4: (n, 2)), loads of finished terms (which 5: (n, 3)) and X products (which 6: (n, 1))."""
         n = c_int64(0)
         _check(lib().stiles_plan_tasks(self._h, which, None, ctypes.byref(n)))
-        width = {0: 16, 1: 8, 2: 8, 3: 8, 4: 2, 5: 3, 6: 1}[which]
+        width = {0: 16, 1: 8, 2: 8, 3: 8, 4: 2, 5: 3, 6: 1, 7: 16}[which]
         out = np.empty((n.value, width), dtype=np.int32)
         _check(lib().stiles_plan_tasks(self._h, which, _ptr(out), ctypes.byref(n)))
         return out
@@ -232,6 +233,20 @@ class Factor:
                                     ctypes.byref(info))
         _check(st, info.value)
         return self
+
+    def factorize_solve(self, values, b, x=None, stream=None):
+        """Factorize and solve A X = B in one pass (FP64 plans; the forward sweep runs inside
+        the factorization launch).  values: as factorize; b: device torch (n,) or (n, nrhs)
+        column-major, nrhs <= min(B, 16).  Returns x (device, b's shape)."""
+        n = self.plan.n
+        b2 = b.reshape(n, -1) if b.dim() == 1 else b.t().contiguous().t()
+        nrhs = b2.shape[1]
+        out = b2.t().contiguous().t().clone() if x is None else x
+        info = c_int64(0)
+        st = lib().stiles_factorize_solve(self.plan.handle, _ptr(values), _ptr(b2), _ptr(out), int(nrhs), int(n),
+                                          _stream(stream), ctypes.byref(self._h), ctypes.byref(info))
+        _check(st, info.value)
+        return out.reshape(-1) if b.dim() == 1 else out
 
     def factorize_async(self, values, stream=None):
         _check(lib().stiles_factorize_async(self.plan.handle, _ptr(values), _stream(stream), ctypes.byref(self._h)))

@@ -270,3 +270,32 @@ def test_selected_inverse_graph_interleaves_nd_halves():
     body = cols[cols < 4000 // 16]
     first = body[:40]
     assert np.any(first < half) and np.any((first >= half) & (first < 2 * half))
+
+
+@pytest.mark.parametrize("T,order", [(16, st.ORDER_ND), (32, st.ORDER_RCM), (64, st.ORDER_AUTO)])
+def test_fused_graph_adds_one_forward_task_per_block(T, order):
+    """The factorization with the forward sweep folded in (host-built, checked for
+    ticket order when built): the factor's tasks in their order, plus the forward
+    solve graph's tasks, a forward block k being an OFF task with output nsub + k
+    placed after the task that finishes L_kk."""
+    m = inputs.band_arrow(3000, 24, 40, 0.4, 11, nrhs=2)
+    plan = st.Plan.from_matrix(m, tile=T, ordering=order)
+    inf = plan.info()
+    nsub, nsb = inf["nsub"], -(-m["n"] // inf["block"])
+    fac, fwd, fus = plan.tasks(0), plan.tasks(1), plan.tasks(7)
+    assert len(fus) == len(fac) + len(fwd)
+    is_fwd = (fus[:, 1] >= nsub) & (fus[:, 0] == 1)
+    assert sorted(fus[is_fwd, 1] - nsub) == list(range(nsb))
+    # factor tasks keep their relative order
+    fac_rows = [tuple(r) for r in fac]
+    kept = [tuple(r) for r, f in zip(fus, is_fwd) if not f and not (r[0] in (2, 3) and r[1] >= inf["nscratch"])]
+    assert kept == fac_rows
+    # each forward block follows the task that produces its diagonal sub-tile
+    pos = {}
+    for t, r in enumerate(fus):
+        if r[0] in (0, 1, 4) and r[1] < nsub:
+            pos[int(r[1])] = t
+            if r[0] == 4:
+                pos[int(r[8])] = t
+    for t in np.where(is_fwd)[0]:
+        assert pos[int(fus[t, 2])] < t
