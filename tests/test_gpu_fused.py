@@ -83,3 +83,24 @@ def test_fused_not_spd_and_bad_arguments():
         st.Factor(plan3).factorize_solve(torch.from_numpy(m2["values"]).cuda(),
                                          torch.ones(m2["n"], dtype=torch.float64).cuda())
     assert e3.value.name == "UNSUPPORTED"
+
+
+def test_fused_in_place_single_block_and_pure_arrowhead():
+    """x may equal b; a matrix of one padded block; a pure arrowhead (diagonal
+    body, dense arrow): the same results as the separate calls."""
+    cases = [inputs.band_arrow(7, 3, 2, 0.5, 5, nrhs=1)]  # n = 10: one block of 16, padded
+    pa = inputs.pure_arrowhead(400, 12, 3)
+    pa = pa[0] if isinstance(pa, tuple) else pa
+    cases.append(dict(pa, rhs=np.asfortranarray(np.random.default_rng(1).normal(size=(pa["n"], 3)))))
+    for m in cases:
+        plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_AUTO)
+        vd = torch.from_numpy(m["values"]).cuda()
+        b = torch.from_numpy(np.asfortranarray(m["rhs"])).cuda()
+        f1 = st.Factor(plan)
+        f1.factorize(vd)
+        x1 = f1.solve(b).cpu().numpy()
+        xb = b.clone()  # solved in place: x is b
+        st.Factor(plan).factorize_solve(vd, xb, x=xb)
+        x2 = xb.cpu().numpy()
+        assert np.max(np.abs(x2 - x1)) <= 1e-12 * np.max(np.abs(x1))
+        assert _residual(m, x2, m["rhs"]) <= 1e-12

@@ -299,3 +299,20 @@ def test_fused_graph_adds_one_forward_task_per_block(T, order):
                 pos[int(r[8])] = t
     for t in np.where(is_fwd)[0]:
         assert pos[int(fus[t, 2])] < t
+
+
+@pytest.mark.parametrize("n_body,n_arrow", [(7, 3), (0, 20), (300, 0)])
+def test_fused_graph_small_and_degenerate(n_body, n_arrow):
+    """One padded block, an arrow alone, a band alone: the merged graph still
+    holds every factor task and one forward OFF task per block."""
+    if n_body == 0:
+        m = inputs.diagonal_matrix(np.arange(1.0, n_arrow + 1.0), n_arrow=n_arrow)
+    else:
+        m = inputs.band_arrow(n_body, n_arrow, 3, 0.5, 2)
+    plan = st.Plan.from_matrix(m, tile=16)
+    inf = plan.info()
+    nsub, nsb = inf["nsub"], -(-m["n"] // inf["block"])
+    fac, fwd, fus = plan.tasks(0), plan.tasks(1), plan.tasks(7)
+    assert len(fus) == len(fac) + len(fwd)
+    is_fwd = (fus[:, 1] >= nsub) & (fus[:, 0] == 1)
+    assert sorted(fus[is_fwd, 1] - nsub) == list(range(nsb))
