@@ -264,6 +264,7 @@ struct TreeNode {
 
 constexpr int kTargetShift = 30;  // bit of a pair/partial index naming the CHAIN accumulator
 constexpr int64_t kChainKeep = 3;  // newest terms a diagonal-chain task applies itself
+constexpr int64_t kSweepKeep = 8;  // newest terms a sweep task keeps when its list is split into leaves
 constexpr double kSplitFlopsPerStep = 1e7;  // below: the chain runs on reserved SMs
 constexpr int32_t kIndexMask = (1 << 30) - 1;
 
@@ -313,10 +314,14 @@ inline void clear_second(SolveTask&) {}
 // so the sums of the old band terms are formed ahead of time by other CTAs
 // (Algorithm 3 applied to band rows) and the chain task applies only the
 // newest terms plus one partial.
+// min_own: a primary whose list is split into leaves by the chunk rule keeps at
+// least its newest min_own terms.  Used for the sweeps: a leaf holding one of a
+// chain block's newest inputs is finished one step before its owner at best, so
+// the chain would cross SMs twice per block (leaf, then owner).
 template <class Task>
 void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32_t leaf_type, int32_t comb_type,
                  std::vector<Task>& tasks, std::vector<int32_t>& pairs, std::vector<int32_t>& parts,
-                 int64_t& nscratch, uint32_t keep_types = 0, int64_t keep = 0) {
+                 int64_t& nscratch, uint32_t keep_types = 0, int64_t keep = 0, int64_t min_own = 0) {
   const int64_t np = int64_t(prim.size());
   std::vector<TreeNode> nodes;
   std::vector<int32_t> node_list;                     // which list of its owner a node belongs to
@@ -335,6 +340,7 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
         if (npairs > keep + 1) split = npairs - keep;
       } else if (npairs > chunk) {
         split = ((npairs + chunk - 1) / chunk - 1) * chunk;
+        if (npairs - split < min_own) split = std::max<int64_t>(0, npairs - min_own);
       }
       if (split == 0) continue;
       const int64_t nleaves = (split + chunk - 1) / chunk;
@@ -892,7 +898,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       }
     }
     build_graph(fp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->fwd.tasks, p->fwd.pairs,
-                p->fwd.parts, p->fwd.nscratch);
+                p->fwd.parts, p->fwd.nscratch, 0u, 0, kSweepKeep);
   }
   // backward sweep: one task per sub-column, descending
   {
@@ -913,7 +919,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       }
     }
     build_graph(bp, o.tree_chunk, o.tree_fanin, SOLVE_PARTIAL, SOLVE_COMBINE, p->bwd.tasks, p->bwd.pairs,
-                p->bwd.parts, p->bwd.nscratch);
+                p->bwd.parts, p->bwd.nscratch, 0u, 0, kSweepKeep);
   }
   if (p->graph.nscratch >= (int64_t(1) << 30)) { *err = "too many tree partials"; return STILES_ERR_UNSUPPORTED; }
   // the two queues of a split launch (critical diagonal chain / everything else)
