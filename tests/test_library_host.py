@@ -316,3 +316,23 @@ def test_fused_graph_small_and_degenerate(n_body, n_arrow):
     assert len(fus) == len(fac) + len(fwd)
     is_fwd = (fus[:, 1] >= nsub) & (fus[:, 0] == 1)
     assert sorted(fus[is_fwd, 1] - nsub) == list(range(nsb))
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_sweep_tasks_split_into_leaves_keep_their_newest_inputs(which):
+    """A sweep task with more inputs than a tree chunk (32 by default) sends only
+    its older inputs to tree leaves and keeps at least its 8 newest itself; the
+    leaves and the task's own list together name each input once."""
+    m = inputs.band_arrow(6000, 100, 500, 0.2, 3)  # up to 31 band blocks + 7 arrow blocks per column at B = 16
+    plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_NONE)
+    tasks = plan.tasks(which)
+    final = tasks[:, 0] == 0
+    own = tasks[:, 5] - tasks[:, 4]
+    has_parts = tasks[:, 7] > tasks[:, 6]
+    assert np.any(final & has_parts)
+    assert np.all(own[final & has_parts] >= 8)
+    assert np.all(own[final & ~has_parts] <= 32)
+    leaves = tasks[tasks[:, 0] == 2]
+    assert np.all(leaves[:, 5] - leaves[:, 4] <= 32)
+    # every input once: the owners' and the leaves' pair counts add up to the sweep's pair total
+    assert own[final].sum() + (leaves[:, 5] - leaves[:, 4]).sum() == tasks[:, 5].max()
