@@ -69,7 +69,8 @@ typedef struct {
   int32_t precision;  /* STILES_PREC_*: arithmetic of the off-diagonal tile updates.  Default F64. */
   int32_t block;      /* B, the device sub-tile size: 16, 32 or 64 dividing T; 0 = min(T, 32).   */
   int32_t tree_chunk; /* accumulation terms per tree leaf (Algorithm 3); 0 = 32.  Tasks with more
-                         terms are split into leaves summed by a fixed-shape tree.               */
+                         terms are split into leaves summed by a fixed-shape tree; a sweep task
+                         keeps at least its 8 newest terms, a diagonal-chain task its 3 newest. */
   int32_t tree_fanin; /* partial tiles summed per tree node; 0 = 16.                             */
   int32_t max_refine; /* iterative-refinement steps for low-precision factors; default 20.      */
   int32_t ctas_per_sm; /* resident CTAs per SM of the persistent kernels; 0 = as many as fit.  Fewer
