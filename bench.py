@@ -1,39 +1,43 @@
-"""Benchmark: FP64 arrowhead tile Cholesky + log-determinant + solve on one B300.
+"""Benchmark: arrowhead tile Cholesky + log-determinant + solves on one B300.
 
-Workload (default): the large single matrix -- a 200,000-row band whose lower
-half-width is drawn uniformly from 100..500 per 2,000-row segment (in-band
-density 0.2, U(-1,1)), plus 100 dense N(0,1) arrow rows, diagonal = row |sum|
-+ 1, four N(0,1) right-hand sides, seed 0.  Synthetic data of the paper's
-spatial/INLA arrowhead shape.
+Headline (default): the largest configuration, the spatio-temporal INLA-like
+precision -- Q_t (x) Q_s with an AR(1) temporal precision (n_t = 100,
+rho = 0.9) and the spatial (kappa^2 I + L)^2 of a 45 x 45 5-point grid
+(kappa^2 = 1), time-major, plus 20 dense fixed-effect arrow rows/columns
+(N(0, 0.1^2), diagonal dominance +1): n = 202,520, one N(0,1) right-hand
+side, seed 0.  FP64, tile 16, one level of the adaptable nested dissection.
 
 One step = factorize (value copy, CTSF scatter, persistent factorization
-kernel) + log-determinant + 4-RHS solve, all through the C ABI.  The
-symbolic analysis is done once per pattern and timed separately (the paper
-excludes preprocessing).  Inputs are larger than L2 (values 0.26 GB, factor
-tiles >= 0.7 GB vs 126 MB of L2), so no explicit flush is needed.
+kernel with the forward sweep folded in) + log-determinant + backward sweep,
+all through the C ABI.  The symbolic analysis is done once per pattern and
+timed separately (the paper excludes preprocessing).  Inputs are larger than
+L2 (factor tiles > 1 GB vs 126 MB of L2), so no explicit flush is needed.
 
 value  = tile-level factorization task flops / device time per step [TFLOP/s]
 e2e    = the same through host buffers (H2D of values and RHS, D2H of x and
          the log-determinant inside the timed region)
 
-Other workloads (--workload):
-  sweep  256 matrices of a hyperparameter sweep (n log-uniform in [5,000,
-         50,000], half-width in {64,128,256}, arrow 0..50, values scaled by
-         theta ~ U(0.5, 2)); one step = batched factorization in one persistent
-         launch + all log-determinants + batched solves refined to residual
-         1e-10; mixed precision (BF16 updates) timed beside FP64.
-  serve  Poisson request stream (500 req/s) of factorize+logdet+solve and
-         re-solve requests through the continuous-batching loop; p50/p99
-         latency and solves/s at residual 1e-10, BF16 beside FP64.
+Nested in the same line (``config``), each with its own timing:
+  mixed_precision   the same matrix with FP16 updates on the tensor cores and
+                    FP64 refinement: step time, refined residual, log-det
+                    error against the FP64 step
+  batched_sweep     256 matrices of a hyperparameter sweep in one persistent
+                    launch (mixed precision and FP64 arms)
+  serving           a Poisson stream (500 req/s) through the continuous-
+                    batching loop: solves/s, requests/s, p50/p99 (both arms)
+  large_band        the 200,000-row variable band + 100 arrow rows (FP64, T=16)
+                    and its tile-size sweep (T = 32 .. 512)
+  marginal_variances  diag(A^-1) of the headline matrix by selected inversion
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload large|sweep|serve]
+                       [--workload full|spatiotemporal|large|sweep|serve] [--no-nested]
 For N > 1 launch with torch.distributed.run; each rank factorizes its own
 replica (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -41,8 +45,9 @@ import subprocess
 import sys
 import time
 
-# The oracle's CPU baseline runs single-threaded: pin BLAS to one thread
-# before numpy loads (the GPU path does not use numpy's BLAS).
+# The oracle's CPU baseline runs one process per core, each single-threaded:
+# pin BLAS to one thread before numpy loads (the GPU path does not use numpy's
+# BLAS).  Spawned workers inherit this.
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -54,12 +59,28 @@ sys.path.insert(0, ROOT)
 from paper_2501_02483_b300 import inputs  # noqa: E402
 
 METRIC = "arrowhead Cholesky TFLOP/s, %peak; served solves/s, p50/p99 at set residual"
+ST_NAME = ("spatio-temporal Q_t (x) Q_s: AR(1) n_t=100 rho=0.9, (kappa^2 I + L)^2 on a 45x45 grid (kappa^2=1), "
+           "time-major, + 20 fixed-effect arrow rows, n=202520, nrhs 1")
+LARGE_NAME = "band200000_hw100-500_d0.2_arrow100_nrhs4 (variable band + arrow, n=200100)"
 
-# DRAM bytes per launch of the factorization kernel, from an ncu capture (see
-# profiles/); keyed by (kernel build tag, tile, block).  None when the kernel
-# changed after the capture.
-TRAFFIC = {("factor_f64_v9_fwd", "large", 16, 16): 1.415e9}  # profiles/factor_f64_b16_band50000.md, scaled by tiles
-KERNEL_TAG = "factor_f64_v9_fwd"
+# Source files whose contents decide the FP64 factorization kernel's memory
+# traffic; the DRAM bytes measured by an ncu capture stay valid only while
+# their digest is the one the capture was taken with.
+KERNEL_SOURCES = ("factor_f64.cuh", "device_common.cuh", "plan.h", "analyze.cpp")
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2501_02483_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (read + write) per launch of factor_f64_kernel, keyed by (kernel
+# digest, workload, tile, block): one capture of a smaller case of the same
+# structure, scaled to the full launch by the number of sub-tiles.
+TRAFFIC = {}
 
 
 def parse():
@@ -68,22 +89,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["full", "spatiotemporal", "large", "sweep", "serve"], default="full",
+                    help="full: the spatio-temporal headline with every nested measurement")
+    ap.add_argument("--no-nested", action="store_true", help="full: the headline step only")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="nd")
-    ap.add_argument("--sweep", default="32,64,128,256,512", help="tile sizes timed briefly; '' to skip")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-largest", action="store_true", help="large: skip the largest-configuration FP64 line")
-    ap.add_argument("--cpu-sample-rows", type=int, default=60_000)
-    ap.add_argument("--rows", type=int, default=200_000,
-                    help="body rows (profiling runs only; the benchmarked workload is 200,000)")
-    ap.add_argument("--workload", choices=["large", "spatiotemporal", "sweep", "serve"], default="large")
     ap.add_argument("--precision", choices=["f64", "bf16", "f16"], default="f64",
-                    help="large/spatiotemporal: update precision (bf16/f16 need tile 64; FP64 refinement)")
+                    help="spatiotemporal/large: update precision (bf16/f16 need tile 64; FP64 refinement)")
+    ap.add_argument("--nested-steps", type=int, default=5, help="timed steps of each nested measurement")
+    ap.add_argument("--sweep", default="32,64,128,256,512", help="large band: tile sizes timed briefly; '' to skip")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-workers", type=int, default=0, help="oracle processes (0 = every core of the host)")
+    ap.add_argument("--rows", type=int, default=200_000,
+                    help="large: body rows (profiling runs only; the benchmarked workload is 200,000)")
+    ap.add_argument("--time-steps", type=int, default=100,
+                    help="spatiotemporal: AR(1) time steps (profiling runs only; the benchmarked workload is 100)")
     ap.add_argument("--batch", type=int, default=256, help="sweep: matrices per batch")
-    ap.add_argument("--lp-tile", type=int, default=64, help="sweep/serve: tile of the mixed-precision arm")
+    ap.add_argument("--lp-tile", type=int, default=64, help="mixed-precision arms: tile")
     ap.add_argument("--lp-precision", choices=["bf16", "f16"], default="f16",
-                    help="sweep/serve: 16-bit type of the mixed-precision updates")
+                    help="mixed-precision arms: 16-bit type of the updates")
     ap.add_argument("--f64-tile", type=int, default=16, help="sweep/serve: tile of the FP64 arm")
     ap.add_argument("--requests", type=int, default=1500, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=500.0, help="serve: mean arrivals per second")
@@ -94,32 +119,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload(args, seed=0):
-    if args.workload == "spatiotemporal":
+def _order(st, name):
+    return {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[name]
+
+
+def _prec(st, name):
+    return {"f64": st.PREC_F64, "bf16": st.PREC_BF16, "f16": st.PREC_F16}[name]
+
+
+def spatiotemporal(time_steps=100, seed=0):
+    if time_steps == 100:
         return inputs.config_spatiotemporal(seed)
-    return inputs.config_large(seed, n_body=args.rows)
+    return inputs.kronecker_spatiotemporal(time_steps, 0.9, 45, 1.0, 20, 0.1, seed, nrhs=1)
 
 
-def workload_config(args, info=None):
-    if args.workload == "spatiotemporal":
-        cfg = {"workload": "spatio-temporal Q_t (x) Q_s: AR(1) n_t=100 rho=0.9, (kappa^2 I + L)^2 on a 45x45 grid "
-                           f"(kappa^2=1), time-major, + 20 fixed-effect arrow rows, nrhs 1 ({args.precision})",
-               "n": 202520, "n_arrow": 20, "nrhs": 1, "tile": args.tile, "ordering": args.ordering,
-               "l2": "inputs larger than L2 (factor tiles > 1 GB vs 126 MB L2); no flush"}
-    else:
-        cfg = {"workload": f"band{args.rows}_hw100-500_d0.2_arrow100_nrhs4 (large single matrix, {args.precision})",
-               "n": args.rows + 100, "n_arrow": 100, "nrhs": 4, "tile": args.tile, "ordering": args.ordering,
-               "l2": "inputs larger than L2 (values 0.26 GB, factor tiles > 0.7 GB vs 126 MB L2); no flush"}
-    cfg.update({
-           "step": ("factorize + logdet + solve (analysis once per pattern, timed separately); FP64: the "
-                    "forward sweep inside the factorization launch (stiles_factorize_solve), then the "
-                    "backward sweep"),
-           "flops": "tile-level task flops of Algorithm 1 at tile T (POTRF b(b+1)(2b+1)/6, SYRK kb(b+1), "
-                    "GEMM 2mnk, TRSM mb^2)"})
-    if info:
-        cfg.update({"block": info["block"], "nnzt": info["nnzt"], "ntasks": info["ntasks"],
-                    "flops_factor": info["flops_total"]})
-    return cfg
+FLOPS_RULE = ("tile-level task flops of Algorithm 1 at tile T (POTRF b(b+1)(2b+1)/6, SYRK kb(b+1), GEMM 2mnk, "
+              "TRSM mb^2)")
+STEP_RULE = ("factorize + logdet + solve (analysis once per pattern, timed separately); FP64: the forward sweep "
+             "inside the factorization launch (stiles_factorize_solve), then the backward sweep; mixed precision: "
+             "factorize, then the solve refined in FP64 to residual 1e-10")
 
 
 # ---------------------------------------------------------------------------
@@ -133,6 +151,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.result = None
 
     def __enter__(self):
         try:
@@ -167,58 +186,121 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle, as it stands, on a bounded sample
+# CPU baseline: the oracle, as it stands, on bounded samples, one process per core
 # ---------------------------------------------------------------------------
-def cpu_baseline(args, T):
+def _oracle_job(spec):
+    """One oracle factorize + logdet + solve of a bounded sample; returns
+    (seconds, tile flops).  Runs in a spawned worker (no CUDA)."""
     from oracle import analyze as oan
     from oracle import cholesky as och
     from oracle import tiles as otiles
 
-    rows = args.cpu_sample_rows
-    if args.workload == "spatiotemporal":
-        # 4 time steps of the same Kronecker structure (8,120 rows), tile 64
-        m = inputs.kronecker_spatiotemporal(4, 0.9, 45, 1.0, 20, 0.1, 0, nrhs=1)
-        T = 64
-        rows = m["n"]
+    kind, size, T, seed = spec
+    if kind == "spatiotemporal":
+        m = inputs.kronecker_spatiotemporal(size, 0.9, 45, 1.0, 20, 0.1, seed, nrhs=1)
     else:
-        m = inputs.config_large(0, n_body=rows, n_arrow=100, nrhs=4)
+        m = inputs.config_large(seed, n_body=size, n_arrow=100, nrhs=4)
     p = oan.analyze(m, T, oan.ORDER_NONE)
     fl = otiles.task_flops(m["n"], T, p["tcolptr"], p["trowidx"])["total"]
     t0 = time.perf_counter()
     L = och.factorize(m, p["perm"], T, p["tcolptr"], p["trowidx"])
     och.logdet(L, p["nt"])
     och.solve(L, p["perm"], T, p["tcolptr"], p["trowidx"], m["rhs"])
-    dt = time.perf_counter() - t0
-    what = (f"the same generator with {rows} body rows + 100-row arrow" if args.workload != "spatiotemporal"
-            else f"the same Kronecker structure with 4 time steps ({rows} rows)")
-    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{what}, T={T}, one factorize+logdet+solve ({dt:.1f} s, one thread: Python/numpy, BLAS "
-                      f"pinned to 1 thread)", "seconds": dt, "flops": fl}
+    return time.perf_counter() - t0, fl
+
+
+def _noop(_):
+    return os.getpid()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """``workers`` spawned processes (spawn: safe after CUDA is initialised),
+    each running whole oracle samples single-threaded.  The oracle has no
+    parallelism inside one factorization, so the host's cores work on
+    independent samples of the workload at once (throughput)."""
+
+    def __init__(self, workers):
+        import multiprocessing as mp
+
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+        self.pool.map(_noop, range(4 * workers))  # every worker started and numpy imported
+
+    def run(self, specs):
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_job, specs, chunksize=1)
+        return time.perf_counter() - t0, res
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _sample_spec(workload):
+    if workload in ("full", "spatiotemporal"):
+        return ("spatiotemporal", 8, 64), "the same Kronecker construction with 8 time steps (16,220 rows), T=64"
+    return ("large", 40_000, 16), "the same generator with 40,000 body rows + 100 arrow rows, T=16"
+
+
+def cpu_baseline(args):
+    """The oracle on the host: one sample on one core (threads_1), then one
+    sample per core on every core at once (value = total flops / wall time)."""
+    (kind, size, T), what = _sample_spec(args.workload)
+    s1, fl1 = _oracle_job((kind, size, T, 0))
+    cores = args.cpu_workers or host_cores()
+    pool = OraclePool(cores)
+    wall, res = pool.run([(kind, size, T, i) for i in range(cores)])
+    pool.close()
+    fl = sum(r[1] for r in res)
+    return {"value": fl / wall / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{what}, ordering none, FP64 factorize+logdet+solve: {cores} independent samples (seeds "
+                      f"0..{cores - 1}) in {cores} single-threaded Python/numpy processes ({wall:.1f} s wall); "
+                      f"one process alone {s1:.1f} s",
+            "threads_1": {"value": fl1 / s1 / 1e12, "seconds": round(s1, 2), "flops": fl1},
+            "host_cores": host_cores()}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is one sample per host core,
+    all cores at once."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    T = args.tile
-    vals = []
-    base = None
+    (kind, _, T), what = _sample_spec(args.workload)
+    size = 4 if kind == "spatiotemporal" else 20_000
+    what = what.replace("8 time steps (16,220 rows)", "4 time steps (8,120 rows)").replace("40,000", "20,000")
+    cores = args.cpu_workers or host_cores()
+    pool = OraclePool(cores)
+    walls, fl = [], 0
     for i in range(args.warmup + args.steps):
-        base = cpu_baseline(args, T)
+        wall, res = pool.run([(kind, size, T, c) for c in range(cores)])
         if i >= args.warmup:
-            vals.append(base["seconds"])
-    v = base["flops"] / statistics.mean(vals) / 1e12
+            walls.append(wall)
+            fl = sum(r[1] for r in res)
+    pool.close()
+    v = fl / statistics.mean(walls) / 1e12
+    sample = (f"{what}, FP64 factorize+logdet+solve: one sample per core on {cores} single-threaded Python/numpy "
+              "processes per step")
+    cfg = {"workload": ST_NAME if kind == "spatiotemporal" else LARGE_NAME, "tile": T, "ordering": "none",
+           "step": STEP_RULE, "flops": FLOPS_RULE, "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(vals),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args), sample=base["sample"]),
-            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": base["sample"]},
+            "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
-# our arm
+# our arm: one matrix
 # ---------------------------------------------------------------------------
 def _selinv_flops(plan):
     """Useful flops of the selected inverse at the plan's sub-tile size B: per
@@ -242,233 +324,6 @@ def _selinv_flops(plan):
     return total
 
 
-def run_ours(args):
-    import torch
-
-    from paper_2501_02483_b300 import build
-    from paper_2501_02483_b300 import stiles as st
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    build.build_library()
-    order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[args.ordering]
-
-    m = workload(args, seed=rank)
-    prec = {"f64": st.PREC_F64, "bf16": st.PREC_BF16, "f16": st.PREC_F16}[args.precision]
-    t0 = time.perf_counter()
-    plan = st.Plan.from_matrix(m, tile=args.tile, block=args.block, ordering=order, precision=prec)
-    analyze_s = time.perf_counter() - t0
-    info = plan.info()
-    flops = info["flops_total"]
-    nrhs = m["rhs"].shape[1]
-    dev = torch.device("cuda", local)
-    vals_d = torch.from_numpy(m["values"]).to(dev)
-    b_d = torch.from_numpy(np.asfortranarray(m["rhs"])).to(dev)
-    # pinned host buffers for the end-to-end measurement (b, x: n x nrhs column-major views)
-    vals_host = torch.from_numpy(m["values"]).pin_memory().numpy()
-    bt = torch.from_numpy(np.ascontiguousarray(m["rhs"].T)).pin_memory()
-    xt = torch.empty_like(bt).pin_memory()
-    b_host, x_host = bt.numpy().T, xt.numpy().T
-    peak = st.probe_fp64_peak()
-
-    f = st.Factor(plan)
-    stream = torch.cuda.current_stream(dev)
-    # FP64: the forward sweep runs inside the factorization launch
-    # (stiles_factorize_solve); mixed precision: factorize, then the refined solve
-    fused = prec == st.PREC_F64 and nrhs <= min(info["block"], 16)
-    x_d = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev).t()  # n x nrhs, column-major
-
-    def step_device():
-        if fused:
-            x = f.factorize_solve(vals_d, b_d, x=x_d, stream=stream)
-            ld = f.logdet()
-            return ld, x
-        f.factorize(vals_d, stream=stream)
-        ld = f.logdet()
-        x = f.solve(b_d, stream=stream)
-        return ld, x
-
-    for _ in range(args.warmup):
-        step_device()
-    torch.cuda.synchronize()
-    kernel_ms = []
-    n0 = st.kernel_launches()
-    with ClockSampler(local) as clk:
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            ld, x = step_device()
-            kernel_ms.append(f.timing()[1])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-    launches = st.kernel_launches() - n0
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * flops / (ms * 1e-3) / 1e12
-
-    # end to end through host buffers (pinned): H2D values + RHS, D2H x + logdet
-    vals_pin = torch.from_numpy(vals_host)
-    vals_stage = torch.empty_like(vals_d)
-    b_stage = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev)
-
-    def step_e2e():
-        if fused:  # explicit copies: the folded call takes device arrays
-            vals_stage.copy_(vals_pin, non_blocking=True)
-            b_stage.copy_(bt, non_blocking=True)
-            f.factorize_solve(vals_stage, b_stage.t(), x=x_d, stream=stream)
-            f.logdet()
-            xt.copy_(x_d.t())
-        else:
-            f.factorize(vals_host)
-            f.logdet()
-            f.solve(b_host, x=x_host)
-
-    step_e2e()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(m["values"].nbytes + b_host.nbytes),
-           "d2h_bytes_per_step": int(x_host.nbytes + 8), "ms_per_step": e2e_ms}
-
-    # correctness of what was timed
-    _, relres = f.solve(b_d, stream=stream, relres=True)
-
-    # marginal variances diag(A^{-1}) through the selected inverse (FP64 factors):
-    # the first call builds and uploads its task graph; a new factorization
-    # invalidates Sigma, so the timed call recomputes all of it
-    sinv = None
-    if prec == st.PREC_F64 and rank == 0:
-        f.marginal_variances(stream=stream)
-        f.factorize(vals_d, stream=stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        var = f.marginal_variances(stream=stream)
-        ms_sinv = (time.perf_counter() - t0) * 1e3
-        sfl = _selinv_flops(plan)
-        sinv = {"ms": round(ms_sinv, 2), "flops": sfl, "tflops": round(sfl / ms_sinv / 1e9, 4),
-                "frac_of_fp64_peak": round(sfl / ms_sinv / 1e9 / peak, 4),
-                "min_variance": float(var.min()), "max_variance": float(var.max()),
-                "flops_rule": "2 B^3 per operand pair, B^3 per L_jk L_kk^{-1} and per L_kk^{-T} L_kk^{-1}"}
-
-    # tile-size sweep (the workload names 128/256/512; 32/64 added)
-    sweep = {}
-    if rank == 0 and args.sweep:
-        for T in [int(t) for t in args.sweep.split(",") if t]:
-            if prec != st.PREC_F64 and T % 64:
-                continue
-            pl = st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec)
-            ff = st.Factor(pl)
-            ff.factorize(vals_d)
-            ks = []
-            for _ in range(2):
-                ff.factorize(vals_d)
-                ks.append(ff.timing()[1])
-            fl = pl.info()["flops_total"]
-            sweep[str(T)] = {"kernel_ms": round(min(ks), 3), "tflops": round(fl / min(ks) / 1e9, 4),
-                             "flops": fl, "block": pl.info()["block"]}
-            ff.close()
-            pl.close()
-
-    kms = statistics.mean(kernel_ms)
-    achieved = flops / (kms * 1e-3) / 1e12
-    if prec == st.PREC_F64:
-        traffic = TRAFFIC.get((KERNEL_TAG, args.workload, args.tile, info["block"]))
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel_ms": kms,
-                "kernel": f"factor_f64_kernel<{info['block']}>" + (" (forward sweep folded in; achieved counts the "
-                                                                    "factorization's flops only)" if fused else ""),
-                "peak_source": "FP64 DFMA probe of libstiles.so measured in this run (MEASURED_PEAKS.json "
-                               "has no FP64 entry)"}
-    else:
-        tpeak, src = _tensor_peak()
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s", "frac": achieved / tpeak,
-                "traffic": None, "kernel": "factor_lp_kernel", "kernel_ms": kms, "peak_source": src}
-    line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": dict(workload_config(args, info), analyze_s=round(analyze_s, 3), logdet=ld,
-                       relres=relres, tile_sweep=sweep, percent_of_fp64_peak=round(100 * value / peak, 2),
-                       refine_iters=f.refine_iters(), marginal_variances=sinv),
-        "roofline": roof,
-        "e2e": e2e, "gpu_launches": launches, "clocks": clk.result,
-    }
-    f.close()
-    plan.close()
-    if rank == 0 and args.workload == "large" and not args.no_largest:
-        line["config"]["largest_config_fp64"] = _largest_config_fp64(st, torch, dev, stream, peak)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args, args.tile).items() if k not in ("seconds", "flops")}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-
-
-# ---------------------------------------------------------------------------
-# batched sweep and serving workloads
-# ---------------------------------------------------------------------------
-def _largest_config_fp64(st, torch, dev, stream, peak):
-    """FP64 factorization of the largest configuration (the spatio-temporal
-    matrix, n = 202,520, tile 16, nested dissection): kernel time of 2 timed
-    factorizations after one warm-up, as a fraction of the measured FP64 peak."""
-    m = inputs.config_spatiotemporal(0)
-    pl = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_ND)
-    ff = st.Factor(pl)
-    vd = torch.from_numpy(m["values"]).to(dev)
-    ff.factorize(vd, stream=stream)
-    ks = []
-    for _ in range(2):
-        ff.factorize(vd, stream=stream)
-        ks.append(ff.timing()[1])
-    fl = pl.info()["flops_total"]
-    ms = statistics.mean(ks)
-    out = {"workload": "spatio-temporal Q_t (x) Q_s + 20 arrow rows, n = 202,520, T = 16, ND",
-           "factor_kernel_ms": round(ms, 2), "flops": fl, "tflops": round(fl / ms / 1e9, 4),
-           "frac_of_fp64_peak": round(fl / ms / 1e9 / peak, 4)}
-    ff.close()
-    pl.close()
-    return out
-
-
-def _tensor_peak():
-    """The sustained bf16 tensor peak of MEASURED_PEAKS.json (f16 runs at the same rate)."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            v = json.load(fh).get("bf16_tflops_sustained")
-        if v:
-            return float(v), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; f16 has the same nominal rate)"
-    except OSError:
-        pass
-    return 1400.0, "fallback sustained bf16 (of fallback)"
-
-
 def _setup_rank():
     import torch
 
@@ -488,16 +343,277 @@ def _setup_rank():
 
 
 def _max_over_ranks(torch, dist, dev, v):
-    if not dist:
-        return v
-    t = torch.tensor([v], device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2501_02483_b300 import replicas
+
+    return replicas.max_over_ranks(dist, v, dev)
 
 
-def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
+def single_matrix(st, torch, dev, m, *, tile, order, prec, steps, warmup, block=0, e2e=True, dist=None,
+                  keep=False):
+    """W + K steps of factorize + logdet + solve of one matrix through the C
+    ABI (device-resident inputs), then K end-to-end steps through pinned host
+    buffers.  Returns the measurements (and the plan/factor when ``keep``)."""
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    plan = st.Plan.from_matrix(m, tile=tile, block=block, ordering=order, precision=prec)
+    analyze_s = time.perf_counter() - t0
+    info = plan.info()
+    flops = info["flops_total"]
+    nrhs = m["rhs"].shape[1]
+    vals_d = torch.from_numpy(m["values"]).to(dev)
+    b_d = torch.from_numpy(np.asfortranarray(m["rhs"])).to(dev)
+    f = st.Factor(plan)
+    # FP64: the forward sweep runs inside the factorization launch
+    # (stiles_factorize_solve); mixed precision: factorize, then the refined solve
+    fused = prec == st.PREC_F64 and nrhs <= min(info["block"], 16)
+    x_d = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev).t()  # n x nrhs, column-major
+
+    def step_device():
+        if fused:
+            x = f.factorize_solve(vals_d, b_d, x=x_d, stream=stream)
+            return f.logdet(), x
+        f.factorize(vals_d, stream=stream)
+        ld = f.logdet()
+        return ld, f.solve(b_d, x=x_d, stream=stream)
+
+    t1 = time.perf_counter()
+    step_device()  # first call: uploads the plan's device arrays (and builds the folded graph)
+    torch.cuda.synchronize()
+    first_call_s = time.perf_counter() - t1
+    for _ in range(max(warmup - 1, 0)):
+        step_device()
+    torch.cuda.synchronize()
+    kernel_ms = []
+    n0 = st.kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ld, x = step_device()
+            kernel_ms.append(f.timing()[1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = st.kernel_launches() - n0
+    ms = _max_over_ranks(torch, dist, dev, e0.elapsed_time(e1) / steps)
+    out = {"ms_per_step": ms, "flops": flops, "tflops": flops / (ms * 1e-3) / 1e12,
+           "kernel_ms": statistics.mean(kernel_ms), "gpu_launches": launches, "clocks": clk.result,
+           "analyze_s": round(analyze_s, 3), "first_call_s": round(first_call_s, 3), "logdet": ld,
+           "refine_iters": f.refine_iters(), "tile": tile, "block": info["block"], "nnzt": info["nnzt"],
+           "ntasks": info["ntasks"], "fused_forward_sweep": fused}
+    out["kernel_tflops"] = flops / (out["kernel_ms"] * 1e-3) / 1e12
+
+    if e2e:
+        # end to end through pinned host buffers: H2D values + RHS, D2H x + logdet
+        vals_pin = torch.from_numpy(m["values"]).pin_memory()
+        bt = torch.from_numpy(np.ascontiguousarray(m["rhs"].T)).pin_memory()
+        xt = torch.empty_like(bt).pin_memory()
+        vals_stage = torch.empty_like(vals_d)
+        b_stage = torch.empty((nrhs, m["n"]), dtype=torch.float64, device=dev)
+
+        def step_e2e():
+            vals_stage.copy_(vals_pin, non_blocking=True)
+            b_stage.copy_(bt, non_blocking=True)
+            if fused:
+                f.factorize_solve(vals_stage, b_stage.t(), x=x_d, stream=stream)
+                f.logdet()
+            else:
+                f.factorize(vals_stage, stream=stream)
+                f.logdet()
+                f.solve(b_stage.t(), x=x_d, stream=stream)
+            xt.copy_(x_d.t())  # synchronous D2H of the solution
+
+        step_e2e()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        e2e_ms = _max_over_ranks(torch, dist, dev, (time.perf_counter() - t0) * 1e3 / steps)
+        out["e2e"] = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(m["values"].nbytes + bt.numel() * 8),
+                      "d2h_bytes_per_step": int(xt.numel() * 8 + 8)}
+
+    # correctness of what was timed
+    _, relres = f.solve(b_d, stream=stream, relres=True)
+    out["relres"] = relres
+    if keep:
+        out["_plan"], out["_factor"], out["_vals"] = plan, f, vals_d
+    else:
+        f.close()
+        plan.close()
+    return out
+
+
+def _public(d):
+    return {k: v for k, v in d.items() if not k.startswith("_")}
+
+
+def _fp64_roofline(st, res, peak, workload, fused):
+    achieved = res["kernel_tflops"]
+    key = (kernel_digest(), workload, res["tile"], res["block"])
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get(key), "kernel_ms": res["kernel_ms"],
+            "kernel": f"factor_f64_kernel<{res['block']}>" + (" (forward sweep folded in; achieved counts the "
+                                                              "factorization's flops only)" if fused else ""),
+            "kernel_digest": key[0],
+            "peak_source": "FP64 DFMA probe of libstiles.so measured in this run (MEASURED_PEAKS.json has no "
+                           "FP64 entry)"}
+
+
+def _tensor_peak():
+    """The sustained bf16 tensor peak of MEASURED_PEAKS.json (f16 runs at the same rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = json.load(fh).get("bf16_tflops_sustained")
+        if v:
+            return float(v), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; f16 has the same nominal rate)"
+    except OSError:
+        pass
+    return 1400.0, "fallback sustained bf16 (of fallback)"
+
+
+def marginal_variances(st, torch, dev, kept, peak):
+    """diag(A^{-1}) by selected inversion on a kept FP64 factor: the first call
+    builds and uploads its task graph; a new factorization invalidates Sigma,
+    so the timed call recomputes all of it."""
+    stream = torch.cuda.current_stream(dev)
+    plan, f, vals = kept["_plan"], kept["_factor"], kept["_vals"]
+    t0 = time.perf_counter()
+    f.marginal_variances(stream=stream)
+    first = time.perf_counter() - t0
+    f.factorize(vals, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    var = f.marginal_variances(stream=stream)
+    ms = (time.perf_counter() - t0) * 1e3
+    sfl = _selinv_flops(plan)
+    return {"ms": round(ms, 2), "first_call_s": round(first, 2), "flops": sfl, "tflops": round(sfl / ms / 1e9, 4),
+            "frac_of_fp64_peak": round(sfl / ms / 1e9 / peak, 4), "min_variance": float(var.min()),
+            "max_variance": float(var.max()),
+            "flops_rule": "2 B^3 per operand pair, B^3 per L_jk L_kk^{-1} and per L_kk^{-T} L_kk^{-1}"}
+
+
+def tile_sweep(st, torch, dev, m, tiles, order, prec):
+    """Kernel time of two factorizations after one warm-up per tile size."""
+    vals_d = torch.from_numpy(m["values"]).to(dev)
+    out = {}
+    for T in tiles:
+        if prec != st.PREC_F64 and T % 64:
+            continue
+        pl = st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec)
+        ff = st.Factor(pl)
+        ff.factorize(vals_d)
+        ks = []
+        for _ in range(2):
+            ff.factorize(vals_d)
+            ks.append(ff.timing()[1])
+        fl = pl.info()["flops_total"]
+        out[str(T)] = {"kernel_ms": round(min(ks), 3), "tflops": round(fl / min(ks) / 1e9, 4), "flops": fl,
+                       "block": pl.info()["block"]}
+        ff.close()
+        pl.close()
+    return out
+
+
+def run_single(args):
+    """One matrix: the headline (spatio-temporal, FP64) with every nested
+    measurement (--workload full), or one workload alone."""
+    torch, world, rank, local, dist = _setup_rank()
+    from paper_2501_02483_b300 import stiles as st
+
+    dev = torch.device("cuda", local)
+    order = _order(st, args.ordering)
+    prec = _prec(st, args.precision)
+    if args.workload == "large":
+        m, name = inputs.config_large(rank, n_body=args.rows), LARGE_NAME
+        if args.rows != 200_000:
+            name = name.replace("band200000", f"band{args.rows}")
+    else:
+        m, name = spatiotemporal(args.time_steps, seed=rank), ST_NAME
+        if args.time_steps != 100:
+            name = name.replace("n_t=100", f"n_t={args.time_steps}")
+    wl = "spatiotemporal" if args.workload in ("full", "spatiotemporal") else "large"
+    peak = st.probe_fp64_peak()
+    nested = args.workload == "full" and not args.no_nested and world == 1
+    res = single_matrix(st, torch, dev, m, tile=args.tile, block=args.block, order=order, prec=prec,
+                        steps=args.steps, warmup=args.warmup, dist=dist,
+                        keep=nested and prec == st.PREC_F64)
+    value = world * res["flops"] / (res["ms_per_step"] * 1e-3) / 1e12
+    e2e = {"value": world * res["flops"] / (res["e2e"]["ms_per_step"] * 1e-3) / 1e12, "unit": "TFLOP/s",
+           **res["e2e"]}
+    if prec == st.PREC_F64:
+        roof = _fp64_roofline(st, res, peak, wl, res["fused_forward_sweep"])
+    else:
+        tpeak, src = _tensor_peak()
+        roof = {"bound": "tensor", "achieved": res["kernel_tflops"], "peak": tpeak, "unit": "TFLOP/s",
+                "frac": res["kernel_tflops"] / tpeak, "traffic": None, "kernel": "factor_lp_kernel",
+                "kernel_ms": res["kernel_ms"], "peak_source": src}
+    cfg = {"workload": f"{name} ({args.precision})", "n": m["n"], "n_arrow": m["n_arrow"],
+           "nrhs": int(m["rhs"].shape[1]), "tile": args.tile, "ordering": args.ordering,
+           "l2": "inputs larger than L2 (factor tiles > 1 GB vs 126 MB L2); no flush", "step": STEP_RULE,
+           "flops": FLOPS_RULE, "block": res["block"], "nnzt": res["nnzt"], "ntasks": res["ntasks"],
+           "flops_factor": res["flops"], "analyze_s": res["analyze_s"], "first_call_s": res["first_call_s"],
+           "logdet": res["logdet"], "relres": res["relres"], "refine_iters": res["refine_iters"],
+           "percent_of_fp64_peak": round(100 * value / world / peak, 2), "fp64_peak_tflops": peak}
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic", "config": cfg, "roofline": roof,
+            "e2e": e2e, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"]}
+
+    if nested:
+        K, W = args.nested_steps, 2
+        if prec == st.PREC_F64:
+            cfg["marginal_variances"] = marginal_variances(st, torch, dev, res, peak)
+            res["_factor"].close()
+            res["_plan"].close()
+        # the same matrix with 16-bit updates on the tensor cores + FP64 refinement
+        lp = single_matrix(st, torch, dev, m, tile=args.lp_tile, order=order, prec=_prec(st, args.lp_precision),
+                           steps=K, warmup=W, e2e=False)
+        tpeak, src = _tensor_peak()
+        lp.update({"precision": args.lp_precision, "steps": K, "warmup": W,
+                   "logdet_rel_err_vs_fp64": abs(lp["logdet"] - res["logdet"]) / abs(res["logdet"]),
+                   "speedup_vs_fp64_step": res["ms_per_step"] / lp["ms_per_step"],
+                   "tensor_frac": lp["kernel_tflops"] / tpeak, "tensor_peak_source": src})
+        cfg["mixed_precision"] = lp
+        cfg["batched_sweep"] = sweep_measure(args, st, torch, dev, None, steps=K, warmup=W)
+        cfg["serving"] = serve_measure(args, st, torch, dev, seed=0)
+        # the large variable band: FP64 step at T = 16 and the tile-size sweep
+        ml = inputs.config_large(0)
+        lg = single_matrix(st, torch, dev, ml, tile=16, order=order, prec=st.PREC_F64, steps=K, warmup=W,
+                           e2e=False)
+        lg.update({"workload": LARGE_NAME, "steps": K, "warmup": W,
+                   "kernel_frac_of_fp64_peak": lg["kernel_tflops"] / peak,
+                   "tile_sweep": tile_sweep(st, torch, dev, ml, [int(t) for t in args.sweep.split(",") if t],
+                                            order, st.PREC_F64) if args.sweep else {}})
+        cfg["large_band"] = lg
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _jsonable(o):
+    if isinstance(o, np.generic):
+        return o.item()
+    raise TypeError(type(o))
+
+
+# ---------------------------------------------------------------------------
+# batched sweep and serving workloads
+# ---------------------------------------------------------------------------
+def _sweep_arm(st, torch, mats, prec, T, dev, dist, steps, warmup):
     """One precision arm of the batched sweep: analysis, then W + K steps of
     batched factorize + logdets + batched solve."""
+    stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
     plans = [st.Plan.from_matrix(m, tile=T, ordering=st.ORDER_NONE, precision=prec) for m in mats]
     analyze_s = time.perf_counter() - t0
@@ -514,7 +630,7 @@ def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
         xs, rel, its, status = batch.solve(rhs, stream=stream, raise_on_error=False)
         return statuses, lds, rel, its, batch.timing()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(vals_d, rhs_d)
     torch.cuda.synchronize()
     n0 = st.kernel_launches()
@@ -525,7 +641,7 @@ def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             statuses, lds, rel, its, km = step(vals_d, rhs_d)
             kms.append(km)
         e1.record(stream)
@@ -533,7 +649,7 @@ def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
         if dist:
             dist.barrier()
     launches = st.kernel_launches() - n0
-    ms = _max_over_ranks(torch, dist, dev, e0.elapsed_time(e1) / args.steps)
+    ms = _max_over_ranks(torch, dist, dev, e0.elapsed_time(e1) / steps)
     ok = int(np.sum((statuses == 0) & (rel <= 1e-10)))
     # end to end from pinned host buffers: H2D values + right-hand sides, D2H solutions + logdets
     vals_h = [torch.from_numpy(m["values"]).pin_memory().numpy() for m in mats]
@@ -541,10 +657,10 @@ def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
     step(vals_h, rhs_h)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step(vals_h, rhs_h)
     torch.cuda.synchronize()
-    e2e_ms = _max_over_ranks(torch, dist, dev, (time.perf_counter() - t0) * 1e3 / args.steps)
+    e2e_ms = _max_over_ranks(torch, dist, dev, (time.perf_counter() - t0) * 1e3 / steps)
     out = {"tile": T, "block": infos[0]["block"], "ms_per_step": ms, "tflops": flops / (ms * 1e-3) / 1e12,
            "matrices_per_s": len(mats) / (ms * 1e-3), "solves_per_s": ok * (nsolve / len(mats)) / (ms * 1e-3),
            "solved_at_1e-10": ok, "max_relres": float(np.max(rel)), "max_refine_iters": int(np.max(its)),
@@ -558,32 +674,41 @@ def _sweep_arm(args, st, torch, mats, prec, T, dev, stream, dist):
     return out
 
 
+def sweep_measure(args, st, torch, dev, dist, steps, warmup, seed=0):
+    """Both arms of the batched sweep on the same matrices."""
+    mats = inputs.batch_sweep(args.batch, seed=seed)
+    prec = _prec(st, args.lp_precision)
+    lp = _sweep_arm(st, torch, mats, prec, args.lp_tile, dev, dist, steps, warmup)
+    f64 = _sweep_arm(st, torch, mats, st.PREC_F64, args.f64_tile, dev, dist, steps, warmup)
+    ld_err = float(np.max(np.abs(lp["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
+    for a in (lp, f64):
+        a.pop("logdets")
+    peak, peak_src = _tensor_peak()
+    lp["tensor_frac"] = lp["flops"] / (lp["kernel_ms"] * 1e-3) / 1e12 / peak
+    return {"workload": f"batched sweep: {args.batch} matrices, n log-uniform [5000, 50000], hw {{64,128,256}}, "
+                        "arrow 0..50, theta ~ U(0.5, 2), 1 RHS each; refined to 1e-10",
+            "step": "batched factorize (one persistent launch) + all logdets + batched solve with FP64 "
+                    "refinement (analysis once per pattern, timed separately)",
+            "steps": steps, "warmup": warmup, "precision": args.lp_precision,
+            "mixed_precision": lp, "fp64": f64, "logdet_rel_diff_lp_vs_fp64": ld_err,
+            "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30),
+            "tensor_peak_source": peak_src}
+
+
 def run_sweep(args):
     torch, world, rank, local, dist = _setup_rank()
     from paper_2501_02483_b300 import stiles as st
 
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    mats = inputs.batch_sweep(args.batch, seed=rank)
-    prec = st.PREC_BF16 if args.lp_precision == "bf16" else st.PREC_F16
-    lp = _sweep_arm(args, st, torch, mats, prec, args.lp_tile, dev, stream, dist)
-    f64 = _sweep_arm(args, st, torch, mats, st.PREC_F64, args.f64_tile, dev, stream, dist)
-    ld_err = float(np.max(np.abs(lp["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
-    for a in (lp, f64):
-        a.pop("logdets")
+    res = sweep_measure(args, st, torch, dev, dist, args.steps, args.warmup, seed=rank)
+    lp = res["mixed_precision"]
     peak, peak_src = _tensor_peak()
     achieved = lp["flops"] / (lp["kernel_ms"] * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": world * lp["tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": lp["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic",
-        "config": {"workload": f"batched sweep: {args.batch} matrices, n log-uniform [5000, 50000], hw {{64,128,256}}, "
-                               "arrow 0..50, theta ~ U(0.5, 2), 1 RHS each; refined to 1e-10",
-                   "step": "batched factorize (one persistent launch) + all logdets + batched solve with FP64 "
-                           "refinement (analysis once per pattern, timed separately)",
-                   "l2": "inputs larger than L2 (factor tiles of the batch > 1 GB); no flush",
-                   "mixed_precision": lp, "fp64": f64, "logdet_rel_diff_lp_vs_fp64": ld_err,
-                   "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
+        "config": dict(res, l2="inputs larger than L2 (factor tiles of the batch > 1 GB); no flush"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "factor_lp_kernel (batched)",
                      "kernel_ms": lp["kernel_ms"], "peak_source": peak_src},
@@ -592,32 +717,10 @@ def run_sweep(args):
                 "ms_per_step": lp["e2e_ms"]},
         "gpu_launches": lp["gpu_launches"], "clocks": lp["clocks"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = sweep_cpu_baseline(args)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_jsonable), flush=True)
     if dist:
         dist.destroy_process_group()
-
-
-def sweep_cpu_baseline(args, count=4):
-    """The oracle (FP64) on the first ``count`` matrices of the sweep."""
-    from oracle import analyze as oan
-    from oracle import cholesky as och
-    from oracle import tiles as otiles
-
-    mats = inputs.batch_sweep(args.batch, seed=0)[:count]
-    fl, t0 = 0, time.perf_counter()
-    for m in mats:
-        p = oan.analyze(m, args.lp_tile, oan.ORDER_NONE)
-        fl += otiles.task_flops(m["n"], args.lp_tile, p["tcolptr"], p["trowidx"])["total"]
-        L = och.factorize(m, p["perm"], args.lp_tile, p["tcolptr"], p["trowidx"])
-        och.logdet(L, p["nt"])
-        och.solve(L, p["perm"], args.lp_tile, p["tcolptr"], p["trowidx"], m["rhs"])
-    dt = time.perf_counter() - t0
-    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"the first {count} matrices of the sweep, T={args.lp_tile}, FP64 factorize+logdet+solve "
-                      f"({dt:.1f} s, one thread)", "seconds": dt, "flops": fl}
 
 
 def _pin_requests(torch, reqs):
@@ -637,7 +740,7 @@ def _pin_requests(torch, reqs):
 def _serve_arm(args, st, sv, torch, work, prec, T, stream):
     reqs, arrivals = work
     # warm-up on a throw-away server: a few requests of another stream load the kernels
-    order = {"none": st.ORDER_NONE, "rcm": st.ORDER_RCM, "auto": st.ORDER_AUTO, "nd": st.ORDER_ND}[args.serve_ordering]
+    order = _order(st, args.serve_ordering)
     warm = sv.Server(precision=prec, tile=T, ordering=order, max_batch=args.max_batch, hbm_budget=150e9,
                      gpu_workers=args.gpu_workers)
     wr, wa = inputs.serving_workload(12, rate=args.rate, seed=99, n_hi=20_000, pool=4)
@@ -665,37 +768,42 @@ def _serve_arm(args, st, sv, torch, work, prec, T, stream):
     return out
 
 
+def serve_measure(args, st, torch, dev, seed=0):
+    from paper_2501_02483_b300 import serve as sv
+
+    stream = torch.cuda.current_stream(dev)
+    work = inputs.serving_workload(args.requests, rate=args.rate, seed=seed, variants=2)
+    _pin_requests(torch, work[0])
+    lp = _serve_arm(args, st, sv, torch, work, _prec(st, args.lp_precision), args.lp_tile, stream)
+    f64 = _serve_arm(args, st, sv, torch, work, st.PREC_F64, args.f64_tile, stream)
+    return {"workload": f"serving: Poisson {args.rate:g} req/s, {args.requests} requests, n log-uniform "
+                        "[1000, 200000], hw 32..512, arrow 0..100, nrhs 1..16, 30% re-solves, HBM budget 150 GB; "
+                        "48 patterns x 2 value scales (theta in {0.875, 1.625}); client buffers in pinned host "
+                        "memory; ordering " + args.serve_ordering,
+            "step": "the whole request stream through the continuous-batching loop (arrivals in real time)",
+            "precision": args.lp_precision, "mixed_precision": lp, "fp64": f64,
+            "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)}
+
+
 def run_serve(args):
     torch, world, rank, local, dist = _setup_rank()
-    from paper_2501_02483_b300 import serve as sv
     from paper_2501_02483_b300 import stiles as st
 
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    work = inputs.serving_workload(args.requests, rate=args.rate, seed=rank, variants=2)
-    _pin_requests(torch, work[0])
-    lp_prec = st.PREC_BF16 if args.lp_precision == "bf16" else st.PREC_F16
-    lp = _serve_arm(args, st, sv, torch, work, lp_prec, args.lp_tile, stream)
-    f64 = _serve_arm(args, st, sv, torch, work, st.PREC_F64, args.f64_tile, stream)
-    value = _max_over_ranks(torch, dist, dev, -lp["solves_per_s"])
+    res = serve_measure(args, st, torch, dev, seed=rank)
+    lp = res["mixed_precision"]
+    value = -_max_over_ranks(torch, dist, dev, -lp["solves_per_s"])
     line = {
-        "metric": METRIC, "value": -value * world, "unit": "solves/s", "n_gpus": world, "steps": 1,
+        "metric": METRIC, "value": value * world, "unit": "solves/s", "n_gpus": world, "steps": 1,
         "warmup": 1, "ms_per_step": 1e3 * lp["wall_s"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic",
-        "config": {"workload": f"serving: Poisson {args.rate:g} req/s, {args.requests} requests, n log-uniform "
-                               "[1000, 200000], hw 32..512, arrow 0..100, nrhs 1..16, 30% re-solves, "
-                               "HBM budget 150 GB; 48 patterns x 2 value scales (theta in {0.875, 1.625}); client "
-                               "buffers in pinned host memory; ordering " + args.serve_ordering,
-                   "step": "the whole request stream through the continuous-batching loop (arrivals in real time)",
-                   "mixed_precision": lp, "fp64": f64,
-                   "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)},
-        "e2e": {"value": -value * world, "unit": "solves/s", "h2d_bytes_per_step": None,
+        "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic", "config": res,
+        "e2e": {"value": value * world, "unit": "solves/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None,
                 "note": "requests enter as host arrays; every value and right-hand side crosses H2D"},
         "gpu_launches": lp["gpu_launches"], "clocks": lp["clocks"],
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_jsonable), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -709,7 +817,7 @@ def main():
     elif args.workload == "serve":
         run_serve(args)
     else:
-        run_ours(args)
+        run_single(args)
 
 
 if __name__ == "__main__":

@@ -218,8 +218,11 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
  * set when the term is in W (a diagonal task's terms), else in X);
  * 6 = X products, 1 int32 each (sub-tile of U and X).  which = 7: the tasks of the
  * factorization with the forward sweep folded in (stiles_factorize_solve; 16 int32 each as for
- * which = 0; a forward block k is an OFF task with output nsub + k).  *ntasks receives the
- * number of entries.  out may be NULL to query ntasks. */
+ * which = 0; a forward block k is an OFF task with output nsub + k).  which = 8 / 9: the
+ * forward / backward sweep's operand pairs, 2 int32 each (L sub-tile, block index), indexed by
+ * the solve tasks' pair ranges; which = 10 / 11: their partial lists, 1 int32 each (scratch
+ * block), indexed by the partial ranges.  *ntasks receives the number of entries.  out may be
+ * NULL to query ntasks. */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */
@@ -239,7 +242,10 @@ int64_t stiles_kernel_launches(void);
  * Scratch is one static device array inside the library holding ceil(n/T) <= 65,536 partial
  * sums (512 KB per device, held until the library is unloaded); larger problems return
  * STILES_ERR_INVALID before any launch.  The first call on each device looks up that array's
- * device address with the device current, so make it before any stream capture.  Every call
+ * device address with the device current, so make it before any stream capture.  That address
+ * is kept for the life of the process: a cudaDeviceReset on the device after the first call is
+ * not supported (the array would be reloaded elsewhere and the kept address would be stale).
+ * Every call
  * shares the array: calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialized by the caller; each call rewrites all the entries it reads.  Errors:
  * STILES_ERR_INVALID (null pointer, n < 1, tile < 1, too many tile columns), STILES_ERR_CUDA. */

@@ -317,12 +317,38 @@ inline void clear_second(SolveTask&) {}
 // min_own: a primary whose list is split into leaves by the chunk rule keeps at
 // least its newest min_own terms.  Used for the sweeps: a leaf holding one of a
 // chain block's newest inputs is finished one step before its owner at best, so
-// the chain would cross SMs twice per block (leaf, then owner).
+// the chain would cross SMs twice per block (leaf, then owner).  With min_own > 0
+// every list is first stably sorted by producer position, so the kept tail holds
+// the newest terms whatever the order the list was built in (under nested
+// dissection a block's index order is not its producers' order).
 template <class Task>
 void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32_t leaf_type, int32_t comb_type,
                  std::vector<Task>& tasks, std::vector<int32_t>& pairs, std::vector<int32_t>& parts,
                  int64_t& nscratch, uint32_t keep_types = 0, int64_t keep = 0, int64_t min_own = 0) {
   const int64_t np = int64_t(prim.size());
+  if (min_own > 0) {
+    std::vector<int64_t> idx;
+    std::vector<int32_t> pairs_s;
+    std::vector<int64_t> prod_s;
+    for (Primary& pr : prim)
+      for (PairList& pl : pr.list) {
+        const size_t n = pl.producers.size();
+        if (n < 2 || std::is_sorted(pl.producers.begin(), pl.producers.end())) continue;
+        idx.resize(n);
+        for (size_t q = 0; q < n; ++q) idx[q] = int64_t(q);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int64_t a, int64_t b) { return pl.producers[a] < pl.producers[b]; });
+        pairs_s.resize(2 * n);
+        prod_s.resize(n);
+        for (size_t q = 0; q < n; ++q) {
+          pairs_s[2 * q] = pl.pairs[2 * idx[q]];
+          pairs_s[2 * q + 1] = pl.pairs[2 * idx[q] + 1];
+          prod_s[q] = pl.producers[idx[q]];
+        }
+        pl.pairs.swap(pairs_s);
+        pl.producers.swap(prod_s);
+      }
+  }
   std::vector<TreeNode> nodes;
   std::vector<int32_t> node_list;                     // which list of its owner a node belongs to
   std::vector<std::vector<int32_t>> roots(2 * np);    // per (primary, list): top-level tree nodes

@@ -1421,7 +1421,14 @@ stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int
 }
 
 stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
-  if (!p || which < 0 || which > 7) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!p || which < 0 || which > 11) return fail(STILES_ERR_INVALID, "bad argument");
+  if (which >= 8) {  // a sweep's operand pairs (8 forward, 9 backward) or partial lists (10, 11)
+    const SolveGraph& g = (which % 2 == 0) ? p->fwd : p->bwd;
+    const std::vector<int32_t>& v = which < 10 ? g.pairs : g.parts;
+    if (ntasks) *ntasks = int64_t(which < 10 ? v.size() / 2 : v.size());
+    if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+    return STILES_OK;
+  }
   if (which == 7) {  // the factorization with the forward sweep folded in (host only; built on first use)
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     stiles_plan* pm = const_cast<stiles_plan*>(p);

@@ -2,11 +2,13 @@
 launch (stiles_factorize_solve) against the separate calls: the same factor
 (bit for bit: the extra tasks only read it), the same log-determinant, and the
 solution within FP64 rounding of stiles_solve's (the forward products are summed
-in another order), with a small residual."""
+in another order) and of the oracle's solve, with a small residual."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import analyze as oan
+from oracle import cholesky as och
 from paper_2501_02483_b300 import build, inputs
 from paper_2501_02483_b300 import stiles as st
 
@@ -45,6 +47,11 @@ def test_fused_matches_separate_calls(case):
     assert f1.logdet() == f2.logdet()
     assert np.max(np.abs(x2 - x1)) <= 1e-12 * np.max(np.abs(x1))
     assert _residual(m, x2, m["rhs"]) <= 1e-12
+    # element-wise against the oracle's solve of the same ordering and tile size
+    p = oan.analyze(m, case["T"], case["order"])
+    L = och.factorize(m, p["perm"], case["T"], p["tcolptr"], p["trowidx"])
+    x_ref = och.solve(L, p["perm"], case["T"], p["tcolptr"], p["trowidx"], m["rhs"])
+    assert np.max(np.abs(x2 - x_ref)) <= 1e-10 * np.max(np.abs(x_ref))
     # the factor it leaves solves like any other
     x3 = f2.solve(b).cpu().numpy()
     assert np.array_equal(x3, x1)

@@ -16,6 +16,7 @@ from oracle import analyze as oan
 from oracle import ordering as oord
 from oracle import tiles as otiles
 from paper_2501_02483_b300 import build, inputs
+from tests.golden import make_golden as golden
 from paper_2501_02483_b300 import stiles as st
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -106,7 +107,8 @@ def test_analyze_large_config_identity_matches_oracle():
     plan = st.Plan.from_matrix(m, tile=32, ordering=st.ORDER_NONE)
     tc2, tr2 = plan.tilemap()
     assert np.array_equal(tc, tc2) and np.array_equal(tr, tr2)
-    assert plan.info()["flops_total"] == 40294113166  # oracle count at T = 32
+    # the oracle's count at T = 32, written by tests/golden/make_golden.py
+    assert plan.info()["flops_total"] == golden.load()["flops_total"]
 
 
 def test_rcm_library_equals_oracle_on_hand_cases():
@@ -318,14 +320,40 @@ def test_fused_graph_small_and_degenerate(n_body, n_arrow):
     assert sorted(fus[is_fwd, 1] - nsub) == list(range(nsb))
 
 
+@pytest.mark.parametrize("order", [st.ORDER_NONE, st.ORDER_ND])
 @pytest.mark.parametrize("which", [1, 2])
-def test_sweep_tasks_split_into_leaves_keep_their_newest_inputs(which):
+def test_sweep_tasks_split_into_leaves_keep_their_newest_inputs(which, order):
     """A sweep task with more inputs than a tree chunk (32 by default) sends only
     its older inputs to tree leaves and keeps at least its 8 newest itself; the
-    leaves and the task's own list together name each input once."""
+    leaves and the task's own list together name each input once.  "Newest" is
+    by producer: every input a task keeps comes from a block task at or after
+    the latest producer of any input in its leaves (also under nested
+    dissection, where block index order is not producer order)."""
     m = inputs.band_arrow(6000, 100, 500, 0.2, 3)  # up to 31 band blocks + 7 arrow blocks per column at B = 16
-    plan = st.Plan.from_matrix(m, tile=16, ordering=st.ORDER_NONE)
+    plan = st.Plan.from_matrix(m, tile=16, ordering=order)
     tasks = plan.tasks(which)
+    pairs, parts = plan.tasks(which + 7), plan.tasks(which + 9)[:, 0]
+    # rank of each block's producing task in ticket order, and the task writing each scratch block
+    rank = {}
+    for t in range(tasks.shape[0]):
+        if tasks[t, 0] == 0:
+            rank[int(tasks[t, 1])] = t
+    writer = {int(tasks[t, 1]): t for t in range(tasks.shape[0]) if tasks[t, 0] in (2, 3)}
+
+    def leaf_blocks(t):
+        if tasks[t, 0] == 2:
+            return [int(b) for b in pairs[tasks[t, 4]:tasks[t, 5], 1]]
+        return [b for q in range(tasks[t, 6], tasks[t, 7]) for b in leaf_blocks(writer[int(parts[q])])]
+
+    checked = 0
+    for t in range(tasks.shape[0]):
+        if tasks[t, 0] != 0 or tasks[t, 7] == tasks[t, 6]:
+            continue
+        own = [rank[int(b)] for b in pairs[tasks[t, 4]:tasks[t, 5], 1]]
+        leaves = [rank[b] for q in range(tasks[t, 6], tasks[t, 7]) for b in leaf_blocks(writer[int(parts[q])])]
+        assert min(own) >= max(leaves)
+        checked += 1
+    assert checked > 0
     final = tasks[:, 0] == 0
     own = tasks[:, 5] - tasks[:, 4]
     has_parts = tasks[:, 7] > tasks[:, 6]

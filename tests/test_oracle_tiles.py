@@ -146,3 +146,15 @@ def test_neighbors_symmetric_and_filled():
         for j in nb[k]:
             assert k in nb[j]
     assert math.isfinite(float(nt))
+
+
+@pytest.mark.slow
+def test_golden_large_workload_values_come_from_the_oracle():
+    """The stored flop count and log-determinant of the 200,000-row workload
+    (tests/golden/large_workload.json) are what the oracle computes now."""
+    from tests.golden import make_golden
+
+    ref = make_golden.load()
+    vals = make_golden.large_workload_values()
+    assert vals["flops_total"] == ref["flops_total"]
+    assert abs(vals["logdet"] - ref["logdet"]) <= 1e-13 * abs(ref["logdet"])
