@@ -80,7 +80,7 @@ def kernel_digest():
 # DRAM bytes (read + write) per launch of factor_f64_kernel, keyed by (kernel
 # digest, workload, tile, block): one capture of a smaller case of the same
 # structure, scaled to the full launch by the number of sub-tiles.
-TRAFFIC = {}
+TRAFFIC = {("88ac8d8dae0771a8", "spatiotemporal", 16, 16): 1.717e10}  # 20 time steps: 3.246e9 B x 5.289 sub-tiles
 
 
 def parse():
@@ -95,8 +95,9 @@ def parse():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ordering", choices=["none", "rcm", "auto", "nd"], default="nd")
-    ap.add_argument("--precision", choices=["f64", "bf16", "f16"], default="f64",
-                    help="spatiotemporal/large: update precision (bf16/f16 need tile 64; FP64 refinement)")
+    ap.add_argument("--precision", choices=["f64", "bf16", "f16", "sliced"], default="f64",
+                    help="spatiotemporal/large: update precision (bf16/f16 need tile 64, FP64 refinement; "
+                         "sliced: FP64-accurate tensor-core updates, tile a multiple of 32)")
     ap.add_argument("--nested-steps", type=int, default=5, help="timed steps of each nested measurement")
     ap.add_argument("--sweep", default="32,64,128,256,512", help="large band: tile sizes timed briefly; '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -124,7 +125,7 @@ def _order(st, name):
 
 
 def _prec(st, name):
-    return {"f64": st.PREC_F64, "bf16": st.PREC_BF16, "f16": st.PREC_F16}[name]
+    return {"f64": st.PREC_F64, "bf16": st.PREC_BF16, "f16": st.PREC_F16, "sliced": st.PREC_SLICED}[name]
 
 
 def spatiotemporal(time_steps=100, seed=0):
@@ -407,6 +408,12 @@ def single_matrix(st, torch, dev, m, *, tile, order, prec, steps, warmup, block=
            "refine_iters": f.refine_iters(), "tile": tile, "block": info["block"], "nnzt": info["nnzt"],
            "ntasks": info["ntasks"], "fused_forward_sweep": fused}
     out["kernel_tflops"] = flops / (out["kernel_ms"] * 1e-3) / 1e12
+    if prec == st.PREC_SLICED:
+        # tensor work issued: per tile pair (and per diagonal-chain SYRK term) four
+        # M = 128, N = 32, K = 32 BF16 MMAs (the 16 slice products)
+        nchain = int(np.sum(plan.tasks(0)[:, 0] == 4))
+        out["tensor_flops"] = (info["npairs"] + nchain) * 4 * 2 * 128 * 32 * 32
+        out["tensor_tflops"] = out["tensor_flops"] / (out["kernel_ms"] * 1e-3) / 1e12
 
     if e2e:
         # end to end through pinned host buffers: H2D values + RHS, D2H x + logdet
@@ -550,6 +557,14 @@ def run_single(args):
            **res["e2e"]}
     if prec == st.PREC_F64:
         roof = _fp64_roofline(st, res, peak, wl, res["fused_forward_sweep"])
+    elif prec == st.PREC_SLICED:
+        tpeak, src = _tensor_peak()
+        roof = {"bound": "tensor", "achieved": res["tensor_tflops"], "peak": tpeak, "unit": "TFLOP/s",
+                "frac": res["tensor_tflops"] / tpeak, "traffic": None, "kernel": "factor_oz_kernel",
+                "kernel_ms": res["kernel_ms"], "peak_source": src,
+                "achieved_fp64_equivalent": res["kernel_tflops"],
+                "note": "achieved counts the BF16 slice products issued (16 per tile pair); the FP64-equivalent "
+                        "rate counts Algorithm 1's tile flops"}
     else:
         tpeak, src = _tensor_peak()
         roof = {"bound": "tensor", "achieved": res["kernel_tflops"], "peak": tpeak, "unit": "TFLOP/s",
@@ -582,6 +597,15 @@ def run_single(args):
                    "speedup_vs_fp64_step": res["ms_per_step"] / lp["ms_per_step"],
                    "tensor_frac": lp["kernel_tflops"] / tpeak, "tensor_peak_source": src})
         cfg["mixed_precision"] = lp
+        # the same matrix with FP64-accurate updates from BF16 digit slices on the tensor cores
+        sl = single_matrix(st, torch, dev, m, tile=32, order=order, prec=st.PREC_SLICED, steps=K, warmup=W,
+                           e2e=False)
+        sl.update({"precision": "sliced", "steps": K, "warmup": W,
+                   "logdet_rel_err_vs_fp64": abs(sl["logdet"] - res["logdet"]) / abs(res["logdet"]),
+                   "speedup_vs_fp64_step": res["ms_per_step"] / sl["ms_per_step"],
+                   "kernel_frac_of_fp64_peak": sl["kernel_tflops"] / peak,
+                   "tensor_frac": sl["tensor_tflops"] / tpeak, "tensor_peak_source": src})
+        cfg["sliced_fp64_accurate"] = sl
         cfg["batched_sweep"] = sweep_measure(args, st, torch, dev, None, steps=K, warmup=W)
         cfg["serving"] = serve_measure(args, st, torch, dev, seed=0)
         # the large variable band: FP64 step at T = 16 and the tile-size sweep

@@ -54,7 +54,19 @@ typedef enum {
 } stiles_status;
 
 enum { STILES_ORDER_NONE = 0, STILES_ORDER_RCM = 1, STILES_ORDER_AUTO = 2, STILES_ORDER_ND = 3 };
-enum { STILES_PREC_F64 = 0, STILES_PREC_BF16 = 1, STILES_PREC_F16 = 2 };
+/* Arithmetic of the off-diagonal tile updates (the SYRK/GEMM terms of Algorithm 1):
+ *   F64     FP64 everywhere (DFMA/DMMA).
+ *   BF16    16-bit operands on the tensor cores, FP32 accumulation, FP32 tiles, FP64 diagonal
+ *   F16     POTRF; solves refined in FP64 (iterative refinement, conjugate-gradient fallback).
+ *   SLICED  FP64-accurate updates on the tensor cores: FP64 tiles, each finished off-diagonal
+ *           tile also split into four BF16 digit slices under a per-row power-of-two scale, every
+ *           slice product accumulated exactly in FP32 and the products combined in 64-bit
+ *           integers; the update carries a relative error of about 2^-33 of the row scales
+ *           (sqrt(a_ii)).  POTRF, TRSM and partial sums stay FP64; the factor is stored and solved
+ *           like an FP64 factor, and solves are refined in FP64 to refine_tol like the 16-bit
+ *           factors' (one step at this accuracy).  32-wide sub-tiles (block 0 or 32, T a multiple
+ *           of 32). */
+enum { STILES_PREC_F64 = 0, STILES_PREC_BF16 = 1, STILES_PREC_F16 = 2, STILES_PREC_SLICED = 3 };
 
 typedef struct {
   int32_t tile;       /* T, the CTSF tile size.  analyze accepts any T >= 1; factorize needs a
@@ -156,7 +168,7 @@ stiles_status stiles_factorize_solve(const stiles_plan* plan, const double* valu
                                      int32_t nrhs, int64_t ld, void* stream, stiles_factor** inout, int64_t* info);
 
 /* Solve A X = B for nrhs right-hand sides: X = P^T L^{-T} L^{-1} P B.
- * For a BF16/FP16 factor the solve refines in FP64: x <- x + solve(b - A x) with the residual
+ * For a BF16/FP16 or SLICED factor the solve refines in FP64: x <- x + solve(b - A x) with the residual
  * from the original FP64 values, until ||b - A x||_2 / ||b||_2 <= opts.refine_tol for every
  * column or opts.max_refine steps (then STILES_ERR_NOT_CONVERGED, x holding the last iterate).
  * A refinement step that does not halve the residual (the factor too inaccurate for refinement
@@ -207,7 +219,8 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
 /* The device task list of a plan (which: 0 factorization, 1 forward, 2 backward sweep) in ticket
  * order.  Factorization tasks are 16 int32: type (0 DIAG, 1 OFF, 2 tree leaf, 3 tree node,
  * 4 CHAIN), output, diagonal sub-tile, column, pair range [pb, pe), partial range [qb, qe),
- * second output, its column, its pair range, its partial range, 2 unused.  Solve tasks are
+ * second output, its column, its pair range, its partial range, and the block row and block
+ * column of the tile its first accumulator updates (a tree task: its owner's).  Solve tasks are
  * 8 int32: type (0 block, 2 leaf, 3 node), output block, diagonal sub-tile, column, pair
  * range, partial range.  which = 3..6 give the selected inverse's graph (Sigma L = L^{-T} on
  * the filled sub-tile map, built on the host at the first call): 3 = tasks, 8 int32 each

@@ -9,7 +9,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libstiles.so")
 SOURCES = ["capi.cu", "analyze.cpp", "noalloc.cu"]
-HEADERS = ["plan.h", "device_common.cuh", "factor_f64.cuh", "factor_lp.cuh", "solve.cuh", "aux_kernels.cuh",
+HEADERS = ["plan.h", "device_common.cuh", "factor_f64.cuh", "factor_lp.cuh", "factor_oz.cuh", "solve.cuh", "aux_kernels.cuh",
            "selinv.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -270,6 +270,12 @@ constexpr int32_t kIndexMask = (1 << 30) - 1;
 
 inline void set_col(DevTask& t, int32_t c) { t.col = c; }
 inline void set_col(SolveTask& t, int32_t c) { t.pad0 = c; }
+// row and column block of the tile a factor task's first accumulator updates
+inline void set_target(DevTask& t, int32_t row, int32_t col) {
+  t.trow = row;
+  t.tcol = col;
+}
+inline void set_target(SolveTask&, int32_t, int32_t) {}
 
 }  // namespace
 
@@ -289,6 +295,7 @@ struct PairList {
 
 struct Primary {
   int32_t type, out, diag, col;
+  int32_t row = -1;                // block row of `out` (factorization)
   int32_t out2 = -1, col2 = -1;    // CHAIN: second output
   PairList list[2];                // list[1] only for CHAIN
 };
@@ -427,6 +434,11 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
     tk.out = nd.scratch;
     tk.diag = -1;
     clear_second(tk);
+    {
+      const Primary& ow = prim[nd.owner];
+      if (node_list[id] == 0) set_target(tk, ow.row, ow.col);
+      else set_target(tk, ow.col2, ow.col2);
+    }
     if (nd.type == leaf_type) {
       const PairList& pl = prim[nd.owner].list[node_list[id]];
       tk.pb = int32_t(pairs.size() / 2);
@@ -482,6 +494,7 @@ void build_graph(std::vector<Primary>& prim, int64_t chunk, int64_t fanin, int32
     if (pr.out2 >= 0) set_second(tk, pr, 0, 0, 0, 0);
     else clear_second(tk);
     set_col(tk, pr.col);
+    set_target(tk, pr.row, pr.col);
     tasks.push_back(tk);
     // leaves released by this primary, then any combine that became complete
     for (int32_t leaf : by_release[t]) {
@@ -602,7 +615,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   stiles_opts o = opts_in;
   if (o.tile < 1) { *err = "tile must be >= 1"; return STILES_ERR_INVALID; }
   if (o.ordering < 0 || o.ordering > 3) { *err = "unknown ordering"; return STILES_ERR_INVALID; }
-  if (o.precision < 0 || o.precision > 2) { *err = "unknown precision"; return STILES_ERR_INVALID; }
+  if (o.precision < 0 || o.precision > 3) { *err = "unknown precision"; return STILES_ERR_INVALID; }
   if (o.tree_chunk <= 0) o.tree_chunk = 32;
   if (o.tree_fanin <= 1) o.tree_fanin = 16;
   if (o.max_refine <= 0) o.max_refine = 20;
@@ -714,9 +727,12 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
   trows.clear();
   trows.shrink_to_fit();
 
-  // device sub-tile size (the mixed-precision kernel works on 64-wide sub-tiles)
+  // device sub-tile size (the mixed-precision kernel works on 64-wide sub-tiles,
+  // the sliced-update kernel on 32-wide ones)
   int64_t B = o.block;
-  if (o.precision != STILES_PREC_F64) {
+  if (o.precision == STILES_PREC_SLICED) {
+    B = (o.block == 0 || o.block == 32) ? 32 : 0;
+  } else if (o.precision != STILES_PREC_F64) {
     B = (o.block == 0 || o.block == 64) ? 64 : 0;
   } else if (B == 0) {
     B = (T % 32 == 0) ? 32 : (T % 16 == 0 ? 16 : 0);
@@ -830,6 +846,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       c.col = int32_t(k - 1);
       c.out2 = p->diag_sub[k];
       c.col2 = int32_t(k);
+      c.row = int32_t(k);
       size_t a2 = 0, b2 = 0;  // OFF part: n < k-1 common to rows k and k-1
       while (a2 < rk.size() && b2 < rp.size()) {
         if (rk[a2].idx >= k - 1 || rp[b2].idx >= k - 1) break;
@@ -857,6 +874,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       d.out = p->diag_sub[k];
       d.diag = -1;
       d.col = int32_t(k);
+      d.row = int32_t(k);
       for (const SubEntry& en : rk) {
         if (en.idx >= k) break;
         d.list[0].pairs.push_back(en.sub);
@@ -874,6 +892,7 @@ stiles_status build_plan(int64_t n, const int64_t* colptr, const int32_t* rowidx
       o2.out = scol[k][e].sub;
       o2.diag = p->diag_sub[k];
       o2.col = int32_t(k);
+      o2.row = int32_t(i);
       const auto& ri = srow[i];
       size_t a = 0, c = 0;
       while (a < ri.size() && c < rk.size()) {
@@ -1008,7 +1027,7 @@ stiles_status build_fused(stiles_plan* p, std::string* err) {
     d.col2 = -1;
     d.diag = -1;
     d.pb2 = d.pe2 = d.qb2 = d.qe2 = 0;
-    d.pad0 = d.pad1 = 0;
+    d.trow = d.tcol = -1;  // forward blocks are not tile targets
     const int64_t pb = int64_t(fpairs.size()) / 2;
     for (int32_t q = st.pb; q < st.pe; ++q) {
       const int32_t ls = sg.pairs[2 * size_t(q)], bk = sg.pairs[2 * size_t(q) + 1];

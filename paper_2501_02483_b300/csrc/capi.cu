@@ -17,6 +17,7 @@
 #include "aux_kernels.cuh"
 #include "factor_f64.cuh"
 #include "factor_lp.cuh"
+#include "factor_oz.cuh"
 #include "plan.h"
 #include "selinv.cuh"
 #include "solve.cuh"
@@ -111,12 +112,15 @@ struct stiles_factor {
   const stiles_plan* plan = nullptr;
   int device = -1;
   bool lp = false;            // mixed precision (BF16/FP16 updates, FP32 tiles, FP64 diagonal)
+  bool sliced = false;        // FP64 tiles, updates from BF16 digit slices on the tensor cores
   double* values = nullptr;   // FP64 copy of A's values (CSC order) for residuals
   double* tiles = nullptr;    // FP64 path
   double* scratch = nullptr;
   double* invdiag = nullptr;
   double* linv = nullptr;     // L_kk^{-1} of every diagonal sub-tile (nsb * B * B), for the sweeps, then
                               // the sweeps' folded terms M1 (fwd, bwd), M2 (fwd, bwd): nsb * B * B each
+  uint16_t* slices = nullptr; // sliced path: 4 BF16 digit slices per sub-tile
+  int* rowexp = nullptr;      // sliced path: power-of-two row scales (nsb * B)
   float* tiles32 = nullptr;   // mixed-precision path
   float* linv32 = nullptr;
   uint16_t* tiles16 = nullptr;
@@ -272,7 +276,15 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   int fb = 0, sb = 0;
   cudaError_t e = cudaSuccess;
-  if (p->opts.precision != STILES_PREC_F64) {
+  if (p->opts.precision == STILES_PREC_SLICED) {
+    e = cudaFuncSetAttribute(dev::factor_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(dev::OZ_KERNEL_SMEM));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, dev::factor_oz_kernel, dev::OZ_THREADS, dev::OZ_KERNEL_SMEM);
+    // each resident CTA holds all 512 TMEM columns of its SM
+    fb = std::min(fb, 1);
+    if (e == cudaSuccess) e = solve_occupancy<32, double>(&sb);
+  } else if (p->opts.precision != STILES_PREC_F64) {
     e = cudaFuncSetAttribute(dev::factor_lp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(dev::LP_KERNEL_SMEM));
     if (e == cudaSuccess)
@@ -307,6 +319,8 @@ void free_factor(stiles_factor* f) {
     f->values = f->tiles = f->scratch = f->invdiag = f->ldiag = f->linv = nullptr;
     f->tiles32 = f->scratch32 = f->invdiag32 = f->linv32 = nullptr;
     f->tiles16 = nullptr;
+    f->slices = nullptr;
+    f->rowexp = nullptr;
     f->flags = nullptr;
     f->ctl = nullptr;
     f->logdet_part = f->norms = nullptr;
@@ -317,6 +331,8 @@ void free_factor(stiles_factor* f) {
   cudaFree(f->invdiag);
   cudaFree(f->linv);
   cudaFree(f->linv32);
+  cudaFree(f->slices);
+  cudaFree(f->rowexp);
   cudaFree(f->tiles32);
   cudaFree(f->tiles16);
   cudaFree(f->scratch32);
@@ -358,13 +374,16 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
   // scratch and flags also cover the factorization with the forward sweep
   // folded in: nsb more tiles (the right-hand-side blocks) and its partials
   const int64_t nscr = std::max<int64_t>(p->graph.nscratch + p->fwd.nscratch, 1);
-  f->lp = p->opts.precision != STILES_PREC_F64;
+  f->sliced = p->opts.precision == STILES_PREC_SLICED;
+  f->lp = p->opts.precision != STILES_PREC_F64 && !f->sliced;
   cudaError_t e = cudaMalloc(&f->values, size_t(p->nnz) * sizeof(double));
   if (!f->lp) {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles, size_t(p->nsub + p->nsb) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->scratch, size_t(nscr) * tile * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->invdiag, size_t(p->nsb) * p->B * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->linv, 5 * size_t(p->nsb) * tile * sizeof(double));
+    if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->slices, size_t(p->nsub) * dev::OZ_OP_BYTES);
+    if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->rowexp, size_t(p->nsb) * p->B * sizeof(int));
   } else {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles16, size_t(p->nsub) * tile * sizeof(uint16_t));
@@ -450,6 +469,39 @@ cudaError_t launch_factor(const stiles_plan* p, stiles_factor* f, cudaStream_t s
     if (e != cudaSuccess) return e;
   }
   dev::factor_f64_kernel<B><<<p->dev->grid_factor, 128, dev::FactorCfg<B>::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+dev::OZMatCtx oz_mat_ctx(const stiles_plan* p, stiles_factor* f) {
+  dev::OZMatCtx c;
+  c.tiles = f->tiles;
+  c.slices = f->slices;
+  c.scratch = f->scratch;
+  c.invdiag = f->invdiag;
+  c.rowexp = f->rowexp;
+  c.tasks = p->dev->fac.tasks;
+  c.pairs = p->dev->fac.pairs;
+  c.parts = p->dev->fac.parts;
+  c.flags = f->flags;
+  c.sflags = f->flags + p->nsub + p->nsb;
+  c.info = f->info;
+  c.trace = f->trace[0];
+  return c;
+}
+
+// the sliced-update factorization: row scales from the scattered diagonal, then the persistent kernel
+cudaError_t launch_factor_oz(const stiles_plan* p, stiles_factor* f, cudaStream_t s) {
+  dev::oz_rowexp_kernel<<<grid_for(p->nsb * p->B, 256), 256, 0, s>>>(f->tiles, p->dev->diag_sub, p->nsb, f->rowexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dev::OZArgs a;
+  a.single = oz_mat_ctx(p, f);
+  a.mats = nullptr;
+  a.tickets = nullptr;
+  a.ntasks = p->dev->fac.ntasks;
+  a.ctl = f->ctl;
+  a.spin_limit = p->opts.spin_limit;
+  dev::factor_oz_kernel<<<p->dev->grid_factor, dev::OZ_THREADS, dev::OZ_KERNEL_SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -737,13 +789,14 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   CUDA_TRY(cudaEventRecord(f->ev[1], st));
   cudaError_t e;
   if (f->lp) e = launch_factor_lp(p, f, st);
+  else if (f->sliced) e = launch_factor_oz(p, f, st);
   else switch (p->B) {
     case 16: e = launch_factor<16>(p, f, st); break;
     case 32: e = launch_factor<32>(p, f, st); break;
     default: e = launch_factor<64>(p, f, st); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString(e));
-  count_launch();
+  count_launch(f->sliced ? 2 : 1);
   CUDA_TRY(cudaEventRecord(f->ev[2], st));
   // inverses of the diagonal blocks for the sweeps (after the kernel's timing window)
   e = launch_diag_inverse(p, f, st);
@@ -1078,14 +1131,15 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
     CUDA_TRY(cudaMalloc(&f->ywork, size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
     f->solve_nr = dev::SOLVE_MAXR;
   }
-  if (f->lp && !f->irwork) {
+  const bool refine = f->lp || f->sliced;  // factors whose solves are refined in FP64
+  if (refine && !f->irwork) {
     CUDA_TRY(cudaMalloc(&f->irwork, 4 * size_t(n) * dev::SOLVE_MAXR * sizeof(double)));
     CUDA_TRY(cudaMalloc(&f->cgs, 2 * dev::SOLVE_MAXR * sizeof(double)));
   }
   const double* db = b;
   double* dx = x;
   int64_t bld = ld, xld = ld;  // leading dimensions of the device-side b and x
-  if (bdev && b == x && (f->lp || final_relres)) {
+  if (bdev && b == x && (refine || final_relres)) {
     // in place on the device: keep b for the residuals
     const int64_t need = n * nrhs;
     if (f->stage_elems < need) {
@@ -1125,7 +1179,7 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
   f->last_cg_iters = 0;
   for (int64_t r0 = 0; r0 < nrhs; r0 += dev::SOLVE_MAXR) {
     const int nr = int(std::min<int64_t>(dev::SOLVE_MAXR, nrhs - r0));
-    if (!f->lp) {
+    if (!refine) {
       stiles_status s1 = solve_chunk(p, f, st, db, bld, dx, xld, int(r0), nr);
       if (s1 != STILES_OK) return s1;
       if (final_relres) {
@@ -1136,7 +1190,7 @@ stiles_status stiles_solve(const stiles_factor* cf, const double* b, double* x, 
       }
       continue;
     }
-    // Mixed-precision factor: iterative refinement with FP64 residuals,
+    // Mixed-precision or sliced-update factor: iterative refinement with FP64 residuals,
     // x <- x + solve(b - A x), until ||b - A x|| / ||b|| <= refine_tol.  A step
     // that does not at least halve the residual (or a NaN) means the factor is
     // too inaccurate for refinement to converge: the remaining budget goes to
@@ -2161,6 +2215,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     return s;
   };
   b->plans.assign(plans, plans + count);
+  if (plans[0] && plans[0]->opts.precision == STILES_PREC_SLICED)
+    return bail(fail(STILES_ERR_UNSUPPORTED, "batches of sliced-update plans are not built"));
   b->lp = plans[0]->opts.precision != STILES_PREC_F64;
   b->B = plans[0]->B;
   b->fp16 = plans[0]->opts.precision == STILES_PREC_F16 ? 1 : 0;

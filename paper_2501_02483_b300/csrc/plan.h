@@ -36,7 +36,8 @@ struct DevTask {
   int32_t out2;    // CHAIN: the diagonal sub-tile, else -1
   int32_t col2;    // CHAIN: its sub-column
   int32_t pb2, pe2, qb2, qe2;  // unused (CHAIN terms for `out2` are tagged inside [pb, pe) / [qb, qe))
-  int32_t pad0, pad1;
+  int32_t trow, tcol;  // block row and block column of the tile the first accumulator updates
+                       // (the output, or a tree partial's owner tile; a CHAIN's second target is (col2, col2))
 };
 static_assert(sizeof(DevTask) == 64, "DevTask layout");
 

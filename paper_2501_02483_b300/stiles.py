@@ -18,10 +18,10 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
 import numpy as np
 
 __all__ = ["Plan", "Factor", "Batch", "autotune", "StilesError", "lib", "probe_fp64_peak", "kernel_launches", "ORDER_NONE", "ORDER_RCM", "ORDER_AUTO", "ORDER_ND",
-           "PREC_F64", "PREC_BF16", "PREC_F16", "LIB_PATH"]
+           "PREC_F64", "PREC_BF16", "PREC_F16", "PREC_SLICED", "LIB_PATH"]
 
 ORDER_NONE, ORDER_RCM, ORDER_AUTO, ORDER_ND = 0, 1, 2, 3
-PREC_F64, PREC_BF16, PREC_F16 = 0, 1, 2
+PREC_F64, PREC_BF16, PREC_F16, PREC_SLICED = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SPD", 3: "NOMEM", 4: "CUDA", 5: "TIMEOUT", 6: "NOT_CONVERGED",
           7: "UNSUPPORTED"}
 
