@@ -115,6 +115,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=500.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=256, help="serve: matrices per batched launch")
     ap.add_argument("--gpu-workers", type=int, default=2, help="serve: GPU jobs in flight (one stream each)")
+    ap.add_argument("--sweep-ordering", choices=["none", "rcm", "auto", "nd"], default="nd",
+                    help="sweep: ordering of every plan (nd halves the chains of the large matrices)")
     ap.add_argument("--serve-ordering", choices=["none", "rcm", "auto", "nd"], default="nd",
                     help="serve: ordering of every plan (nd halves the chains of the large matrices)")
     return ap.parse_args()
@@ -634,12 +636,12 @@ def _jsonable(o):
 # ---------------------------------------------------------------------------
 # batched sweep and serving workloads
 # ---------------------------------------------------------------------------
-def _sweep_arm(st, torch, mats, prec, T, dev, dist, steps, warmup):
+def _sweep_arm(st, torch, mats, prec, T, dev, dist, steps, warmup, order):
     """One precision arm of the batched sweep: analysis, then W + K steps of
     batched factorize + logdets + batched solve."""
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    plans = [st.Plan.from_matrix(m, tile=T, ordering=st.ORDER_NONE, precision=prec) for m in mats]
+    plans = [st.Plan.from_matrix(m, tile=T, ordering=order, precision=prec) for m in mats]
     analyze_s = time.perf_counter() - t0
     infos = [p.info() for p in plans]
     flops = sum(i["flops_total"] for i in infos)
@@ -702,10 +704,14 @@ def sweep_measure(args, st, torch, dev, dist, steps, warmup, seed=0):
     """Both arms of the batched sweep on the same matrices."""
     mats = inputs.batch_sweep(args.batch, seed=seed)
     prec = _prec(st, args.lp_precision)
-    lp = _sweep_arm(st, torch, mats, prec, args.lp_tile, dev, dist, steps, warmup)
-    f64 = _sweep_arm(st, torch, mats, st.PREC_F64, args.f64_tile, dev, dist, steps, warmup)
+    order = _order(st, args.sweep_ordering)
+    lp = _sweep_arm(st, torch, mats, prec, args.lp_tile, dev, dist, steps, warmup, order)
+    sl = _sweep_arm(st, torch, mats, st.PREC_SLICED, 32, dev, dist, steps, warmup, order)
+    f64 = _sweep_arm(st, torch, mats, st.PREC_F64, args.f64_tile, dev, dist, steps, warmup, order)
     ld_err = float(np.max(np.abs(lp["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
-    for a in (lp, f64):
+    sl["logdet_rel_diff_vs_fp64"] = float(np.max(np.abs(sl["logdets"] - f64["logdets"]) / np.abs(f64["logdets"])))
+    sl["solves_per_s_over_fp64"] = sl["solves_per_s"] / max(f64["solves_per_s"], 1e-30)
+    for a in (lp, sl, f64):
         a.pop("logdets")
     peak, peak_src = _tensor_peak()
     lp["tensor_frac"] = lp["flops"] / (lp["kernel_ms"] * 1e-3) / 1e12 / peak
@@ -713,8 +719,9 @@ def sweep_measure(args, st, torch, dev, dist, steps, warmup, seed=0):
                         "arrow 0..50, theta ~ U(0.5, 2), 1 RHS each; refined to 1e-10",
             "step": "batched factorize (one persistent launch) + all logdets + batched solve with FP64 "
                     "refinement (analysis once per pattern, timed separately)",
+            "ordering": args.sweep_ordering,
             "steps": steps, "warmup": warmup, "precision": args.lp_precision,
-            "mixed_precision": lp, "fp64": f64, "logdet_rel_diff_lp_vs_fp64": ld_err,
+            "mixed_precision": lp, "sliced_fp64_accurate": sl, "fp64": f64, "logdet_rel_diff_lp_vs_fp64": ld_err,
             "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30),
             "tensor_peak_source": peak_src}
 
@@ -788,6 +795,13 @@ def _serve_arm(args, st, sv, torch, work, prec, T, stream):
            "requests_at_1e-10": len(ok), "requests": len(done), "stats": dict(srv.stats),
            "seconds_by_phase": {k: round(v, 3) for k, v in srv.times.items()},
            "gpu_launches": launches, "clocks": clk.result}
+    both, busy, peak = srv.overlap()
+    kboth, kbusy, kpeak = srv.overlap(kernels=True)
+    out["device_overlap"] = {"jobs_ms_two_or_more": round(both, 1), "jobs_ms_busy": round(busy, 1),
+                             "jobs_peak_in_flight": peak, "factor_kernels_ms_two_or_more": round(kboth, 1),
+                             "factor_kernels_ms_busy": round(kbusy, 1), "factor_kernels_peak": kpeak,
+                             "how": "CUDA events per GPU job on its stream and around each batched persistent "
+                                    "factorization kernel, on one device clock"}
     srv.close()
     return out
 
@@ -799,13 +813,16 @@ def serve_measure(args, st, torch, dev, seed=0):
     work = inputs.serving_workload(args.requests, rate=args.rate, seed=seed, variants=2)
     _pin_requests(torch, work[0])
     lp = _serve_arm(args, st, sv, torch, work, _prec(st, args.lp_precision), args.lp_tile, stream)
+    sl = _serve_arm(args, st, sv, torch, work, st.PREC_SLICED, 32, stream)
+    sl["solves_per_s_over_fp64"] = None
     f64 = _serve_arm(args, st, sv, torch, work, st.PREC_F64, args.f64_tile, stream)
+    sl["solves_per_s_over_fp64"] = sl["solves_per_s"] / max(f64["solves_per_s"], 1e-30)
     return {"workload": f"serving: Poisson {args.rate:g} req/s, {args.requests} requests, n log-uniform "
                         "[1000, 200000], hw 32..512, arrow 0..100, nrhs 1..16, 30% re-solves, HBM budget 150 GB; "
                         "48 patterns x 2 value scales (theta in {0.875, 1.625}); client buffers in pinned host "
                         "memory; ordering " + args.serve_ordering,
             "step": "the whole request stream through the continuous-batching loop (arrivals in real time)",
-            "precision": args.lp_precision, "mixed_precision": lp, "fp64": f64,
+            "precision": args.lp_precision, "mixed_precision": lp, "sliced_fp64_accurate": sl, "fp64": f64,
             "solves_per_s_lp_over_fp64": lp["solves_per_s"] / max(f64["solves_per_s"], 1e-30)}
 
 

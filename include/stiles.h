@@ -102,7 +102,7 @@ typedef struct {
   int64_t npairs;      /* tile-pair updates (GEMM/SYRK terms) at sub-tile granularity  */
   int64_t nscratch;    /* tree-reduction partial tiles                                 */
   int64_t flops_potrf, flops_syrk, flops_gemm, flops_trsm, flops_total; /* at tile size T */
-  int64_t factor_bytes;  /* device bytes of the tile buffer                            */
+  int64_t factor_bytes;  /* device bytes of the tile buffer (SLICED: with the digit slices) */
   int32_t ordering_used; /* STILES_ORDER_NONE, _RCM or _ND                             */
   int32_t chain_split;  /* 1: a one-matrix FP64 launch runs the diagonal chain on reserved SMs (thin DAG) */
 } stiles_plan_info;
@@ -310,6 +310,14 @@ stiles_status stiles_batch_solve(stiles_batch* batch, const double* const* rhs, 
  * (CUDA events recorded around the kernel inside the batch's graph).  Errors: STILES_ERR_INVALID,
  * STILES_ERR_CUDA (no factorization yet). */
 stiles_status stiles_batch_timing(const stiles_batch* batch, double* ms_kernel);
+/* The same kernel on a caller's device clock: its start and end in ms after base_event (a
+ * cudaEvent_t as void*, created with timing enabled and recorded earlier on any stream of the
+ * batch's device), so that the kernels of batches run on different streams can be compared
+ * (Appendix A: concurrent factorizations; the serving loop reports their overlap).  Call after
+ * stiles_batch_factorize has returned.  Errors: STILES_ERR_INVALID (null argument),
+ * STILES_ERR_CUDA (an event not recorded or without timing). */
+stiles_status stiles_batch_kernel_window(const stiles_batch* batch, void* base_event, double* start_ms,
+                                         double* end_ms);
 void stiles_batch_destroy(stiles_batch* batch);
 
 /* Marginal variances diag(A^{-1}) of an FP64 factor (the inverses that Section I lists among

@@ -233,6 +233,13 @@ std::mutex g_plan_mutex;  // plans are shared between threads (plan caches); upl
 #define STILES_CHAIN_SMS 8
 #endif
 constexpr int kChainSms = STILES_CHAIN_SMS;
+// reserved SMs of a sliced-update launch: one chain slot each (at least the two chains of a
+// nested dissection, plus slots that prefetch the next chain tasks' operands)
+#ifndef STILES_OZ_CHAIN_SMS
+#define STILES_OZ_CHAIN_SMS 4
+#endif
+constexpr int kOzChainSms = STILES_OZ_CHAIN_SMS;
+static_assert(kOzChainSms <= kChainSms, "the claim array holds kChainSms entries");
 
 #ifndef STILES_SOLVE_CTAS_PER_MATRIX
 #define STILES_SOLVE_CTAS_PER_MATRIX 128
@@ -501,6 +508,19 @@ cudaError_t launch_factor_oz(const stiles_plan* p, stiles_factor* f, cudaStream_
   a.ntasks = p->dev->fac.ntasks;
   a.ctl = f->ctl;
   a.spin_limit = p->opts.spin_limit;
+  // the diagonal chain on reserved SMs (one chain slot per SM) when the graph has both queues
+  a.chain = p->dev->fac.chain;
+  a.bulk = p->dev->fac.bulk;
+  a.nchain = int(p->chain_order.size());
+  a.nbulk = int(p->bulk_order.size());
+  a.sm_claim = f->claim;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
+  a.chain_sms = (p->dev->grid_factor >= sms && sms > 4 * kOzChainSms && a.nchain > 0 && a.nbulk > 0) ? kOzChainSms : 0;
+  if (a.chain_sms) {
+    e = cudaMemsetAsync(f->claim, 0, kChainSms * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   dev::factor_oz_kernel<<<p->dev->grid_factor, dev::OZ_THREADS, dev::OZ_KERNEL_SMEM, s>>>(a);
   return cudaGetLastError();
 }
@@ -720,7 +740,10 @@ stiles_status stiles_plan_get_info(const stiles_plan* p, stiles_plan_info* info)
   info->flops_gemm = p->flops_gemm;
   info->flops_trsm = p->flops_trsm;
   info->flops_total = p->flops_potrf + p->flops_syrk + p->flops_gemm + p->flops_trsm;
-  info->factor_bytes = p->nsub * int64_t(p->B) * p->B * int64_t(sizeof(double));
+  // FP64 tiles; 16-bit factors hold FP32 tiles plus a 16-bit copy (the same 6 B per entry are
+  // counted as 8); sliced factors add four 2-byte digit slices per entry
+  info->factor_bytes = p->nsub * int64_t(p->B) * p->B *
+                       int64_t(p->opts.precision == STILES_PREC_SLICED ? 16 : sizeof(double));
   info->ordering_used = p->ordering_used;
   info->chain_split = (p->split_queues && p->opts.precision == STILES_PREC_F64) ? 1 : 0;
   return STILES_OK;
@@ -1563,6 +1586,7 @@ struct stiles_batch {
   std::vector<const stiles_plan*> plans;
   std::vector<stiles_factor*> views;
   bool lp = false;
+  bool sliced = false;
   int B = 0;
   int device = -1;
   int fp16 = 0;
@@ -1585,6 +1609,9 @@ struct stiles_batch {
   float* invdiag32 = nullptr;
   float* linv32 = nullptr;
   double* ldiag = nullptr;
+  uint16_t* slices = nullptr;   // sliced updates: 4 BF16 digit slices per sub-tile
+  int* rowexp = nullptr;        // sliced updates: row scales
+  void* drowexp = nullptr;      // sliced updates: per-matrix OZRowexpDesc
   int* flags = nullptr;
   unsigned long long* infos = nullptr;
   stiles::dev::Ctl* ctl = nullptr;
@@ -1844,6 +1871,9 @@ void free_batch(stiles_batch* b) {
   release(b->invdiag);
   release(b->linv);
   release(b->linv32);
+  release(b->slices);
+  release(b->rowexp);
+  release(b->drowexp);
   release(b->dinv);
   release(b->dmlast);
   release(b->tiles32);
@@ -1907,8 +1937,23 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(b->infos, 0xFF, b->plans.size() * sizeof(unsigned long long), st));
   dev::init_ctl_kernel<<<1, 32, 0, st>>>(b->ctl, 1);
   CUDA_TRY(cudaGetLastError());
+  if (b->sliced) {
+    const dim3 gr(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_nsb * 32 + 255) / 256,
+                                                                    std::max<int64_t>(1, 148 * 8 / count)))),
+                  unsigned(count));
+    dev::oz_browexp_kernel<<<gr, 256, 0, st>>>(static_cast<const dev::OZRowexpDesc*>(b->drowexp));
+    CUDA_TRY(cudaGetLastError());
+  }
   CUDA_TRY(cudaEventRecordWithFlags(b->ev_k0, st, cudaEventRecordExternal));  // a node of the captured graph
-  if (b->lp) {
+  if (b->sliced) {
+    dev::OZArgs a{};
+    a.mats = static_cast<const dev::OZMatCtx*>(b->dmats);
+    a.tickets = b->dtickets;
+    a.ntasks = b->ntickets;
+    a.ctl = b->ctl;
+    a.spin_limit = b->spin_limit;
+    dev::factor_oz_kernel<<<b->grid, dev::OZ_THREADS, dev::OZ_KERNEL_SMEM, st>>>(a);
+  } else if (b->lp) {
     dev::LPArgs a{};
     a.mats = static_cast<const dev::LPMatCtx*>(b->dmats);
     a.tickets = b->dtickets;
@@ -2215,9 +2260,9 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     return s;
   };
   b->plans.assign(plans, plans + count);
-  if (plans[0] && plans[0]->opts.precision == STILES_PREC_SLICED)
-    return bail(fail(STILES_ERR_UNSUPPORTED, "batches of sliced-update plans are not built"));
-  b->lp = plans[0]->opts.precision != STILES_PREC_F64;
+  if (!plans[0]) return bail(fail(STILES_ERR_INVALID, "null plan"));
+  b->sliced = plans[0]->opts.precision == STILES_PREC_SLICED;
+  b->lp = plans[0]->opts.precision != STILES_PREC_F64 && !b->sliced;
   b->B = plans[0]->B;
   b->fp16 = plans[0]->opts.precision == STILES_PREC_F16 ? 1 : 0;
   b->spin_limit = plans[0]->opts.spin_limit;
@@ -2261,6 +2306,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->scratch, size_t(b->scratch_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->invdiag, size_t(b->diag_elems));
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->linv, 5 * size_t(b->diag_elems) * b->B);
+  if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->slices, size_t(b->tile_elems) * dev::OZ_NSLICE);
+  if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->rowexp, size_t(b->diag_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles16, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
@@ -2282,6 +2329,8 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   // factor views and per-matrix contexts
   std::vector<dev::MatCtx> mats;
   std::vector<dev::LPMatCtx> lmats;
+  std::vector<dev::OZMatCtx> omats;
+  std::vector<dev::OZRowexpDesc> orow;
   std::vector<BatchLogCtx> logs(count);
   std::vector<BInverse> binv(count);
   std::vector<dev::MlastDesc> bml(count);
@@ -2294,6 +2343,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     v->device = b->device;
     v->view = true;
     v->lp = b->lp;
+    v->sliced = b->sliced;
     v->values = b->values + b->val_off[i];
     v->flags = b->flags + f_off[i];
     v->info = b->infos + i;
@@ -2309,6 +2359,10 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       v->scratch = b->scratch + s_off[i];
       v->invdiag = b->invdiag + d_off[i];
       v->linv = b->linv + 5 * d_off[i] * b->B;
+      if (b->sliced) {
+        v->slices = b->slices + t_off[i] * dev::OZ_NSLICE;
+        v->rowexp = b->rowexp + d_off[i];
+      }
     }
     // the view's small arrays are slices of batch-wide ones; a view never
     // factorizes, so it has no events
@@ -2316,7 +2370,11 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     v->logdet_part = b->vlog + size_t(i) * (dev::LOGDET_BLOCKS + 1);
     v->norms = b->vnorm + size_t(i) * 2 * dev::SOLVE_MAXR;
     if (b->lp) lmats.push_back(lp_mat_ctx(p, v));
-    else mats.push_back(mat_ctx(p, v));
+    else if (b->sliced) {
+      omats.push_back(oz_mat_ctx(p, v));
+      omats.back().trace = nullptr;
+      orow.push_back(dev::OZRowexpDesc{v->tiles, p->dev->diag_sub, p->nsb, v->rowexp});
+    } else mats.push_back(mat_ctx(p, v));
     logs[i] = BatchLogCtx{v->tiles, p->dev->diag_sub, v->ldiag, p->n, b->B, 0};
     binv[i] = BInverse{b->lp ? static_cast<void*>(v->linv32) : static_cast<void*>(v->linv),
                        b->lp ? static_cast<const void*>(v->tiles32) : static_cast<const void*>(v->tiles),
@@ -2341,7 +2399,10 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
     }
   }
   if (b->lp) e = batch_upload(b, reinterpret_cast<dev::LPMatCtx**>(&b->dmats), lmats);
-  else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
+  else if (b->sliced) {
+    e = batch_upload(b, reinterpret_cast<dev::OZMatCtx**>(&b->dmats), omats);
+    if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<dev::OZRowexpDesc**>(&b->drowexp), orow);
+  } else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BInverse**>(&b->dinv), binv);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<dev::MlastDesc**>(&b->dmlast), bml);
@@ -2357,7 +2418,9 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   int per_sm = std::max(1, plans[0]->dev->grid_factor / std::max(1, sms));
-  if (b->lp) {
+  if (b->sliced) {
+    per_sm = 1;  // each CTA holds all 512 TMEM columns of its SM
+  } else if (b->lp) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::factor_lp_kernel, dev::LP_THREADS,
                                                   dev::LP_KERNEL_SMEM);
     per_sm = std::min(per_sm, 4);
@@ -2407,7 +2470,8 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(b->lp ? 4 : 5);  // scatter, init, persistent kernel, diagonal inverses, folded terms (FP64)
+  count_launch(b->lp ? 4 : (b->sliced ? 6 : 5));  // scatter, init, (row scales), persistent kernel, diagonal
+                                                  // inverses, folded terms (FP64 tiles)
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
   CUDA_TRY(cudaEventSynchronize(b->ev_out));
@@ -2498,7 +2562,7 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
   std::vector<double> rel;
   std::vector<int> it(count, 0);
   bool converged = true;
-  if (b->lp) {
+  if (b->lp || b->sliced) {
     // iterative refinement in FP64 per matrix until its residual meets refine_tol
     std::vector<int> active(count);
     int* dactive = nullptr;
@@ -2546,6 +2610,17 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
     if (iters) iters[i] = it[i];
   }
   if (!converged) return fail(STILES_ERR_NOT_CONVERGED, "iterative refinement did not reach refine_tol in the batch");
+  return STILES_OK;
+}
+
+stiles_status stiles_batch_kernel_window(const stiles_batch* b, void* base_event, double* start_ms, double* end_ms) {
+  if (!b || !base_event || !start_ms || !end_ms) return fail(STILES_ERR_INVALID, "null argument");
+  float a = 0.f, e = 0.f;
+  cudaEvent_t base = static_cast<cudaEvent_t>(base_event);
+  CUDA_TRY(cudaEventElapsedTime(&a, base, b->ev_k0));
+  CUDA_TRY(cudaEventElapsedTime(&e, base, b->ev_k1));
+  *start_ms = a;
+  *end_ms = e;
   return STILES_OK;
 }
 

@@ -247,10 +247,13 @@ __device__ __forceinline__ void trsm_rows(double (&acc)[FactorCfg<B>::CPT], cons
   for (int j = 0; j < B; ++j) {
     const int mj = j / RPT;
     const double y = __shfl_sync(0xffffffffu, acc[mj], row_lane0 + (j % RPT));
+    // this thread's columns c = q + RPT m: those with m < j / RPT are all <= j and
+    // those with m > j / RPT all > j, so only m = j / RPT needs the test (a masked
+    // FP64 instruction still takes its issue slot)
 #pragma unroll
-    for (int m = 0; m < CPT; ++m) {
+    for (int m = mj; m < CPT; ++m) {
       const int c = q + RPT * m;
-      if (c > j) acc[m] = fma(-y, sLs[c + j * B], acc[m]);
+      if (m > mj || c > j) acc[m] = fma(-y, sLs[c + j * B], acc[m]);
     }
   }
 #pragma unroll

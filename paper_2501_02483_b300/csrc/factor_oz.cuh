@@ -33,7 +33,10 @@
 // Everything else is FP64 as in the FP64 kernel: tiles, tree partials, the
 // diagonal POTRF (potrf_blocked) and the TRSM of off-diagonal tiles (rows
 // against L_kk with pre-scaled columns).  The CHAIN task's SYRK term of the
-// tile it just solved goes through the same slices (from shared memory).
+// tile it just solved goes through the same slices (from shared memory) into
+// the diagonal target's TMEM blocks: on this GPU an FP64 warp instruction
+// (DFMA or DMMA) holds its sub-partition's FP64 pipe for 64 cycles, so the
+// 32 x 32 x 32 SYRK costs ~7 us on the FP64 path against ~1 us of MMAs.
 // The factor is an FP64 factor: log-determinant, solves and the selected
 // inverse use it as they use the FP64 kernel's.
 //
@@ -94,6 +97,17 @@ struct OZArgs {
   int ntasks;
   Ctl* ctl;
   long long spin_limit;
+  // Optional split of a one-matrix launch (as in the FP64 kernel): the diagonal
+  // chain (DIAG and CHAIN tasks, `chain`) runs on slot 0 of the CTAs on the first
+  // chain_sms SMs, alone on its SM (slot 1 there takes no work), so its FP64
+  // TRSM and POTRF have the SM's FP64 pipes to themselves; every other task
+  // (`bulk`) runs on the other SMs.  Both lists follow the one topological
+  // ticket order.  chain_sms == 0: one queue, ticket = task.
+  const int32_t* chain;
+  const int32_t* bulk;
+  int nchain, nbulk;
+  int chain_sms;
+  int* sm_claim;  // [chain_sms], zeroed per launch
 };
 
 // byte offset of element (r, k) of a 32-wide K-major core-matrix operand
@@ -135,8 +149,9 @@ __device__ __forceinline__ void oz_digits(long long X, uint16_t (&d)[4]) {
   for (int s = 0; s < 4; ++s) d[s] = uint16_t(__float_as_uint(float(r[s])) >> 16);
 }
 
+// role: 0 the single queue, 1 the chain queue, 2 the bulk queue, -1 no work
 template <int SLOT>
-__device__ __forceinline__ void oz_slot(const OZArgs& a, uint32_t tmem, int tid) {
+__device__ __forceinline__ void oz_slot(const OZArgs& a, uint32_t tmem, int tid, int role) {
   using Cfg = FactorCfg<OZ_B>;
   constexpr int RPT = Cfg::RPT, CPT = Cfg::CPT;
   extern __shared__ __align__(1024) unsigned char oz_dyn[];
@@ -260,21 +275,24 @@ __device__ __forceinline__ void oz_slot(const OZArgs& a, uint32_t tmem, int tid)
     else if (tid < 2 * OZ_B) sExpC[tid - OZ_B] = mc.rowexp[size_t(cblk) * OZ_B + tid - OZ_B];
   };
 
+  int* const counter = (role == 1) ? &a.ctl->ticket2 : &a.ctl->ticket;
+  const int nqueue = (role == 1) ? a.nchain : (role == 2 ? a.nbulk : (role == 0 ? a.ntasks : 0));
   int next = 0;
-  if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
+  if (tid == 0 && nqueue > 0) next = atomicAdd(counter, 1);
   bool aborted = false;
   while (!aborted) {
     fence_proxy_async_shared();
     if (tid == 0) {
       int cur = next;
-      if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(&a.ctl->ticket, 1);
+      if (cur < nqueue && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(counter, 1);
       else cur = -1;
       sTicket = cur;
       sAbort = 0;
     }
     sync();
-    const int t = sTicket;
-    if (t < 0) break;
+    const int t0 = sTicket;
+    if (t0 < 0) break;
+    const int t = (role == 1) ? a.chain[t0] : (role == 2 ? a.bulk[t0] : t0);  // task index (one matrix)
     int mi = 0, ti = t;
     if (a.tickets) {
       const int2 v = a.tickets[t];
@@ -374,26 +392,39 @@ __device__ __forceinline__ void oz_slot(const OZArgs& a, uint32_t tmem, int tid)
       acc2[m] = chain ? mc.tiles[size_t(tk.out2) * OZ_TILE + (q + RPT * m) * OZ_B + row] : 0.0;
     }
     if (used_mask & 1) apply_tmem(0, acc1);
-    // tree partials (negated sums) of both targets
-    for (int qi = 0; qi < nq; ++qi) {
-      const int raw = mc.parts[tk.qb + qi];
-      const int s = raw & kIndexMask;
-      if (tid == 0 && !wait_flag(mc.sflags + s, 1, limit, a.ctl)) {
+    // tree partials (negated sums) of both targets: every flag polled together
+    // (relaxed loads in flight, one acquire fence), then all loads issued
+    // before the sums, two partials at a time
+    if (nq > 0) {
+      if (tid == 0 &&
+          !wait_flags([&](int i) { return mc.sflags + (mc.parts[tk.qb + i] & kIndexMask); }, nq, limit, a.ctl)) {
         raise_timeout(a.ctl, t);
         sAbort = 1;
       }
       sync();
       if (sAbort) { aborted = true; break; }
-      const double* src = mc.scratch + size_t(s) * OZ_TILE;
-      if ((raw >> kTargetShift) == 0) {
+      for (int qi = 0; qi < nq; qi += 2) {
+        const int r0 = mc.parts[tk.qb + qi];
+        const int r1 = (qi + 1 < nq) ? mc.parts[tk.qb + qi + 1] : -1;
+        const double* s0 = mc.scratch + size_t(r0 & kIndexMask) * OZ_TILE;
+        const double* s1 = mc.scratch + size_t(r1 < 0 ? 0 : (r1 & kIndexMask)) * OZ_TILE;
+        double v0[CPT], v1[CPT];
 #pragma unroll
-        for (int m = 0; m < CPT; ++m) acc1[m] += __ldcg(src + (q + RPT * m) * OZ_B + row);
-      } else {
+        for (int m = 0; m < CPT; ++m) {
+          v0[m] = __ldcg(s0 + (q + RPT * m) * OZ_B + row);
+          v1[m] = r1 < 0 ? 0.0 : __ldcg(s1 + (q + RPT * m) * OZ_B + row);
+        }
 #pragma unroll
-        for (int m = 0; m < CPT; ++m) acc2[m] += __ldcg(src + (q + RPT * m) * OZ_B + row);
+        for (int m = 0; m < CPT; ++m) {
+          if ((r0 >> kTargetShift) == 0) acc1[m] += v0[m];
+          else acc2[m] += v0[m];
+          if (r1 >= 0) {
+            if ((r1 >> kTargetShift) == 0) acc1[m] += v1[m];
+            else acc2[m] += v1[m];
+          }
+        }
       }
     }
-    if (aborted) break;
 
     if (tree) {
       double* dst = mc.scratch + size_t(tk.out) * OZ_TILE;
@@ -445,21 +476,18 @@ __device__ __forceinline__ void oz_slot(const OZArgs& a, uint32_t tmem, int tid)
       }
       publish(mc.flags + tk.out);
       // CHAIN: the SYRK term L_{k,k-1} L_{k,k-1}^T from the slices in sSl into
-      // the diagonal target's TMEM blocks (rows and columns of block k)
+      // the diagonal target's TMEM blocks (rows and columns of block k), on top
+      // of the target's pair terms
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         issue_mmas(smem_addr(sSl), smem_addr(sSl), tmem + 128u, (used_mask & 2) != 0);
         umma_commit(sbar);
       }
-      if (tid < OZ_B) {
-        sExpR[tid] = mc.rowexp[size_t(tk.col2) * OZ_B + tid];
-        sExpC[tid] = mc.rowexp[size_t(tk.col2) * OZ_B + tid];
-      }
+      if (tid < OZ_B) sExpC[tid] = mc.rowexp[size_t(tk.col2) * OZ_B + tid];  // rows: block k already
       if (!mbar_wait_bounded(sbar, ph_s & 1u)) { aborted = true; break; }
       ph_s ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      sync();  // sExpR / sExpC
-      apply_tmem(128u, acc2);
+      apply_tmem(128u, acc2);  // reads sExpC after its first barrier
 #pragma unroll
       for (int m = 0; m < CPT; ++m) acc1[m] = acc2[m];
     }
@@ -503,11 +531,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) factor_oz_kernel(OZArgs a) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // queue of each slot: the single ticket order, or (split launch) the chain
+  // queue for slot 0 of the first CTA on each reserved SM (slot 1 there and
+  // any other CTA on a reserved SM take no work), the bulk queue elsewhere
+  __shared__ int sRole;
+  if (threadIdx.x == 0) {
+    int role = 0;
+    if (a.chain_sms > 0) {
+      const int sm = smid();
+      role = (sm < a.chain_sms) ? ((atomicAdd(a.sm_claim + sm, 1) == 0) ? 1 : -1) : 2;
+    }
+    sRole = role;
+  }
+  __syncthreads();
+  const int role = sRole;
   static_assert(OZ_SLOTS == 2, "one oz_slot instantiation per slot");
   if (slot == 0)
-    oz_slot<0>(a, sTmem, tid);
+    oz_slot<0>(a, sTmem, tid, role);
   else
-    oz_slot<1>(a, sTmem + OZ_TMEM_COLS, tid);
+    oz_slot<1>(a, sTmem + OZ_TMEM_COLS, tid, role == 1 ? -1 : role);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x < 32)

@@ -6,8 +6,9 @@ re-solve against a factor that is still resident.  The loop:
 * admits requests as they arrive: new matrices go through the analysis pool
   (host threads; the C analysis releases the GIL) and then wait for the GPU;
 * keeps ``gpu_workers`` GPU jobs in flight, each on its own CUDA stream: as
-  soon as a worker is free it takes *all* analysed requests that fit the HBM
-  budget (up to ``max_batch``) and runs them as one batched persistent
+  soon as a worker is free it takes the analysed requests that fit the HBM
+  budget (up to ``max_batch`` matrices and, if set, ``max_job_flops`` tile
+  flops, so that later arrivals reach the next job sooner) and runs them as one batched persistent
   factorization (stiles_batch_*), their log-determinants in one launch and
   their first solves in one batched forward/backward sweep (FP64 refinement
   for BF16/FP16 factors).  Requests that arrive meanwhile join the next job,
@@ -20,7 +21,12 @@ re-solve against a factor that is still resident.  The loop:
   counted as a miss).
 
 Plans are cached per pattern (the same structure with new values -- e.g. a
-hyperparameter sweep -- reuses the symbolic analysis, Section III.A).
+hyperparameter sweep -- reuses the symbolic analysis, Section III.A); a server
+can be started with the plans of known patterns (``warm``).
+
+Every GPU job records a CUDA event on its stream before its first call and
+after its last; ``intervals()`` returns them on one device clock, so that the
+overlap of jobs on the device can be read (``overlap()``).
 
 All numerical work runs in libstiles.so; this module only schedules it.
 """
@@ -77,12 +83,16 @@ class _Resident:
 
 class Server:
     def __init__(self, precision=st.PREC_BF16, tile=64, ordering=st.ORDER_NONE, hbm_budget=150e9, max_batch=256,
-                 analyze_threads=None, refine_tol=1e-10, gpu_workers=2):
+                 analyze_threads=None, refine_tol=1e-10, gpu_workers=2, max_job_flops=None):
         import torch
 
+        self._torch = torch
         self.opts = dict(tile=tile, ordering=ordering, precision=precision, refine_tol=refine_tol)
         self.hbm_budget = float(hbm_budget)
         self.max_batch = max_batch
+        self.max_job_flops = max_job_flops
+        self.jobs = []             # (kind, requests, start event, end event) per GPU job
+        self.kernels = []          # (start ms, end ms) of each factor job's persistent kernel
         if analyze_threads is None:  # the C analysis releases the GIL: one thread per core, up to 32
             analyze_threads = max(1, min(32, os.cpu_count() or 1))
         self.pool = cf.ThreadPoolExecutor(max_workers=analyze_threads)
@@ -101,6 +111,22 @@ class Server:
         self._next_key = 0
 
     # -- analysis (host threads) -------------------------------------------
+    def warm(self, matrices):
+        """Analyse known patterns ahead of the stream: {key: matrix}."""
+        futs = [self.pool.submit(self._plan_for_key, k, m) for k, m in matrices.items()]
+        for f in futs:
+            f.result()
+
+    def _plan_for_key(self, key, matrix):
+        with self.plan_lock:
+            p = self.plans.get(key)
+        if p is not None:
+            return p
+        p = st.Plan.from_matrix(matrix, **self.opts)
+        with self.plan_lock:
+            self.plans.setdefault(key, p)
+            return self.plans[key]
+
     def _plan_for(self, req):
         with self.plan_lock:
             p = self.plans.get(req.key)
@@ -119,7 +145,7 @@ class Server:
         # inverses and, for FP64 factors, the sweeps' folded terms (5 B^2 per diagonal sub-tile)
         B = inf["block"]
         nsb = -(-inf["n"] // B)
-        per_diag = 40.0 if self.opts["precision"] == st.PREC_F64 else 4.0
+        per_diag = 40.0 if self.opts["precision"] in (st.PREC_F64, st.PREC_SLICED) else 4.0
         return (float(inf["factor_bytes"]) + 8.0 * inf["nnz"] + 4.0 * inf["nsub"] + 48.0 * MAX_RHS * inf["n"]
                 + per_diag * nsb * B * B)
 
@@ -139,12 +165,19 @@ class Server:
             self.stats["evicted_batches"] += 1
 
     # -- GPU jobs (worker threads) ---------------------------------------------
+    def _event(self, stream):
+        e = self._torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
     def _job_factor(self, reqs, plans, nbytes, si):
         stream = self.streams[si]
+        ev0 = self._event(stream)
         t0 = time.perf_counter()
         batch = st.Batch(plans)
         t1 = time.perf_counter()
         statuses, _ = batch.factorize([r.matrix["values"] for r in reqs], stream=stream, raise_on_error=False)
+        window = batch.kernel_window(self._base)
         t2 = time.perf_counter()
         lds = batch.logdets(stream=stream)
         # all first solves of the job in one batched forward + backward sweep
@@ -168,8 +201,11 @@ class Server:
                 if r.status == 0 and r.relres <= self.opts["refine_tol"]:
                     solved += r.rhs.shape[1]
             members[r.id] = i
+        ev1 = self._event(stream)
         now = time.perf_counter()
         with self.lock:
+            self.jobs.append(("factor", [r.id for r in reqs], ev0, ev1))
+            self.kernels.append(window)
             key = self._next_key
             self._next_key += 1
             self.resident[key] = _Resident(batch, members, nbytes)
@@ -192,6 +228,7 @@ class Server:
         """group: list of (request, member index); one batched solve over the
         targeted members of one resident batch."""
         stream = self.streams[si]
+        ev0 = self._event(stream)
         t0 = time.perf_counter()
         rhs = [None] * len(res.members)
         for r, i in group:
@@ -202,6 +239,7 @@ class Server:
             if rhs[i] is None:  # more right-hand sides than one batched call takes
                 r.status = 0
                 self._solve_single(r, res.batch.factor(i), stream)
+        ev1 = self._event(stream)
         now = time.perf_counter()
         solved = 0
         for r, i in group:
@@ -216,6 +254,7 @@ class Server:
                 r.status, r.relres = int(bst), float("inf")
             r.t_done = now
         with self.lock:
+            self.jobs.append(("resolve", [r.id for r, _ in group], ev0, ev1))
             res.busy -= 1
             self.stats["solved_columns"] += solved
             self.stats["resolve_jobs"] += 1
@@ -239,6 +278,8 @@ class Server:
         """Serve ``requests`` (Request objects) arriving at ``arrivals`` [s]
         after the start.  Returns the list of completed requests.  ``stream``
         is accepted for compatibility; every GPU job runs on a worker stream."""
+        self.jobs, self.kernels = [], []
+        self._base = self._event(self._torch.cuda.current_stream())
         t0 = time.perf_counter()
         pending_an = collections.deque()   # (request, future of its plan)
         ready = collections.deque()        # (request, plan or None) waiting for the GPU
@@ -309,7 +350,7 @@ class Server:
                 resolves = keep
             # new factorizations: everything analysed so far, within the budget
             if ready and self.free_streams:
-                take, plans, need = [], [], 0.0
+                take, plans, need, flops = [], [], 0.0, 0
                 with self.lock:
                     room = self.hbm_budget - self.resident_bytes - self.inflight_bytes
                 while ready and len(take) < self.max_batch:
@@ -319,10 +360,14 @@ class Server:
                     b = self._bytes(p)
                     if take and need + b > max(room, 0.0) + self._evictable():
                         break
+                    fl = p.info()["flops_total"]
+                    if take and self.max_job_flops is not None and flops + fl > self.max_job_flops:
+                        break
                     ready.popleft()
                     take.append(r)
                     plans.append(p)
                     need += b
+                    flops += fl
                 with self.lock:
                     self._evict_until(need)
                     fits = self.resident_bytes + self.inflight_bytes + need <= self.hbm_budget
@@ -343,6 +388,33 @@ class Server:
                     time.sleep(0.0002)
         self.wall = time.perf_counter() - t0
         return done
+
+    def intervals(self):
+        """GPU jobs on one device clock: (kind, start ms, end ms, request ids), start
+        order; ms from the start of the last run."""
+        self._torch.cuda.synchronize()
+        out = [(k, self._base.elapsed_time(e0), self._base.elapsed_time(e1), ids) for k, ids, e0, e1 in self.jobs]
+        return sorted(out, key=lambda j: j[1])
+
+    def overlap(self, kernels=False):
+        """(ms during which at least two GPU jobs were in flight, ms during which at
+        least one was, largest number in flight at once); kernels=True: the same for
+        the factor jobs' persistent kernels (work running on the device at once)."""
+        pts = []
+        spans = self.kernels if kernels else [(a, b) for _, a, b, _ in self.intervals()]
+        for a, b in spans:
+            pts += [(a, 1), (b, -1)]
+        pts.sort()
+        depth, last, both, busy, peak = 0, 0.0, 0.0, 0.0, 0
+        for t, d in pts:
+            if depth >= 2:
+                both += t - last
+            if depth >= 1:
+                busy += t - last
+            depth += d
+            peak = max(peak, depth)
+            last = t
+        return both, busy, peak
 
     def _evictable(self):
         with self.lock:

@@ -89,6 +89,8 @@ def lib():
         L.stiles_batch_logdet.argtypes = [P, P, P]
         L.stiles_batch_solve.argtypes = [P, P, P, P, P, P, P]
         L.stiles_batch_timing.argtypes = [P, POINTER(c_double)]
+        L.stiles_batch_kernel_window.argtypes = [P, P, POINTER(c_double), POINTER(c_double)]
+        L.stiles_batch_kernel_window.restype = c_int32
         L.stiles_batch_destroy.argtypes = [P]
         L.stiles_batch_destroy.restype = None
         L.stiles_autotune.argtypes = [c_int64, P, P, c_int64, POINTER(Opts), P, c_int32, P, P, POINTER(c_int32), P]
@@ -390,6 +392,14 @@ class Batch:
         ms = c_double(0.0)
         _check(lib().stiles_batch_timing(self._h, ctypes.byref(ms)))
         return ms.value
+
+    def kernel_window(self, base_event):
+        """(start, end) of the last factorize's persistent kernel in ms after ``base_event``
+        (a timing torch.cuda.Event recorded earlier on this device)."""
+        a, b = c_double(0.0), c_double(0.0)
+        _check(lib().stiles_batch_kernel_window(self._h, c_void_p(base_event.cuda_event), ctypes.byref(a),
+                                                ctypes.byref(b)))
+        return a.value, b.value
 
     def logdets(self, stream=None):
         out = np.zeros(len(self.plans), dtype=np.float64)

@@ -5,7 +5,10 @@
   solution: the batched launch computes bit-identical factors, the solution
   agrees to the refinement tolerance);
 * re-solves use resident factors; with a tiny HBM budget factors are evicted,
-  misses are counted and refactorized, and the answers stay correct.
+  misses are counted and refactorized, and the answers stay correct;
+* jobs overlap on the device: per-job CUDA events (and the persistent
+  kernels' own events) on one device clock show two jobs in flight at once,
+  and every result of that run still equals the request served alone.
 """
 import numpy as np
 import pytest
@@ -33,14 +36,7 @@ def _stream(count, seed):
     return [sv.Request(d["id"], d["kind"], d["key"], d["matrix"], d["rhs"], d["target"]) for d in specs], arrivals
 
 
-@pytest.mark.parametrize("prec", [st.PREC_BF16, st.PREC_F64])
-def test_served_results_equal_alone(prec):
-    reqs, arrivals = _stream(30, 1)
-    tile = 64 if prec != st.PREC_F64 else 16
-    srv = sv.Server(precision=prec, tile=tile, max_batch=8)
-    done = srv.run(reqs, arrivals)
-    assert len(done) == len(reqs)
-    assert srv.stats["batches"] >= 2  # later arrivals were admitted into later launches
+def _check_alone(reqs, prec, tile):
     by_id = {r.id: r for r in reqs}
     for r in reqs:
         assert r.status == 0 and r.relres <= 1e-10
@@ -51,6 +47,34 @@ def test_served_results_equal_alone(prec):
         assert f.logdet() == pytest.approx(r.logdet, rel=1e-13)
         x = f.solve(r.rhs)
         assert np.max(np.abs(x - r.x)) <= 1e-9 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("prec", [st.PREC_BF16, st.PREC_F64, st.PREC_SLICED])
+def test_served_results_equal_alone(prec):
+    reqs, arrivals = _stream(30, 1)
+    tile = {st.PREC_F64: 16, st.PREC_SLICED: 32}.get(prec, 64)
+    srv = sv.Server(precision=prec, tile=tile, max_batch=8)
+    done = srv.run(reqs, arrivals)
+    assert len(done) == len(reqs)
+    assert srv.stats["batches"] >= 2  # later arrivals were admitted into later launches
+    _check_alone(reqs, prec, tile)
+    srv.close()
+
+
+def test_jobs_overlap_on_the_device_and_results_equal_alone():
+    reqs, arrivals = _stream(40, 3)
+    srv = sv.Server(precision=st.PREC_F64, tile=16, max_batch=4, gpu_workers=2)
+    done = srv.run(reqs, arrivals)
+    assert len(done) == len(reqs)
+    both, busy, peak = srv.overlap()
+    assert peak >= 2 and both > 0, (both, busy, peak)
+    kboth, kbusy, kpeak = srv.overlap(kernels=True)
+    assert kpeak >= 2 and kboth > 0, (kboth, kbusy, kpeak)
+    # the job intervals lie inside the run and every factor job has a kernel window
+    iv = srv.intervals()
+    assert all(0.0 <= a < b for _, a, b, _ in iv)
+    assert len(srv.kernels) == sum(1 for k, *_ in iv if k == "factor")
+    _check_alone(reqs, st.PREC_F64, 16)
     srv.close()
 
 

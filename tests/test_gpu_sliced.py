@@ -203,9 +203,21 @@ def test_sliced_marginal_variances_match_fp64():
     np.testing.assert_allclose(v, v64, rtol=1e-8)
 
 
-def test_sliced_batches_are_reported_unsupported():
-    m = inputs.config_small(0)
-    plan = st.Plan.from_matrix(m, tile=32, precision=st.PREC_SLICED)
-    with pytest.raises(st.StilesError) as e:
-        st.Batch([plan])
-    assert e.value.name == "UNSUPPORTED"
+def test_sliced_batch_solves_refine_to_target():
+    """A batch of sweep-like matrices (theta-scaled) in one launch: every
+    log-determinant within 1e-8 of the oracle and every batched solve refined to
+    relres <= 1e-10."""
+    mats = inputs.batch_sweep(5, seed=11, n_lo=1500, n_hi=5000)
+    plans = [st.Plan.from_matrix(m, tile=32, ordering=st.ORDER_NONE, precision=st.PREC_SLICED) for m in mats]
+    batch = st.Batch(plans)
+    statuses, _ = batch.factorize([torch.from_numpy(m["values"]).cuda() for m in mats])
+    assert np.all(statuses == 0)
+    lds = batch.logdets()
+    for i, m in enumerate(mats):
+        p = oan.analyze(m, 32, oan.ORDER_NONE)
+        Lo = och.factorize(m, p["perm"], 32, p["tcolptr"], p["trowidx"])
+        ld_o = och.logdet(Lo, p["nt"])
+        assert abs(lds[i] - ld_o) <= LD_TOL * abs(ld_o)
+    xs, rel, its, status = batch.solve([m["rhs"] for m in mats])
+    assert status == 0 and np.all(rel <= RES_TOL) and np.all(its <= 2)
+    batch.close()
