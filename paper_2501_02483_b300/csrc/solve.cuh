@@ -75,7 +75,47 @@ struct SolveArgs {
   int ntasks;
   Ctl* ctl;
   long long spin_limit;
+  // Ready-queue launch (rq_slots != NULL): tickets index a.tickets (batched) or
+  // the task list (one matrix) as before, but they are handed out in the order
+  // in which tasks were released, and a task is released once every task whose
+  // output it reads has started (rq_cnt counts those not yet started; rq_cptr /
+  // rq_cons list each task's readers).  Queue slot i (ctl->ticket hands out i,
+  // ctl->ticket2 the next free slot) holds the i-th released task, -1 until then.
+  // Deadlock-free: a task waits only for tasks that started before it was
+  // released, so the earliest-started unfinished task has all its inputs.
+  int* rq_slots;
+  int* rq_cnt;
+  const int32_t* rq_cptr;
+  const int32_t* rq_cons;
 };
+
+// The ticket in queue slot s once it has been released: -1 when the launch was
+// aborted, -2 when the wait gave up (the caller raises the timeout).
+__device__ __forceinline__ int wait_slot(const int* s, long long limit, Ctl* ctl) {
+  int v = ld_acquire(s);
+  if (v >= 0) return v;
+  for (long long it = 0; it < limit; ++it) {
+    if (it >= 2048) __nanosleep(128);
+    v = ld_acquire(s);
+    if (v >= 0) return v;
+    if ((it & 255) == 255 && ld_volatile(&ctl->abort)) return -1;
+  }
+  return -2;
+}
+
+// Reset of a ready-queue launch: counters from cnt0, the first nsrc slots from
+// src (the tasks that read no other task's output), the rest empty.
+__global__ void rq_reset_kernel(int* slots, int* cnt, const int32_t* cnt0, const int32_t* src, int nsrc, int n,
+                                Ctl* ctl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    cnt[i] = cnt0[i];
+    slots[i] = i < nsrc ? src[i] : -1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->ticket = 0;
+    ctl->ticket2 = nsrc;
+  }
+}
 
 // out(i, r) = [z(i, r) -] sum_p M(i, p) w(p, r) for a B x nr block (128
 // threads; M column-major, or its transpose with TRANS; out may be global or
@@ -146,22 +186,38 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs<TF> a) {
   __syncthreads();
   uint32_t phase = 0;
 
+  const bool rq = a.rq_slots != nullptr;
   int next = 0;
-  if (tid == 0) next = atomicAdd(&a.ctl->ticket, 1);
+  if (tid == 0 && !rq) next = atomicAdd(&a.ctl->ticket, 1);
   while (true) {
     // generic-proxy writes of the previous task to shared buffers that TMA
     // refills (in-place scaling, reused stage areas) before the next copies
     fence_proxy_async_shared();
     if (tid == 0) {
-      int cur = next;
-      if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(&a.ctl->ticket, 1);
-      else cur = -1;
+      int cur = -1;
+      if (rq) {
+        const int slot = ld_volatile(&a.ctl->abort) == 0 ? atomicAdd(&a.ctl->ticket, 1) : a.ntasks;
+        if (slot < a.ntasks) {
+          cur = wait_slot(a.rq_slots + slot, limit, a.ctl);
+          if (cur == -2) raise_timeout(a.ctl, -2 - slot);
+        }
+      } else {
+        cur = next;
+        if (cur < a.ntasks && ld_volatile(&a.ctl->abort) == 0) next = atomicAdd(&a.ctl->ticket, 1);
+        else cur = -1;
+      }
       sTicket = cur;
       sAbort = 0;
     }
     __syncthreads();
     const int t = sTicket;
     if (t < 0) break;
+    if (rq) {  // release the readers for which this was the last producer to start
+      for (int c = a.rq_cptr[t] + tid; c < a.rq_cptr[t + 1]; c += blockDim.x) {
+        const int v = a.rq_cons[c];
+        if (atomicSub(a.rq_cnt + v, 1) == 1) atomicExch(a.rq_slots + atomicAdd(&a.ctl->ticket2, 1), v);
+      }
+    }
     int mi = 0, ti = t;
     if (a.tickets) {
       const int2 v = a.tickets[t];
