@@ -80,7 +80,7 @@ def kernel_digest():
 # DRAM bytes (read + write) per launch of factor_f64_kernel, keyed by (kernel
 # digest, workload, tile, block): one capture of a smaller case of the same
 # structure, scaled to the full launch by the number of sub-tiles.
-TRAFFIC = {("88ac8d8dae0771a8", "spatiotemporal", 16, 16): 1.717e10}  # 20 time steps: 3.246e9 B x 5.289 sub-tiles
+TRAFFIC = {("4481f1c3dac5fd48", "spatiotemporal", 16, 16): 1.717e10}  # 20 time steps: 3.246e9 B x 5.289 sub-tiles
 
 
 def parse():
