@@ -62,10 +62,11 @@ enum { STILES_ORDER_NONE = 0, STILES_ORDER_RCM = 1, STILES_ORDER_AUTO = 2, STILE
  *           tile also split into four BF16 digit slices under a per-row power-of-two scale, every
  *           slice product accumulated exactly in FP32 and the products combined in 64-bit
  *           integers; the update carries a relative error of about 2^-33 of the row scales
- *           (sqrt(a_ii)).  POTRF, TRSM and partial sums stay FP64; the factor is stored and solved
- *           like an FP64 factor, and solves are refined in FP64 to refine_tol like the 16-bit
- *           factors' (one step at this accuracy).  32-wide sub-tiles (block 0 or 32, T a multiple
- *           of 32). */
+ *           (sqrt(a_ii)).  POTRF, TRSM and partial sums stay FP64; the factor is stored (and
+ *           exported, and used by the selected inverse) like an FP64 factor.  Its solves run
+ *           their sweeps on an FP32 copy of the tiles (made after the factorization) and are
+ *           refined in FP64 to refine_tol like the 16-bit factors'.  32-wide sub-tiles (block 0
+ *           or 32, T a multiple of 32). */
 enum { STILES_PREC_F64 = 0, STILES_PREC_BF16 = 1, STILES_PREC_F16 = 2, STILES_PREC_SLICED = 3 };
 
 typedef struct {
@@ -102,7 +103,7 @@ typedef struct {
   int64_t npairs;      /* tile-pair updates (GEMM/SYRK terms) at sub-tile granularity  */
   int64_t nscratch;    /* tree-reduction partial tiles                                 */
   int64_t flops_potrf, flops_syrk, flops_gemm, flops_trsm, flops_total; /* at tile size T */
-  int64_t factor_bytes;  /* device bytes of the tile buffer (SLICED: with the digit slices) */
+  int64_t factor_bytes;  /* device bytes of the tile buffer (SLICED: with the digit slices and the FP32 copy) */
   int32_t ordering_used; /* STILES_ORDER_NONE, _RCM or _ND                             */
   int32_t chain_split;  /* 1: a one-matrix FP64 launch runs the diagonal chain on reserved SMs (thin DAG) */
 } stiles_plan_info;

@@ -55,6 +55,13 @@ __global__ void sub_cols_kernel(double* __restrict__ r, const double* __restrict
   }
 }
 
+// FP32 copy of FP64 tiles, rounded to nearest (the sweeps of a sliced-update
+// factor run on it; its solves are refined against the FP64 matrix).
+__global__ void to_f32_kernel(float* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
+}
+
 __global__ void init_ctl_kernel(Ctl* ctl, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) {

@@ -290,7 +290,7 @@ stiles_status ensure_dev_plan(const stiles_plan* cp) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, dev::factor_oz_kernel, dev::OZ_THREADS, dev::OZ_KERNEL_SMEM);
     // each resident CTA holds all 512 TMEM columns of its SM
     fb = std::min(fb, 1);
-    if (e == cudaSuccess) e = solve_occupancy<32, double>(&sb);
+    if (e == cudaSuccess) e = solve_occupancy<32, float>(&sb);
   } else if (p->opts.precision != STILES_PREC_F64) {
     e = cudaFuncSetAttribute(dev::factor_lp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(dev::LP_KERNEL_SMEM));
@@ -391,6 +391,10 @@ stiles_status alloc_factor(const stiles_plan* p, stiles_factor** out) {
     if (e == cudaSuccess) e = cudaMalloc(&f->linv, 5 * size_t(p->nsb) * tile * sizeof(double));
     if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->slices, size_t(p->nsub) * dev::OZ_OP_BYTES);
     if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->rowexp, size_t(p->nsb) * p->B * sizeof(int));
+    // sliced factors: FP32 copies for the sweeps (refined in FP64)
+    if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
+    if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->invdiag32, size_t(p->nsb) * p->B * sizeof(float));
+    if (f->sliced && e == cudaSuccess) e = cudaMalloc(&f->linv32, size_t(p->nsb) * tile * sizeof(float));
   } else {
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles32, size_t(p->nsub) * tile * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->tiles16, size_t(p->nsub) * tile * sizeof(uint16_t));
@@ -561,6 +565,17 @@ cudaError_t launch_diag_inverse(const stiles_plan* p, stiles_factor* f, cudaStre
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || f->lp) return e;
+  if (f->sliced) {
+    // the sweeps of a sliced-update factor run in FP32 and are refined in FP64:
+    // an FP32 copy of its tiles and the inverses of that copy's diagonal blocks
+    // (the FP64 inverses above serve the selected inverse)
+    const int64_t ne = p->nsub * int64_t(p->B) * p->B;
+    dev::to_f32_kernel<<<grid_for(ne, 256), 256, 0, st>>>(f->tiles32, f->tiles, ne);
+    dev::to_f32_kernel<<<grid_for(p->nsb * p->B, 256), 256, 0, st>>>(f->invdiag32, f->invdiag, p->nsb * p->B);
+    dev::diag_inverse_kernel<32, float><<<grid, 256, 0, st>>>(f->linv32, f->tiles32, f->invdiag32, p->dev->diag_sub,
+                                                              p->nsb);
+    return cudaGetLastError();
+  }
   // then the folded newest terms of every sweep task (reads the inverses; FP64 factors)
   const size_t nt = size_t(p->nsb) * p->B * p->B;
   dev::MlastDesc md{};
@@ -741,9 +756,9 @@ stiles_status stiles_plan_get_info(const stiles_plan* p, stiles_plan_info* info)
   info->flops_trsm = p->flops_trsm;
   info->flops_total = p->flops_potrf + p->flops_syrk + p->flops_gemm + p->flops_trsm;
   // FP64 tiles; 16-bit factors hold FP32 tiles plus a 16-bit copy (the same 6 B per entry are
-  // counted as 8); sliced factors add four 2-byte digit slices per entry
+  // counted as 8); sliced factors add four 2-byte digit slices and an FP32 copy per entry
   info->factor_bytes = p->nsub * int64_t(p->B) * p->B *
-                       int64_t(p->opts.precision == STILES_PREC_SLICED ? 16 : sizeof(double));
+                       int64_t(p->opts.precision == STILES_PREC_SLICED ? 20 : sizeof(double));
   info->ordering_used = p->ordering_used;
   info->chain_split = (p->split_queues && p->opts.precision == STILES_PREC_F64) ? 1 : 0;
   return STILES_OK;
@@ -824,7 +839,7 @@ stiles_status stiles_factorize_async(const stiles_plan* p, const double* values,
   // inverses of the diagonal blocks for the sweeps (after the kernel's timing window)
   e = launch_diag_inverse(p, f, st);
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("diagonal inverses: ") + cudaGetErrorString(e));
-  count_launch(f->lp ? 1 : 2);
+  count_launch(f->lp ? 1 : (f->sliced ? 4 : 2));
   CUDA_TRY(cudaEventRecord(f->done, st));
   f->pending = true;
   f->sinv_valid = false;
@@ -991,7 +1006,8 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
                           double* out, int64_t old_, int r0, int nr) {
   const int64_t n = p->n, B = p->B;
   const int64_t nf = std::max<int64_t>(p->fwd.nscratch, 1), nb = std::max<int64_t>(p->bwd.nscratch, 1);
-  if (f->lp)
+  const bool f32 = f->lp || f->sliced;  // FP32 sweeps (refined in FP64)
+  if (f32)
     dev::permute_in_kernel<float><<<grid_for(p->nsb * B * nr, 256), 256, 0, st>>>(
         reinterpret_cast<float*>(f->Y), rhs, p->dev->perm, n, rld, r0, nr, int(B), p->nsb);
   else
@@ -1003,13 +1019,14 @@ stiles_status solve_chunk(const stiles_plan* p, stiles_factor* f, cudaStream_t s
   CUDA_TRY(cudaGetLastError());
   cudaError_t e;
   if (f->lp) e = launch_solve<64, float>(p, f, st, nr, f->tiles32, f->invdiag32, f->linv32);
+  else if (f->sliced) e = launch_solve<32, float>(p, f, st, nr, f->tiles32, f->invdiag32, f->linv32);
   else switch (p->B) {
     case 16: e = launch_solve<16, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
     case 32: e = launch_solve<32, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
     default: e = launch_solve<64, double>(p, f, st, nr, f->tiles, f->invdiag, f->linv); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
-  if (f->lp)
+  if (f32)
     dev::permute_out_kernel<float><<<grid_for(n * nr, 256), 256, 0, st>>>(out, reinterpret_cast<const float*>(f->Y),
                                                                           p->dev->perm, n, old_, r0, nr, int(B));
   else
@@ -1601,6 +1618,7 @@ struct stiles_batch {
   double* invdiag = nullptr;
   double* linv = nullptr;       // per matrix: L_kk^{-1} and the sweeps' folded terms (5 nsb B^2)
   void* dinv = nullptr;         // per-matrix BInverse descriptors
+  void* dinv32 = nullptr;       // sliced updates: the same for the FP32 copies (the sweeps)
   void* dmlast = nullptr;       // per-matrix MlastDesc descriptors (the sweeps' folded newest terms)
   int64_t max_stasks = 0;       // largest 2 x (forward + backward sweep tasks) of one matrix
   float* tiles32 = nullptr;
@@ -1884,6 +1902,7 @@ void free_batch(stiles_batch* b) {
   release(b->rowexp);
   release(b->drowexp);
   release(b->dinv);
+  release(b->dinv32);
   release(b->dmlast);
   release(b->tiles32);
   release(b->tiles16);
@@ -2002,6 +2021,13 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
       default: bdiag_inverse_kernel<64, double><<<g, 256, 0, st>>>(di); break;
     }
     CUDA_TRY(cudaGetLastError());
+    if (b->sliced) {  // the FP32 copies that the sweeps read (see launch_diag_inverse)
+      dev::to_f32_kernel<<<grid_for(b->tile_elems, 256), 256, 0, st>>>(b->tiles32, b->tiles, b->tile_elems);
+      dev::to_f32_kernel<<<grid_for(b->diag_elems, 256), 256, 0, st>>>(b->invdiag32, b->invdiag, b->diag_elems);
+      bdiag_inverse_kernel<32, float><<<g, 256, 0, st>>>(static_cast<const BInverse*>(b->dinv32));
+      CUDA_TRY(cudaGetLastError());
+      return STILES_OK;
+    }
     const dim3 gm(unsigned(std::max<int64_t>(1, std::min<int64_t>(b->max_stasks, std::max(1, 148 * 8 / count)))),
                   unsigned(count));
     const dev::MlastDesc* dm = static_cast<const dev::MlastDesc*>(b->dmlast);
@@ -2123,7 +2149,7 @@ stiles_status ensure_batch_solve(stiles_batch* b) {
   }
   b->nfwd = int(tf.size());
   b->nbwd = int(tb.size());
-  const size_t ctx_bytes = b->lp ? sizeof(dev::SolveCtx<float>) : sizeof(dev::SolveCtx<double>);
+  const size_t ctx_bytes = (b->lp || b->sliced) ? sizeof(dev::SolveCtx<float>) : sizeof(dev::SolveCtx<double>);
   cudaError_t e = batch_alloc(b, &b->sY, size_t(ytot));
   if (e == cudaSuccess) e = batch_alloc(b, &b->sScr, size_t(stot));
   if (e == cudaSuccess) e = batch_alloc(b, &b->sFlags, size_t(ftot));
@@ -2158,6 +2184,7 @@ stiles_status ensure_batch_solve(stiles_batch* b) {
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   cudaError_t oe;
   if (b->lp) oe = solve_occupancy<64, float>(&per_sm);
+  else if (b->sliced) oe = solve_occupancy<32, float>(&per_sm);
   else switch (b->B) {
     case 16: oe = solve_occupancy<16, double>(&per_sm); break;
     case 32: oe = solve_occupancy<32, double>(&per_sm); break;
@@ -2285,7 +2312,7 @@ stiles_status batch_solve_pass(stiles_batch* b, const SweepTickets& tk, cudaStre
                                int64_t max_rows) {
   const BSolveDesc* desc = static_cast<const BSolveDesc*>(b->ddesc);
   const dim3 g = batch_grid(b, max_rows * dev::SOLVE_MAXR);
-  if (b->lp) bpermute_in_kernel<float><<<g, 256, 0, st>>>(desc, which);
+  if (b->lp || b->sliced) bpermute_in_kernel<float><<<g, 256, 0, st>>>(desc, which);
   else bpermute_in_kernel<double><<<g, 256, 0, st>>>(desc, which);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(b->sFlags, 0, size_t(b->sflag_total) * sizeof(int), st));
@@ -2293,13 +2320,14 @@ stiles_status batch_solve_pass(stiles_batch* b, const SweepTickets& tk, cudaStre
   CUDA_TRY(cudaGetLastError());
   cudaError_t e;
   if (b->lp) e = launch_batch_sweeps<64, float>(b, tk, st);
+  else if (b->sliced) e = launch_batch_sweeps<32, float>(b, tk, st);
   else switch (b->B) {
     case 16: e = launch_batch_sweeps<16, double>(b, tk, st); break;
     case 32: e = launch_batch_sweeps<32, double>(b, tk, st); break;
     default: e = launch_batch_sweeps<64, double>(b, tk, st); break;
   }
   if (e != cudaSuccess) return fail(STILES_ERR_CUDA, std::string("batched solve launch: ") + cudaGetErrorString(e));
-  if (b->lp) bpermute_out_kernel<float><<<g, 256, 0, st>>>(desc, which);
+  if (b->lp || b->sliced) bpermute_out_kernel<float><<<g, 256, 0, st>>>(desc, which);
   else bpermute_out_kernel<double><<<g, 256, 0, st>>>(desc, which);
   CUDA_TRY(cudaGetLastError());
   count_launch(7);
@@ -2413,6 +2441,9 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   if (e == cudaSuccess && !b->lp) e = batch_alloc(b, &b->linv, 5 * size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->slices, size_t(b->tile_elems) * dev::OZ_NSLICE);
   if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->rowexp, size_t(b->diag_elems));
+  if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
+  if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->invdiag32, size_t(b->diag_elems));
+  if (e == cudaSuccess && b->sliced) e = batch_alloc(b, &b->linv32, size_t(b->diag_elems) * b->B);
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles32, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->tiles16, size_t(b->tile_elems));
   if (e == cudaSuccess && b->lp) e = batch_alloc(b, &b->scratch32, size_t(b->scratch_elems));
@@ -2437,7 +2468,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   std::vector<dev::OZMatCtx> omats;
   std::vector<dev::OZRowexpDesc> orow;
   std::vector<BatchLogCtx> logs(count);
-  std::vector<BInverse> binv(count);
+  std::vector<BInverse> binv(count), binv32;
   std::vector<dev::MlastDesc> bml(count);
   for (int i = 0; i < count; ++i) {
     const stiles_plan* p = plans[i];
@@ -2467,6 +2498,10 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
       if (b->sliced) {
         v->slices = b->slices + t_off[i] * dev::OZ_NSLICE;
         v->rowexp = b->rowexp + d_off[i];
+        v->tiles32 = b->tiles32 + t_off[i];
+        v->invdiag32 = b->invdiag32 + d_off[i];
+        v->linv32 = b->linv32 + d_off[i] * b->B;
+        binv32.push_back(BInverse{v->linv32, v->tiles32, v->invdiag32, p->dev->diag_sub, p->nsb});
       }
     }
     // the view's small arrays are slices of batch-wide ones; a view never
@@ -2510,6 +2545,7 @@ stiles_status stiles_batch_create(const stiles_plan* const* plans, int32_t count
   } else e = batch_upload(b, reinterpret_cast<dev::MatCtx**>(&b->dmats), mats);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BatchLogCtx**>(&b->dlog), logs);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<BInverse**>(&b->dinv), binv);
+  if (e == cudaSuccess && b->sliced) e = batch_upload(b, reinterpret_cast<BInverse**>(&b->dinv32), binv32);
   if (e == cudaSuccess) e = batch_upload(b, reinterpret_cast<dev::MlastDesc**>(&b->dmlast), bml);
   if (e != cudaSuccess) return bail(fail(STILES_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   std::vector<int64_t> lens(count);
@@ -2575,7 +2611,7 @@ stiles_status stiles_batch_factorize(stiles_batch* b, const double* const* value
                              cudaMemcpyDefault, b->stream));
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
-  count_launch(b->lp ? 4 : (b->sliced ? 6 : 5));  // scatter, init, (row scales), persistent kernel, diagonal
+  count_launch(b->lp ? 4 : (b->sliced ? 8 : 5));  // scatter, init, (row scales), persistent kernel, diagonal
                                                   // inverses, folded terms (FP64 tiles)
   CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
   CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
@@ -2657,7 +2693,7 @@ stiles_status stiles_batch_solve(stiles_batch* b, const double* const* rhs, doub
     CUDA_TRY(cudaMemcpy(b->rq_call_b, sb.data(), sb.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     tk = SweepTickets{b->rq_call_f, b->rq_call_b, int(sf.size()), int(sb.size()), int(nf), int(nb), nact};
   }
-  if (b->lp) s = upload_solve_ctx<float>(b, nr, st);
+  if (b->lp || b->sliced) s = upload_solve_ctx<float>(b, nr, st);
   else s = upload_solve_ctx<double>(b, nr, st);
   if (s != STILES_OK) return s;
   for (int i = 0; i < count; ++i)

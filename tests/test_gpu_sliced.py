@@ -6,7 +6,7 @@ four BF16 digit slices per operand (per-row power-of-two scales), combined in
 Tolerances against the FP64 oracle (and closed forms):
 * log-determinant: relative 1e-8 (the stated target for the tensor-core path);
 * solves: ||b - A x|| / ||b|| <= 1e-10 after FP64 refinement (the stated target);
-  the factor alone gives ~3e-10 on these inputs, so one refinement step is taken;
+  the sweeps run on an FP32 copy of the factor (~1e-7 alone), one refinement step;
 * factor entries: |L - L_oracle| <= 1e-8 max|L|.  Derivation: every update
   term is exact up to the slices' representation error, |dL_ij| <= 2^-33 2^e_i
   with 2^e_i <= 2 sqrt(a_ii), i.e. a backward error of about
