@@ -2028,8 +2028,10 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
       CUDA_TRY(cudaGetLastError());
       return STILES_OK;
     }
-    const dim3 gm(unsigned(std::max<int64_t>(1, std::min<int64_t>(b->max_stasks, std::max(1, 148 * 8 / count)))),
-                  unsigned(count));
+    // x spans the largest matrix's products (CTAs past a smaller matrix's end leave at once):
+    // x = 148 * 8 / count left the largest matrices' products nearly serial (~11 ms of a
+    // 256-matrix batch at B = 16, ~70 ms at B = 32)
+    const dim3 gm(unsigned(std::max<int64_t>(1, std::min<int64_t>(b->max_stasks, 148 * 8))), unsigned(count));
     const dev::MlastDesc* dm = static_cast<const dev::MlastDesc*>(b->dmlast);
     if (!b->lp) switch (b->B) {
       case 16: dev::bmlast_kernel<16, double><<<gm, 128, 0, st>>>(dm); break;
