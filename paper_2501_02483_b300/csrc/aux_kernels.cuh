@@ -190,46 +190,48 @@ __global__ void permute_out_kernel(double* __restrict__ x, const TY* __restrict_
 // terms i >= k, row k of the CSR the terms j < k, so the product is a pure
 // gather (no atomics, a fixed summation order).  One warp per index k, the
 // lanes striding over the entries (coalesced), each loaded entry serving all
-// NR right-hand sides.  The NR per-lane sums are combined by a butterfly
-// reduce-scatter: at each of the first log2(NR) shuffle levels a lane keeps
-// half of its sums and adds the partner's copy of that half, so NR = 16 costs
-// 16 FP64 adds per warp instead of 5 * 16 for separate reductions (an FP64 add
-// takes as much pipe time as an FMA); lane l ends with column (l >> (5 - log2 NR)).
+// NR right-hand sides.  NR is the exact count: every FMA is an FP64 instruction
+// (64 cycles of issue per warp here) and a predicated-off one still takes its
+// slot, so the products are not padded.  The NR per-lane sums are combined by
+// a butterfly reduce-scatter over NP = NR rounded up to a power of two (the
+// padding sums are zeros): at each of the first log2(NP) shuffle levels a lane
+// keeps half of its sums and adds the partner's copy of that half, so NP = 16
+// costs 16 FP64 adds per warp instead of 5 * 16 for separate reductions; lane
+// l ends with column (l >> (5 - log2 NP)).
 template <int NR>
 __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* __restrict__ colptr,
                                            const int32_t* __restrict__ rowidx, const int64_t* __restrict__ rptr,
                                            const int32_t* __restrict__ rcol, const int64_t* __restrict__ rval,
                                            const double* __restrict__ val, const double* __restrict__ x, int64_t sx,
-                                           int64_t ldx, double* __restrict__ y, int64_t ldy, int nr) {
-  static_assert(NR == 1 || NR == 2 || NR == 4 || NR == 8 || NR == 16, "NR is a power of two <= 16");
-  double v[NR];
+                                           int64_t ldx, double* __restrict__ y, int64_t ldy) {
+  static_assert(NR >= 1 && NR <= 16, "1 to 16 right-hand sides");
+  constexpr int NP = NR == 1 ? 1 : NR <= 2 ? 2 : NR <= 4 ? 4 : NR <= 8 ? 8 : 16;
+  double v[NP];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) v[r] = 0.0;
+  for (int r = 0; r < NP; ++r) v[r] = 0.0;
   const int64_t c1 = colptr[k + 1];
   for (int64_t e = colptr[k] + lane; e < c1; e += 32) {
     const double a = __ldg(val + e);
     const int64_t i = __ldg(rowidx + e);
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nr) v[r] = fma(a, __ldg(x + i * sx + r * ldx), v[r]);
+    for (int r = 0; r < NR; ++r) v[r] = fma(a, __ldg(x + i * sx + r * ldx), v[r]);
   }
   const int64_t r1 = rptr[k + 1];
   for (int64_t e = rptr[k] + lane; e < r1; e += 32) {
     const double a = __ldg(val + __ldg(rval + e));
     const int64_t j = __ldg(rcol + e);
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nr) v[r] = fma(a, __ldg(x + j * sx + r * ldx), v[r]);
+    for (int r = 0; r < NR; ++r) v[r] = fma(a, __ldg(x + j * sx + r * ldx), v[r]);
   }
   // butterfly reduce-scatter over the 32 lanes
-  int cnt = NR;
+  int cnt = NP;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     if (cnt > 1) {
       const int half = cnt / 2;
       const bool upper = (lane & off) != 0;
 #pragma unroll
-      for (int h = 0; h < NR / 2; ++h) {
+      for (int h = 0; h < NP / 2; ++h) {
         if (h < half) {
           const double send = upper ? v[h] : v[h + half];
           const double keep = upper ? v[h + half] : v[h];
@@ -241,22 +243,26 @@ __device__ __forceinline__ void symv_index(int64_t k, int lane, const int64_t* _
       v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
     }
   }
-  constexpr int SHIFT = (NR == 1) ? 5 : (NR == 2) ? 4 : (NR == 4) ? 3 : (NR == 8) ? 2 : 1;
+  constexpr int SHIFT = (NP == 1) ? 5 : (NP == 2) ? 4 : (NP == 4) ? 3 : (NP == 8) ? 2 : 1;
   const int r = lane >> SHIFT;
-  if ((lane & ((1 << SHIFT) - 1)) == 0 && r < nr) y[k + r * ldy] = v[0];
+  if ((lane & ((1 << SHIFT) - 1)) == 0 && r < NR) y[k + r * ldy] = v[0];
 }
 
-// nr <= 16 right-hand sides in groups of 1, 2, 4, 8 or 16 (an FP64 instruction
-// predicated off still takes its pipe slot, so the group fits nr)
+// nr <= 16 right-hand sides, one instantiation per count
 __device__ __forceinline__ void symv_index_any(int64_t k, int lane, const int64_t* colptr, const int32_t* rowidx,
                                                const int64_t* rptr, const int32_t* rcol, const int64_t* rval,
                                                const double* val, const double* x, int64_t sx, int64_t ldx, double* y,
                                                int64_t ldy, int nr) {
-  if (nr <= 1) symv_index<1>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
-  else if (nr <= 2) symv_index<2>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
-  else if (nr <= 4) symv_index<4>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
-  else if (nr <= 8) symv_index<8>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
-  else symv_index<16>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy, nr);
+#define STILES_SYMV_CASE(N) \
+  case N: symv_index<N>(k, lane, colptr, rowidx, rptr, rcol, rval, val, x, sx, ldx, y, ldy); break;
+  switch (nr) {
+    STILES_SYMV_CASE(1) STILES_SYMV_CASE(2) STILES_SYMV_CASE(3) STILES_SYMV_CASE(4)
+    STILES_SYMV_CASE(5) STILES_SYMV_CASE(6) STILES_SYMV_CASE(7) STILES_SYMV_CASE(8)
+    STILES_SYMV_CASE(9) STILES_SYMV_CASE(10) STILES_SYMV_CASE(11) STILES_SYMV_CASE(12)
+    STILES_SYMV_CASE(13) STILES_SYMV_CASE(14) STILES_SYMV_CASE(15) STILES_SYMV_CASE(16)
+    default: break;  // no right-hand side (callers pass 1 to 16)
+  }
+#undef STILES_SYMV_CASE
 }
 
 // y = A x (n x nr, leading dimensions ldx / n), one warp per index

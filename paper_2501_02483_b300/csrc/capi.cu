@@ -11,6 +11,7 @@
 #include <limits>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -1666,6 +1667,9 @@ struct stiles_batch {
   void* dfwd = nullptr;
   void* dbwd = nullptr;
   void* ddesc = nullptr;
+  int2* dspmv = nullptr;            // (matrix, its block) of every block of a batched A x
+  int nspmv = 0;
+  std::vector<int> spmv_blocks;     // per matrix
   int2* tfwd = nullptr;  // sweep ticket -> (matrix, task): every matrix's list in turn
   int2* tbwd = nullptr;
   int nfwd = 0, nbwd = 0;
@@ -1730,6 +1734,7 @@ struct BSolveDesc {
   const int64_t* perm;
   int64_t n, nsb;
   int B, nr;
+  int spmv_blocks, pad0;  // blocks of the batched A x that serve this matrix
   void* Y;  // sweep blocks, in the factor's storage type
   double* b;
   double* x;
@@ -1785,12 +1790,19 @@ __global__ void binterleave_kernel(const BSolveDesc* desc) {
 }
 
 // y = A x for matrix blockIdx.y (x read interleaved from d), one warp per index (no atomics)
-__global__ void bspmv_kernel(const BSolveDesc* desc) {
-  const BSolveDesc c = desc[blockIdx.y];
+// Batched A x: block b serves matrix blocks[b].x as its blocks[b].y-th of
+// desc.spmv_blocks blocks, whose warps stride over the matrix's indices (the
+// dense arrow rows, consecutive indices, land on different warps and SMs).
+// Every matrix gets blocks in proportion to its nonzeros, largest first: one
+// row of blocks per matrix left the largest matrices' rows on a few SMs (SMs
+// active 56% of a 52-matrix product, its FP64 pipe 92% busy while they were).
+__global__ void bspmv_kernel(const BSolveDesc* desc, const int2* blocks) {
+  const int2 bl = blocks[blockIdx.x];
+  const BSolveDesc c = desc[bl.x];
   if (c.nr == 0) return;
   const int lane = threadIdx.x & 31;
-  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c.n; k += warps)
+  const int64_t warps = int64_t(c.spmv_blocks) * (blockDim.x >> 5);
+  for (int64_t k = int64_t(bl.y) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c.n; k += warps)
     dev::symv_index_any(k, lane, c.colptr, c.rowidx, c.rptr, c.rcol, c.rval, c.values, c.d, c.nr, 1, c.y, c.n, c.nr);
 }
 
@@ -1903,6 +1915,7 @@ void free_batch(stiles_batch* b) {
   release(b->drowexp);
   release(b->dinv);
   release(b->dinv32);
+  release(b->dspmv);
   release(b->dmlast);
   release(b->tiles32);
   release(b->tiles16);
@@ -2164,6 +2177,26 @@ stiles_status ensure_batch_solve(stiles_batch* b) {
   if (e == cudaSuccess) e = batch_alloc(b, reinterpret_cast<BSolveDesc**>(&b->ddesc), size_t(count));
   if (e == cudaSuccess) e = batch_upload(b, &b->tfwd, tf);
   if (e == cudaSuccess) e = batch_upload(b, &b->tbwd, tb);
+  {
+    // blocks of the batched A x: 148 x 32 in all, in proportion to each matrix's
+    // nonzeros (at least one, at most one warp per index), largest matrix first
+    std::vector<int> ord(count);
+    std::iota(ord.begin(), ord.end(), 0);
+    double wsum = 0.0;
+    for (int i = 0; i < count; ++i) wsum += double(b->plans[i]->nnz);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return b->plans[x]->nnz > b->plans[y]->nnz; });
+    b->spmv_blocks.assign(count, 1);
+    std::vector<int2> sb;
+    for (int i : ord) {
+      const stiles_plan* p = b->plans[i];
+      const int64_t cap = std::max<int64_t>(1, (p->n + 7) / 8);
+      const int64_t nb = std::min<int64_t>(cap, std::max<int64_t>(1, int64_t(148.0 * 32.0 * double(p->nnz) / wsum + 0.5)));
+      b->spmv_blocks[i] = int(nb);
+      for (int64_t j = 0; j < nb; ++j) sb.push_back(make_int2(i, int(j)));
+    }
+    b->nspmv = int(sb.size());
+    if (e == cudaSuccess) e = batch_upload(b, &b->dspmv, sb);
+  }
   if (e == cudaSuccess) e = batch_upload(b, &b->rq_cptr_f, cpf);
   if (e == cudaSuccess) e = batch_upload(b, &b->rq_cons_f, cnf);
   if (e == cudaSuccess) e = batch_upload(b, &b->rq_cnt0_f, c0f);
@@ -2231,6 +2264,7 @@ stiles_status upload_solve_ctx(stiles_batch* b, const std::vector<int>& nr, cuda
     d.nsb = p->nsb;
     d.B = p->B;
     d.nr = nr[i];
+    d.spmv_blocks = b->spmv_blocks[i];
     d.Y = Y;
     d.b = b->vb + b->vec_off[i];
     d.x = b->vx + b->vec_off[i];
@@ -2353,7 +2387,7 @@ stiles_status batch_residual(stiles_batch* b, cudaStream_t st, int64_t max_rows,
   const int count = int(b->plans.size());
   CUDA_TRY(cudaMemsetAsync(b->vnorms, 0, size_t(count) * 2 * dev::SOLVE_MAXR * sizeof(double), st));
   binterleave_kernel<<<batch_grid(b, max_rows * dev::SOLVE_MAXR), 256, 0, st>>>(desc);
-  bspmv_kernel<<<batch_grid(b, max_rows * 32), 256, 0, st>>>(desc);
+  bspmv_kernel<<<unsigned(b->nspmv), 256, 0, st>>>(desc, b->dspmv);
   CUDA_TRY(cudaGetLastError());
   dim3 g = batch_grid(b, max_rows);
   g.z = dev::SOLVE_MAXR;
