@@ -1965,8 +1965,12 @@ void free_batch(stiles_batch* b) {
 stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   const size_t tbytes = b->lp ? sizeof(float) : sizeof(double);
   const int count = int(b->plans.size());
+  // The per-matrix helper grids below span the largest matrix up to a cap that
+  // does not shrink with the batch (blocks past a smaller matrix's end leave at
+  // once): a cap of 148 x k / count blocks left the largest matrices' entries
+  // and diagonal tiles to a few SMs.
   const dim3 sg(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_scatter + 255) / 256,
-                                                                  std::max<int64_t>(1, 148 * 32 / count)))),
+                                                                  std::max<int64_t>(256, 148 * 32 / count)))),
                 unsigned(count));
   const BScatter* sd = static_cast<const BScatter*>(b->dscatter);
   if (b->lp) {
@@ -1983,7 +1987,7 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   CUDA_TRY(cudaGetLastError());
   if (b->sliced) {
     const dim3 gr(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_nsb * 32 + 255) / 256,
-                                                                    std::max<int64_t>(1, 148 * 8 / count)))),
+                                                                    std::max<int64_t>(64, 148 * 8 / count)))),
                   unsigned(count));
     dev::oz_browexp_kernel<<<gr, 256, 0, st>>>(static_cast<const dev::OZRowexpDesc*>(b->drowexp));
     CUDA_TRY(cudaGetLastError());
@@ -2024,7 +2028,7 @@ stiles_status batch_enqueue(stiles_batch* b, cudaStream_t st) {
   {
     const int count = int(b->plans.size());
     const dim3 g(unsigned(std::max<int64_t>(1, std::min<int64_t>((b->max_nsb * 32 + 255) / 256,
-                                                                   std::max<int64_t>(1, 148 * 16 / count)))),
+                                                                   std::max<int64_t>(128, 148 * 16 / count)))),
                  unsigned(count));
     const BInverse* di = static_cast<const BInverse*>(b->dinv);
     if (b->lp) bdiag_inverse_kernel<64, float><<<g, 256, 0, st>>>(di);
