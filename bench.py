@@ -22,7 +22,8 @@ Nested in the same line (``config``), each with its own timing:
                     FP64 refinement: step time, refined residual, log-det
                     error against the FP64 step
   batched_sweep     256 matrices of a hyperparameter sweep in one persistent
-                    launch (mixed precision and FP64 arms)
+                    launch (mixed precision, sliced and FP64 arms)
+  batched_sweep_8   the same with 8 matrices (chain-bound)
   serving           a Poisson stream (500 req/s) through the continuous-
                     batching loop: solves/s, requests/s, p50/p99 (both arms)
   large_band        the 200,000-row variable band + 100 arrow rows (FP64, T=16)
@@ -609,6 +610,11 @@ def run_single(args):
                    "tensor_frac": sl["tensor_tflops"] / tpeak, "tensor_peak_source": src})
         cfg["sliced_fp64_accurate"] = sl
         cfg["batched_sweep"] = sweep_measure(args, st, torch, dev, None, steps=K, warmup=W)
+        # a small batch of the same generator: chain-bound, each arm's step is the dependency
+        # chain of its largest matrix
+        a8 = argparse.Namespace(**vars(args))
+        a8.batch = 8
+        cfg["batched_sweep_8"] = sweep_measure(a8, st, torch, dev, None, steps=K, warmup=W)
         cfg["serving"] = serve_measure(args, st, torch, dev, seed=0)
         # the large variable band: FP64 step at T = 16 and the tile-size sweep
         ml = inputs.config_large(0)
