@@ -235,8 +235,12 @@ stiles_status stiles_factor_get_trace(const stiles_factor* factor, int32_t which
  * which = 0; a forward block k is an OFF task with output nsub + k).  which = 8 / 9: the
  * forward / backward sweep's operand pairs, 2 int32 each (L sub-tile, block index), indexed by
  * the solve tasks' pair ranges; which = 10 / 11: their partial lists, 1 int32 each (scratch
- * block), indexed by the partial ranges.  *ntasks receives the number of entries.  out may be
- * NULL to query ntasks. */
+ * block), indexed by the partial ranges.  which = 12..14 / 15..17: the forward / backward
+ * sweep's release lists of a batched (ready-queue) solve launch, 1 int32 each: 12 / 15 the
+ * number of distinct tasks each task reads from (ntasks entries; the tasks with none start the
+ * queue), 13 / 16 the offsets of each task's readers (ntasks + 1 entries), 14 / 17 the readers
+ * (each once per producer).  *ntasks receives the number of entries.  out may be NULL to query
+ * ntasks.  Errors: STILES_ERR_INVALID (null plan, which out of range). */
 stiles_status stiles_plan_tasks(const stiles_plan* plan, int32_t which, int32_t* out, int64_t* ntasks);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */

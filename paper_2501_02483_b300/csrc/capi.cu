@@ -1426,6 +1426,11 @@ stiles_status ensure_selinv(stiles_factor* f, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+bool append_release(const stiles::SolveGraph& g, int64_t nsb, int32_t off, std::vector<int32_t>& cptr,
+                    std::vector<int32_t>& cons, std::vector<int32_t>& cnt0, std::vector<int32_t>& src);
+}  // namespace
+
 extern "C" {
 
 stiles_status stiles_marginal_variances(stiles_factor* f, double* out, void* stream) {
@@ -1516,7 +1521,17 @@ stiles_status stiles_factor_get_trace(const stiles_factor* f, int32_t which, int
 }
 
 stiles_status stiles_plan_tasks(const stiles_plan* p, int32_t which, int32_t* out, int64_t* ntasks) {
-  if (!p || which < 0 || which > 11) return fail(STILES_ERR_INVALID, "bad argument");
+  if (!p || which < 0 || which > 17) return fail(STILES_ERR_INVALID, "bad argument");
+  if (which >= 12) {  // a sweep's ready-queue release lists (12-14 forward, 15-17 backward)
+    std::vector<int32_t> cptr{0}, cons, cnt0, src;
+    if (!append_release(which < 15 ? p->fwd : p->bwd, p->nsb, 0, cptr, cons, cnt0, src))
+      return fail(STILES_ERR_INVALID, "internal: a sweep task reads an output produced after it");
+    const int k = (which - 12) % 3;
+    const std::vector<int32_t>& v = k == 0 ? cnt0 : k == 1 ? cptr : cons;
+    if (ntasks) *ntasks = int64_t(v.size());
+    if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+    return STILES_OK;
+  }
   if (which >= 8) {  // a sweep's operand pairs (8 forward, 9 backward) or partial lists (10, 11)
     const SolveGraph& g = (which % 2 == 0) ? p->fwd : p->bwd;
     const std::vector<int32_t>& v = which < 10 ? g.pairs : g.parts;

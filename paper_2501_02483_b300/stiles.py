@@ -202,10 +202,12 @@ class Plan:
         """Device task list (ticket order): int32 (ntasks, 16) for the factorization, (ntasks, 8)
         for a sweep (which 1, 2); the selected inverse's tasks (which 3: (ntasks, 8)), products
         (which 4: (n, 2)), loads of finished terms (which 5: (n, 3)) and X products (which 6: (n, 1));
-        the sweeps' operand pairs (which 8 forward, 9 backward: (n, 2)) and partial lists (10, 11: (n, 1))."""
+        the sweeps' operand pairs (which 8 forward, 9 backward: (n, 2)) and partial lists (10, 11: (n, 1));
+        the sweeps' release lists of a batched solve (12-14 forward, 15-17 backward: producer
+        counts, reader offsets, readers; (n, 1) each)."""
         n = c_int64(0)
         _check(lib().stiles_plan_tasks(self._h, which, None, ctypes.byref(n)))
-        width = {0: 16, 1: 8, 2: 8, 3: 8, 4: 2, 5: 3, 6: 1, 7: 16, 8: 2, 9: 2, 10: 1, 11: 1}[which]
+        width = {0: 16, 1: 8, 2: 8, 3: 8, 4: 2, 5: 3, 6: 1, 7: 16, 8: 2, 9: 2, 10: 1, 11: 1}.get(which, 1)
         out = np.empty((n.value, width), dtype=np.int32)
         _check(lib().stiles_plan_tasks(self._h, which, _ptr(out), ctypes.byref(n)))
         return out

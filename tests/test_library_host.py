@@ -364,3 +364,66 @@ def test_sweep_tasks_split_into_leaves_keep_their_newest_inputs(which, order):
     assert np.all(leaves[:, 5] - leaves[:, 4] <= 32)
     # every input once: the owners' and the leaves' pair counts add up to the sweep's pair total
     assert own[final].sum() + (leaves[:, 5] - leaves[:, 4]).sum() == tasks[:, 5].max()
+
+
+@pytest.mark.parametrize("order", [st.ORDER_NONE, st.ORDER_ND])
+@pytest.mark.parametrize("which", [1, 2])
+def test_sweep_release_lists_and_ready_queue_model(which, order):
+    """The release lists of a batched (ready-queue) sweep launch, read back from
+    the library, against lists rebuilt here from the sweep's pairs and partial
+    lists: each task counts its distinct producers, each producer lists each
+    reader once.  Then the queue rule itself, modelled with 1-3 workers: a
+    worker takes the next released task, which releases every reader whose
+    last producer this was as it starts, and finishes once its producers have
+    finished.  Every task must be released exactly once and finish (no worker
+    waits on a task that can never run)."""
+    m = inputs.band_arrow(6000, 100, 500, 0.2, 3)  # tree partials on the arrow rows
+    plan = st.Plan.from_matrix(m, tile=16, ordering=order)
+    tasks = plan.tasks(which)
+    pairs, parts = plan.tasks(which + 7), plan.tasks(which + 9)[:, 0]
+    base = 12 if which == 1 else 15
+    cnt0, cptr, cons = (plan.tasks(base + k)[:, 0] for k in range(3))
+    n = tasks.shape[0]
+    assert cnt0.shape == (n,) and cptr.shape == (n + 1,) and cons.shape == (int(cptr[-1]),)
+    final = {int(tasks[t, 1]): t for t in range(n) if tasks[t, 0] == 0}
+    writer = {int(tasks[t, 1]): t for t in range(n) if tasks[t, 0] != 0}
+    prods = []
+    for t in range(n):
+        ps = {final[int(b)] for b in pairs[tasks[t, 4]:tasks[t, 5], 1]}
+        ps |= {writer[int(s)] for s in parts[tasks[t, 6]:tasks[t, 7]]}
+        assert all(p < t for p in ps)  # producers precede their readers in the list
+        prods.append(ps)
+    assert [len(ps) for ps in prods] == list(cnt0)
+    readers = [[] for _ in range(n)]
+    for t, ps in enumerate(prods):
+        for p in ps:
+            readers[p].append(t)
+    for p in range(n):
+        got = list(cons[cptr[p]:cptr[p + 1]])
+        assert sorted(got) == sorted(readers[p]) and len(set(got)) == len(got)
+    assert np.any(tasks[:, 0] != 0)  # the case has tree partials
+
+    for workers in (1, 2, 3):
+        cnt = cnt0.copy()
+        queue = [t for t in range(n) if cnt0[t] == 0]
+        head, finished, busy = 0, set(), [None] * workers
+        while len(finished) < n:
+            progress = False
+            for w in range(workers):
+                t = busy[w]
+                if t is not None and prods[t] <= finished:
+                    finished.add(t)
+                    busy[w] = None
+                    progress = True
+            for w in range(workers):
+                if busy[w] is None and head < len(queue):
+                    t = queue[head]
+                    head += 1
+                    busy[w] = t
+                    for v in cons[cptr[t]:cptr[t + 1]]:
+                        cnt[v] -= 1
+                        if cnt[v] == 0:
+                            queue.append(int(v))
+                    progress = True
+            assert progress, (workers, len(finished), n)
+        assert sorted(queue) == list(range(n))
