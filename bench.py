@@ -31,7 +31,7 @@ Nested in the same line (``config``), each with its own timing:
   marginal_variances  diag(A^-1) of the headline matrix by selected inversion
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload full|spatiotemporal|large|sweep|serve] [--no-nested]
+                       [--workload full|spatiotemporal|large|sweep|serve|servebatch] [--no-nested]
 For N > 1 launch with torch.distributed.run; each rank factorizes its own
 replica (weak scaling, no collective on the data path).
 """
@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["full", "spatiotemporal", "large", "sweep", "serve"], default="full",
+    ap.add_argument("--workload", choices=["full", "spatiotemporal", "large", "sweep", "serve", "servebatch"],
+                    default="full",
                     help="full: the spatio-temporal headline with every nested measurement")
     ap.add_argument("--no-nested", action="store_true", help="full: the headline step only")
     ap.add_argument("--tile", type=int, default=16)
@@ -855,6 +856,67 @@ def run_serve(args):
         dist.destroy_process_group()
 
 
+def run_servebatch(args):
+    """The batched refined solve of serving requests, for profiling the solve
+    phase of a served job: the first --batch new requests of the serving
+    generator (n up to 200,000, 1..16 right-hand sides each; the mixed-precision
+    arm's precision and tile), factorized once; then W + K timed batched solves
+    with FP64 refinement to 1e-10 (device-resident right-hand sides)."""
+    torch, world, rank, local, dist = _setup_rank()
+    from paper_2501_02483_b300 import stiles as st
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    reqs, _ = inputs.serving_workload(int(args.batch * 1.6) + 16, rate=args.rate, seed=rank, variants=2)
+    new = [r for r in reqs if r["kind"] == "new"][:args.batch]
+    prec = _prec(st, args.lp_precision)
+    t0 = time.perf_counter()
+    plans = [st.Plan.from_matrix(r["matrix"], tile=args.lp_tile, ordering=_order(st, args.serve_ordering),
+                                 precision=prec) for r in new]
+    analyze_s = time.perf_counter() - t0
+    batch = st.Batch(plans)
+    statuses, _ = batch.factorize([torch.from_numpy(r["matrix"]["values"]).to(dev) for r in new], stream=stream)
+    rhs = [torch.from_numpy(np.asfortranarray(r["rhs"])).to(dev) for r in new]
+    ncol = sum(r["rhs"].shape[1] for r in new)
+    for _ in range(args.warmup):
+        batch.solve(rhs, stream=stream, raise_on_error=False)
+    torch.cuda.synchronize()
+    n0 = st.kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            xs, rel, its, status = batch.solve(rhs, stream=stream, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = st.kernel_launches() - n0
+    ms = _max_over_ranks(torch, dist, dev, e0.elapsed_time(e1) / args.steps)
+    ok = int(np.sum((statuses == 0) & (rel <= 1e-10)))
+    line = {
+        "metric": METRIC, "value": world * ncol / (ms * 1e-3), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.lp_precision, "data": "synthetic",
+        "config": {"workload": f"served batch solve: the first {len(new)} new requests of the serving generator "
+                               "(n log-uniform [1000, 200000], hw 32..512, arrow 0..100, nrhs 1..16), "
+                               f"{args.lp_precision} factors at T = {args.lp_tile}, ordering {args.serve_ordering}",
+                   "step": "one batched solve of every request's right-hand sides, refined in FP64 to 1e-10",
+                   "matrices": len(new), "columns": ncol, "n_max": max(r["matrix"]["n"] for r in new),
+                   "solved_at_1e-10": ok, "max_relres": float(np.max(rel)), "max_refine_iters": int(np.max(its)),
+                   "status": status, "analyze_s": round(analyze_s, 2),
+                   "l2": "inputs larger than L2 (factors of the batch > 10 GB); no flush"},
+        "roofline": None, "e2e": None, "gpu_launches": launches, "clocks": clk.result,
+    }
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -863,6 +925,8 @@ def main():
         run_sweep(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "servebatch":
+        run_servebatch(args)
     else:
         run_single(args)
 
