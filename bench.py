@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--nested-steps", type=int, default=5, help="timed steps of each nested measurement")
     ap.add_argument("--sweep", default="32,64,128,256,512", help="large band: tile sizes timed briefly; '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--marginal-variances", action="store_true",
+                    help="spatiotemporal/large (FP64): also time diag(A^-1) by selected inversion")
     ap.add_argument("--cpu-workers", type=int, default=0, help="oracle processes (0 = every core of the host)")
     ap.add_argument("--rows", type=int, default=200_000,
                     help="large: body rows (profiling runs only; the benchmarked workload is 200,000)")
@@ -553,9 +555,9 @@ def run_single(args):
     wl = "spatiotemporal" if args.workload in ("full", "spatiotemporal") else "large"
     peak = st.probe_fp64_peak()
     nested = args.workload == "full" and not args.no_nested and world == 1
+    keep = (nested or args.marginal_variances) and prec == st.PREC_F64
     res = single_matrix(st, torch, dev, m, tile=args.tile, block=args.block, order=order, prec=prec,
-                        steps=args.steps, warmup=args.warmup, dist=dist,
-                        keep=nested and prec == st.PREC_F64)
+                        steps=args.steps, warmup=args.warmup, dist=dist, keep=keep)
     value = world * res["flops"] / (res["ms_per_step"] * 1e-3) / 1e12
     e2e = {"value": world * res["flops"] / (res["e2e"]["ms_per_step"] * 1e-3) / 1e12, "unit": "TFLOP/s",
            **res["e2e"]}
@@ -586,12 +588,12 @@ def run_single(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic", "config": cfg, "roofline": roof,
             "e2e": e2e, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"]}
 
+    if keep:
+        cfg["marginal_variances"] = marginal_variances(st, torch, dev, res, peak)
+        res["_factor"].close()
+        res["_plan"].close()
     if nested:
         K, W = args.nested_steps, 2
-        if prec == st.PREC_F64:
-            cfg["marginal_variances"] = marginal_variances(st, torch, dev, res, peak)
-            res["_factor"].close()
-            res["_plan"].close()
         # the same matrix with 16-bit updates on the tensor cores + FP64 refinement
         lp = single_matrix(st, torch, dev, m, tile=args.lp_tile, order=order, prec=_prec(st, args.lp_precision),
                            steps=K, warmup=W, e2e=False)
