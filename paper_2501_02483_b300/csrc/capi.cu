@@ -2320,7 +2320,7 @@ struct SweepTickets {
 // tickets: a task enters the queue once every task it reads from has started,
 // so the persistent CTAs take tasks in the order the matrices' chains reach
 // them rather than in one fixed interleaving of all the lists (256 matrices
-// with ND plans: FP64 solves 12% faster, those of sliced factors 16%).  What
+// with ND plans: FP64 solves 12% faster, FP32 ones ~10%).  For FP64 sweeps what
 // remains is the FP64 pipe: seven CTAs share an SM's 2 FMA a cycle, so a chain
 // task next to heavy tree partials runs several times slower than alone.
 template <int B, typename TF>
